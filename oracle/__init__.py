@@ -1,0 +1,115 @@
+"""FP64 CPU oracle for the all-pairs softened N-body force (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg use this package; the CUDA library neither imports nor links it, and it
+shares no code with the library.  The arithmetic lives in ``oracle.c``
+(Eq. 1 of Miki & Hanawa, Sec. III.A, summed directly in double precision); this
+module compiles it with gcc and wraps it for numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, OpenMP, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-std=c11", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        i64, dbl, vp = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+        lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.oracle_accel.argtypes = [i64, vp, vp, dbl, vp, vp]
+        lib.oracle_accel_subset.argtypes = [i64, vp, vp, dbl, i64, vp, vp, vp]
+        lib.oracle_leapfrog.argtypes = [i64, vp, vp, vp, dbl, dbl, i64, vp]
+        lib.oracle_energy.argtypes = [i64, vp, vp, vp, dbl, vp]
+        _lib = lib
+    return _lib
+
+
+def _c(a, dtype=np.float64, shape=None):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def set_threads(nt: int) -> None:
+    _load().oracle_set_threads(int(nt))
+
+
+def accel(pos, mass, eps, with_pot: bool = True):
+    """Eq. 1 for all bodies: returns (acc (n,3), pot (n,) or None), float64."""
+    pos = _c(pos)
+    n = pos.shape[0]
+    pos = _c(pos, shape=(n, 3))
+    mass = _c(mass, shape=(n,))
+    acc = np.zeros((n, 3))
+    pot = np.zeros(n) if with_pot else None
+    _load().oracle_accel(n, _p(pos), _p(mass), float(eps), _p(acc), _p(pot))
+    return acc, pot
+
+
+def accel_subset(pos, mass, eps, idx, with_pot: bool = True):
+    """Eq. 1 for the bodies listed in ``idx`` against all bodies."""
+    pos = _c(pos)
+    n = pos.shape[0]
+    mass = _c(mass, shape=(n,))
+    idx = _c(idx, dtype=np.int64)
+    if idx.size and (idx.min() < 0 or idx.max() >= n):
+        raise IndexError("subset index out of range")
+    ns = idx.shape[0]
+    acc = np.zeros((ns, 3))
+    pot = np.zeros(ns) if with_pot else None
+    _load().oracle_accel_subset(n, _p(pos), _p(mass), float(eps), ns, _p(idx), _p(acc), _p(pot))
+    return acc, pot
+
+
+def leapfrog(pos, vel, mass, eps, dt, steps):
+    """KDK leapfrog for ``steps`` steps: returns (pos, vel, acc) at the end (copies)."""
+    pos = np.array(pos, dtype=np.float64, order="C", copy=True)
+    vel = np.array(vel, dtype=np.float64, order="C", copy=True)
+    n = pos.shape[0]
+    mass = _c(mass, shape=(n,))
+    acc = np.zeros((n, 3))
+    _load().oracle_leapfrog(n, _p(pos), _p(vel), _p(mass), float(eps), float(dt), int(steps), _p(acc))
+    return pos, vel, acc
+
+
+def energy(pos, vel, mass, eps):
+    """Returns dict T, W, E, P (3,), F (3,) = sum m a."""
+    pos = _c(pos)
+    n = pos.shape[0]
+    vel = _c(vel, shape=(n, 3))
+    mass = _c(mass, shape=(n,))
+    out = np.zeros(9)
+    _load().oracle_energy(n, _p(pos), _p(vel), _p(mass), float(eps), _p(out))
+    return {"T": out[0], "W": out[1], "E": out[2], "P": out[3:6].copy(), "F": out[6:9].copy()}

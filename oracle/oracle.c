@@ -1,0 +1,141 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle for the all-pairs softened N-body force.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the parity reference for the CUDA
+ * library and the timed CPU baseline; the library never links, loads or calls
+ * it, and it includes nothing from the library.  Only the tests, the smoke
+ * check and the benchmark's CPU leg use it.
+ *
+ * What it computes (Miki & Hanawa, "Unified schemes for directive-based GPU
+ * offloading", Sec. III.A):
+ *
+ *   Eq. 1 with G = 1 (Henon units):
+ *       a_i   =  sum_{j != i} m_j (r_j - r_i) / (|r_j - r_i|^2 + eps^2)^{3/2}
+ *   the potential accumulated under CALCULATE_POTENTIAL in Listing 4, read as
+ *   the physical (negative) potential with the self term removed:
+ *       phi_i = -sum_{j != i} m_j / (|r_j - r_i|^2 + eps^2)^{1/2}
+ *
+ * Everything is double precision, summed over j in index order, with 1/sqrt
+ * taken as 1.0 / sqrt(s).  OpenMP parallelises over i only, so the result does
+ * not depend on the thread count.  Build with -ffp-contract=off so that no
+ * multiply-add is fused and x86 and Arm give the same bits.
+ *
+ * The integrator, the energy and the adjoint are not in the paper; they follow
+ * the kick-drift-kick leapfrog the library implements:
+ *       v <- v + (dt/2) a(x);  x <- x + dt v;  v <- v + (dt/2) a(x)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void oracle_set_threads(int nt) {
+#ifdef _OPENMP
+    if (nt > 0) omp_set_num_threads(nt);
+#else
+    (void)nt;
+#endif
+}
+
+/* Force and potential on body i from every j != i (Eq. 1, G = 1). */
+static void body_sum(int64_t i, int64_t n, const double* pos, const double* mass, double eps2,
+                     double* a3, double* phi) {
+    const double xi = pos[3 * i + 0], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
+    double ax = 0.0, ay = 0.0, az = 0.0, p = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        const double dx = pos[3 * j + 0] - xi;
+        const double dy = pos[3 * j + 1] - yi;
+        const double dz = pos[3 * j + 2] - zi;
+        const double s = dx * dx + dy * dy + dz * dz + eps2;
+        const double rinv = 1.0 / sqrt(s);
+        const double w = mass[j] * rinv * rinv * rinv; /* m_j s^{-3/2} */
+        ax += w * dx;
+        ay += w * dy;
+        az += w * dz;
+        p -= mass[j] * rinv; /* -m_j s^{-1/2} */
+    }
+    a3[0] = ax;
+    a3[1] = ay;
+    a3[2] = az;
+    if (phi) *phi = p;
+}
+
+/* acc (n,3) and pot (n, may be NULL) for all n bodies. */
+void oracle_accel(int64_t n, const double* pos, const double* mass, double eps, double* acc,
+                  double* pot) {
+    const double eps2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) body_sum(i, n, pos, mass, eps2, acc + 3 * i, pot ? pot + i : NULL);
+}
+
+/* The same sums for the ns bodies listed in idx (each against all n bodies,
+ * itself excluded): acc (ns,3), pot (ns) or NULL. */
+void oracle_accel_subset(int64_t n, const double* pos, const double* mass, double eps, int64_t ns,
+                         const int64_t* idx, double* acc, double* pot) {
+    const double eps2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t k = 0; k < ns; ++k) body_sum(idx[k], n, pos, mass, eps2, acc + 3 * k, pot ? pot + k : NULL);
+}
+
+/* Kick-drift-kick leapfrog, in place, steps >= 0.  The force at the end of a
+ * step is reused for the first kick of the next, so steps + 1 evaluations.
+ * acc_out (n,3), optional: the force at the final positions. */
+void oracle_leapfrog(int64_t n, double* pos, double* vel, const double* mass, double eps, double dt,
+                     int64_t steps, double* acc_out) {
+    double* a = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    oracle_accel(n, pos, mass, eps, a, NULL);
+    const double h = 0.5 * dt;
+    for (int64_t s = 0; s < steps; ++s) {
+        for (int64_t k = 0; k < 3 * n; ++k) vel[k] += h * a[k];
+        for (int64_t k = 0; k < 3 * n; ++k) pos[k] += dt * vel[k];
+        oracle_accel(n, pos, mass, eps, a, NULL);
+        for (int64_t k = 0; k < 3 * n; ++k) vel[k] += h * a[k];
+    }
+    if (acc_out) memcpy(acc_out, a, sizeof(double) * 3 * (size_t)n);
+    free(a);
+}
+
+/* Diagnostics: out[0] = kinetic T = sum m|v|^2/2, out[1] = potential
+ * W = (1/2) sum m_i phi_i, out[2] = E = T + W, out[3..5] = momentum sum m v,
+ * out[6..8] = net force sum m a (zero by Newton's third law). */
+void oracle_energy(int64_t n, const double* pos, const double* vel, const double* mass, double eps,
+                   double* out) {
+    double* a = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double* phi = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    oracle_accel(n, pos, mass, eps, a, phi);
+    double t = 0, w = 0, px = 0, py = 0, pz = 0, fx = 0, fy = 0, fz = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double vx = vel[3 * i], vy = vel[3 * i + 1], vz = vel[3 * i + 2];
+        t += 0.5 * mass[i] * (vx * vx + vy * vy + vz * vz);
+        w += 0.5 * mass[i] * phi[i];
+        px += mass[i] * vx;
+        py += mass[i] * vy;
+        pz += mass[i] * vz;
+        fx += mass[i] * a[3 * i];
+        fy += mass[i] * a[3 * i + 1];
+        fz += mass[i] * a[3 * i + 2];
+    }
+    out[0] = t;
+    out[1] = w;
+    out[2] = t + w;
+    out[3] = px;
+    out[4] = py;
+    out[5] = pz;
+    out[6] = fx;
+    out[7] = fy;
+    out[8] = fz;
+    free(a);
+    free(phi);
+}

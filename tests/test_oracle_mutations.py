@@ -1,0 +1,45 @@
+"""The oracle's pins are sharp enough to catch plausible slips.
+
+Each case copies oracle.c to a temporary directory, plants one mistake in the
+copy (on the CPU, never in the committed file), rebuilds it and runs the pin
+tests against the mutant; every mutant must fail at least one pin.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTANTS = {
+    "force_exponent_1": ("mass[j] * rinv * rinv * rinv", "mass[j] * rinv * rinv"),
+    "self_term_kept_with_softening": ("if (j == i) continue;", "if (j == i && eps2 == 0.0) continue;"),
+    "potential_sign": ("p -= mass[j] * rinv;", "p += mass[j] * rinv;"),
+    "transposed_coordinate": ("pos[3 * j + 1] - yi", "pos[3 * j + 0] - yi"),
+    "softening_dropped": ("+ dz * dz + eps2", "+ dz * dz"),
+    "full_kick_instead_of_half": ("const double h = 0.5 * dt;", "const double h = dt;"),
+    "sink_mass_instead_of_source": ("const double w = mass[j] *", "const double w = mass[i] *"),
+    "drift_uses_old_velocity_sign": ("pos[k] += dt * vel[k];", "pos[k] -= dt * vel[k];"),
+    "energy_half_missing": ("w += 0.5 * mass[i] * phi[i];", "w += mass[i] * phi[i];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, name):
+    old, new = MUTANTS[name]
+    src = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found"
+    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle",
+                    ignore=shutil.ignore_patterns("*.so", "*.tmp*", "__pycache__"))
+    (tmp_path / "oracle" / "oracle.c").write_text(src.replace(old, new))
+    shutil.copytree(os.path.join(ROOT, "nbody_inputs"), tmp_path / "nbody_inputs",
+                    ignore=shutil.ignore_patterns("__pycache__"))
+    os.makedirs(tmp_path / "tests")
+    for f in ("conftest.py", "test_oracle_pins.py", "test_oracle_integrator.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        "tests/test_oracle_pins.py", "tests/test_oracle_integrator.py"],
+                       cwd=tmp_path, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 1, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
