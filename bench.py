@@ -1,0 +1,333 @@
+#!/usr/bin/env python3
+"""Benchmark: all-pairs softened gravity driving a KDK leapfrog on one GB300.
+
+Workload (one "step"): the precision workload -- a Plummer sphere of
+N = 2^20 bodies offset to (1e4, -3e3, 7e2), log-uniform masses in [1e-3, 1]
+renormalised to 1, eps = 2^-9 -- advanced by one nbody_leapfrog call of 4 KDK
+steps with dt = 2^-9: one initial force evaluation plus 4 more, i.e.
+5 * N^2 pair interactions, with FP64 positions and FP32 pair math relative to
+FP64 cell centres.  The metric is pair interactions per second (Gint/s); the
+fraction of the FP32 CUDA-core peak counts 20 flop per interaction.
+
+Legs (one JSON line on rank 0):
+  value       device-resident state, CUDA events around each timed step on
+              the library's stream; L2 flushed (256 MiB write) between steps.
+  plain       the same leapfrog with FP32 absolute coordinates.
+  e2e         the same call on pinned host arrays: host->device copy of the
+              state, the run, device->host copy, all inside the timed region.
+  roofline    the force kernel alone: its summed CUDA-event time over the timed
+              region / launches, against the FP32 ALU peak.
+  cpu_baseline the FP64 oracle on the host cores, on a bounded subsample.
+``--impl reference`` times the oracle alone (the reference arm of this
+comparison) and prints its own line.  Under torchrun each rank runs an
+independent replica (the force does not shard without a position exchange
+that this one-GPU build does not implement); value sums the ranks' work over
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+METRIC = "Gint/s & %FP32 peak at N=2^20, plain vs mixed/batched; adjoint:fwd time"
+UNIT = "Gint/s"
+FLOP_PER_INTERACTION = 20
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_DEFAULT = 2070.0
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(x: float, ws: int) -> float:
+    """Max over ranks of a host scalar (timing bookkeeping only)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                pw.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "power_w_max": max(pw),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm / CPU baseline: the FP64 oracle on a bounded subsample
+# ---------------------------------------------------------------------------
+def oracle_rate(w, target_s: float, max_sample: int = 1 << 14):
+    """Gint/s of the oracle's direct sum for a subsample of sink bodies against
+    all N sources of the workload; the sample grows until it takes ~target_s."""
+    import oracle
+    import nbody_inputs as ni
+    oracle.build()
+    k = 64
+    while True:
+        idx = ni.subsample(w.n, k, 77)
+        t0 = time.perf_counter()
+        oracle.accel_subset(w.pos, w.mass, w.eps, idx, with_pot=False)
+        dt = time.perf_counter() - t0
+        if dt >= target_s or k >= max_sample:
+            return k * w.n / dt / 1e9, k, dt, oracle.num_threads()
+        k = min(max_sample, max(2 * k, int(k * target_s / max(dt, 1e-3))))
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    import nbody_inputs as ni
+    w = ni.precision_offset()
+    rate, k, dt, cores = oracle_rate(w, 2.0, max_sample=4096)
+    vals = []
+    for s in range(args.warmup + args.steps):
+        idx = ni.subsample(w.n, k, 1000 + s)
+        import oracle
+        t0 = time.perf_counter()
+        oracle.accel_subset(w.pos, w.mass, w.eps, idx, with_pot=False)
+        el = time.perf_counter() - t0
+        if s >= args.warmup:
+            vals.append(el)
+    per = statistics.mean(vals)
+    value = k * w.n / per / 1e9
+    sample = f"{k} sink bodies x all {w.n} sources of the workload's initial state, one FP64 force sum per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(w),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(w):
+    return {"workload": "plummer_n1048576_offset1e4_loguniform_mass_eps2^-9_kdk4_dt2^-9", "n": w.n,
+            "eps": w.eps, "dt": w.dt, "kdk_steps_per_step": w.steps, "force_evals_per_step": w.steps + 1,
+            "interactions_per_step": (w.steps + 1) * w.n * w.n, "precision": "mixed (FP64 state, FP32 pair math "
+            "on cell-centred coordinates, Kahan-folded per-tile sums)", "l2": "flushed between timed steps "
+            "(256 MiB write); the force kernel's 32 MiB j-array is L2-resident by design"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    import nbody_inputs as ni
+    import paper_2411_18889_gb300 as nb
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    nb.load()
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+
+    w = ni.precision_offset()
+    n = w.n
+    inter_per_step = (w.steps + 1) * n * n
+    m32 = w.mass.astype(np.float32)
+    P0 = torch.from_numpy(w.pos).to(dev)
+    V0 = torch.from_numpy(w.vel).to(dev)
+    M = torch.from_numpy(m32).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed_leg(precision, steps, warmup):
+        P, V = P0.clone(), V0.clone()
+        torch.cuda.synchronize()
+        for _ in range(warmup):
+            nb.nbody_leapfrog(P, V, M, w.eps, w.dt, w.steps, precision=precision)
+        torch.cuda.synchronize()
+        nb.nbody_profile_read()  # reset counters
+        nb.nbody_profile_enable(True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier(ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(steps):
+            flush.fill_(float(s))
+            evs[s][0].record(stream)
+            nb.nbody_leapfrog(P, V, M, w.eps, w.dt, w.steps, precision=precision)
+            evs[s][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        wall = time.perf_counter() - t0
+        nb.nbody_profile_enable(False)
+        kms, klaunch, alllaunch = nb.nbody_profile_read()
+        step_s = [a.elapsed_time(b) / 1e3 for a, b in evs]
+        assert nb.nbody_last_device_error() == 0
+        return sum(step_s), wall, kms / 1e3, klaunch, alllaunch, step_s
+
+    with ClockSampler(local) as clk:
+        dev_s, wall_s, kern_s, klaunch, launches, per_step = timed_leg(nb.NBODY_PREC_MIXED, args.steps, args.warmup)
+    clocks = clk.summary()
+    t_max = reduce_max(dev_s, ws)
+    value = ws * args.steps * inter_per_step / t_max / 1e9
+    peak_int_s = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_DEFAULT * 1e6 / FLOP_PER_INTERACTION
+    pct = value / ws * 1e9 / peak_int_s * 100
+
+    # plain FP32 absolute coordinates, same launch otherwise
+    psteps = max(1, min(args.steps, 2))
+    pdev_s, _, _, _, _, _ = timed_leg(nb.NBODY_PREC_PLAIN, psteps, 1)
+    plain_value = psteps * inter_per_step / pdev_s / 1e9
+
+    # end to end from pinned host memory through the C ABI
+    Ph = torch.from_numpy(w.pos.copy()).pin_memory()
+    Vh = torch.from_numpy(w.vel.copy()).pin_memory()
+    Mh = torch.from_numpy(m32.copy()).pin_memory()
+    nb.nbody_leapfrog(Ph, Vh, Mh, w.eps, w.dt, w.steps)  # warm the staging buffers
+    esteps = max(1, min(args.steps, 2))
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(esteps):
+        nb.nbody_leapfrog(Ph, Vh, Mh, w.eps, w.dt, w.steps)  # synchronous for host arrays
+    e2e_s = reduce_max(time.perf_counter() - t0, ws)
+    e2e_value = ws * esteps * inter_per_step / e2e_s / 1e9
+    h2d = Ph.numel() * 8 + Vh.numel() * 8 + Mh.numel() * 4
+    d2h = Ph.numel() * 8 + Vh.numel() * 8
+
+    # roofline of the force kernel (ALU bound: 20 flop per interaction)
+    per_launch_s = kern_s / max(klaunch, 1)
+    achieved_tflops = n * n * FLOP_PER_INTERACTION / per_launch_s / 1e12
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_DEFAULT * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved_tflops / peak_tflops, "traffic": None,
+                "kernel": "nbk::force_kernel (stream-K all-pairs; mixed precision, compensated, no potential)",
+                "launches": klaunch, "ms_per_launch": per_launch_s * 1e3,
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {SM_MAX_MHZ_DEFAULT:.0f} MHz"}
+    traffic_file = os.path.join(ROOT, "profiles", "force_traffic.json")
+    if os.path.exists(traffic_file):
+        try:
+            tr = json.load(open(traffic_file))
+            if tr.get("n") == n:
+                roofline["traffic"] = tr.get("dram_bytes_per_launch")
+        except Exception:
+            pass
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_measured_clock"] = achieved_tflops / (peak_tflops * clocks["sm_mhz"] / SM_MAX_MHZ_DEFAULT)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, k, dt, cores = oracle_rate(w, 12.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{k} sink bodies x all {n} sources, one FP64 force sum ({dt:.1f} s)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": workload_config(w),
+        "pct_fp32_peak": pct, "pct_fp32_peak_basis": f"{sms} SMs x 128 lanes x 2 x 2070 MHz at 20 flop/int",
+        "plain": {"value": plain_value, "unit": UNIT, "pct_fp32_peak": plain_value * 1e9 / peak_int_s * 100,
+                  "precision": "FP32 absolute coordinates (fails the accuracy target at this offset by design)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+        "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
+        "wall_s_timed_region": wall_s, "step_ms": [s * 1e3 for s in per_step],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,164 @@
+/*
+ * nbody.h -- C ABI of libnbody: all-pairs Plummer-softened gravity on one
+ * NVIDIA GB300 (sm_103a), with a kick-drift-kick leapfrog driven by it.
+ *
+ * The operation is the N-body demonstration of Miki & Hanawa, "Unified
+ * schemes for directive-based GPU offloading" (IEEE Access 2024), Sec. III.A:
+ *
+ *   Eq. 1 (G = 1, Henon units):
+ *     a_i = sum_{j != i} m_j (r_j - r_i) / (|r_j - r_i|^2 + eps^2)^{3/2}
+ *   and the potential that Listing 4 accumulates under CALCULATE_POTENTIAL,
+ *   returned with the physical sign and without the self term:
+ *     phi_i = -sum_{j != i} m_j / (|r_j - r_i|^2 + eps^2)^{1/2}
+ *
+ * Listing 4's calc_acc(Ni, ipos, iacc, Nj, jpos, eps) fixes the per-pair
+ * arithmetic these kernels keep: r2 as an FMA chain seeded with eps^2, an
+ * approximate reciprocal square root cubed and scaled by m_j, FMA
+ * accumulation, single precision with flush-to-zero (Sec. III.A notes that
+ * fast approximate rsqrt is essential to performance).
+ *
+ * Conventions shared by every call:
+ *  - Arrays are contiguous: positions, velocities and accelerations are
+ *    array-of-structures [n][3]; mass and potential are [n].
+ *  - A pointer may address device memory or host memory (pageable or pinned).
+ *    Device arrays are used in place and the call is asynchronous on
+ *    opts->stream; results are valid once that stream has synchronised.
+ *    If any array of a call is in host memory, the library copies the host
+ *    arrays through its device workspace and the call returns only after the
+ *    results are back in host memory.
+ *  - The caller owns every array; the library never frees or keeps them past
+ *    the call.  Internal workspace is cached per (device, stream) and freed by
+ *    nbody_finalize().  Calls on the same stream are ordered; calls on
+ *    different streams use different workspaces.
+ *  - The current CUDA device of the calling thread is used.
+ *  - Return value: NBODY_OK (0) or one of the negative codes below.
+ *    n == 0 is a no-op returning NBODY_OK.  Arguments are validated before
+ *    any GPU work is queued (NBODY_EINVAL: n < 0, a required pointer NULL,
+ *    eps < 0 or not finite, dt not finite, steps < 0).
+ *  - Coincident bodies with eps == 0 give non-finite results, as Eq. 1 does;
+ *    the self pair is always excluded exactly, so eps == 0 is valid for
+ *    distinct positions.
+ *  - Interactions are counted as n*n per force evaluation (the paper's
+ *    "interaction pairs", Sec. III.A).
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NBODY_OK 0
+#define NBODY_EINVAL (-1)   /* invalid argument */
+#define NBODY_ENOMEM (-2)   /* device or pinned memory allocation failed */
+#define NBODY_ECUDA (-3)    /* a CUDA runtime call failed; see nbody_last_cuda_error() */
+#define NBODY_ETIMEOUT (-4) /* a bounded device-side wait expired (kernel returned early) */
+#define NBODY_ENOTSUP (-5)  /* no usable sm_103 device or unsupported option */
+
+/* Pair arithmetic precision. */
+#define NBODY_PREC_MIXED 0 /* FP64 positions; FP32 pair math on coordinates
+                              relative to FP64 cell centres (default) */
+#define NBODY_PREC_PLAIN 1 /* FP32 absolute coordinates (FP64 input rounded) */
+
+/* Per-body summation over j. */
+#define NBODY_ACC_COMPENSATED 0 /* FP32 per j-tile, tiles folded by Kahan
+                                   summation (default) */
+#define NBODY_ACC_FP32 1        /* one running FP32 sum over all j */
+
+typedef struct nbody_opts {
+    void* stream;   /* cudaStream_t to run on; NULL = legacy default stream */
+    int precision;  /* NBODY_PREC_*; ignored by the *_f32 calls (always plain) */
+    int accumulate; /* NBODY_ACC_* */
+    int config;     /* force-kernel shape index, -1 = the tuned choice for n;
+                       valid indices are 0 .. nbody_num_configs()-1 */
+    int reserved;   /* must be 0 */
+} nbody_opts;
+
+/* Fill *opts with the defaults (NULL stream, mixed, compensated, tuned). */
+void nbody_opts_default(nbody_opts* opts);
+
+/*
+ * Acceleration (Eq. 1) and potential for all n bodies, FP64 positions.
+ *  pos  [n][3] double, mass [n] float, eps >= 0
+ *  acc  [n][3] float, written
+ *  pot  [n] float or NULL (NULL skips the potential term, a cheaper kernel)
+ * opts->precision selects mixed (default) or plain FP32 coordinates.
+ */
+int nbody_accel(int64_t n, const double* pos, const float* mass, double eps, float* acc, float* pot,
+                const nbody_opts* opts);
+
+/* The same with FP32 positions and softening (plain precision, Listing 4's
+ * data types). */
+int nbody_accel_f32(int64_t n, const float* pos, const float* mass, float eps, float* acc, float* pot,
+                    const nbody_opts* opts);
+
+/*
+ * Kick-drift-kick leapfrog driven by Eq. 1, in place (not in the paper; the
+ * integrator the demonstration's force evaluation drives):
+ *   v += (dt/2) a(x);  x += dt v;  v += (dt/2) a(x)      (per step)
+ * The force at the end of a step serves the first kick of the next, so a call
+ * makes steps + 1 force evaluations.  pos, vel [n][3] double (FP64 drift and
+ * kicks), mass [n] float.  steps == 0 leaves the state unchanged.
+ */
+int nbody_leapfrog(int64_t n, double* pos, double* vel, const float* mass, double eps, double dt,
+                   int64_t steps, const nbody_opts* opts);
+
+/* The same with FP32 state (plain precision). */
+int nbody_leapfrog_f32(int64_t n, float* pos, float* vel, const float* mass, float eps, float dt,
+                       int64_t steps, const nbody_opts* opts);
+
+/*
+ * Diagnostics, reduced in FP64 on the device (synchronous; out is host memory):
+ *  out[0] T = sum m|v|^2/2, out[1] W = (1/2) sum m_i phi_i, out[2] E = T + W,
+ *  out[3..5] momentum sum m v, out[6..8] net force sum m a (zero by Newton's
+ *  third law up to rounding).  One force-and-potential evaluation.
+ */
+int nbody_energy(int64_t n, const double* pos, const double* vel, const float* mass, double eps,
+                 double* out, const nbody_opts* opts);
+int nbody_energy_f32(int64_t n, const float* pos, const float* vel, const float* mass, float eps,
+                     double* out, const nbody_opts* opts);
+
+/* Number of force-kernel shapes compiled in (for opts->config) and the
+ * bodies per i-block of shape k (0 if k is out of range). */
+int nbody_num_configs(void);
+int nbody_config_block(int k);
+
+/* Synchronise the current device and report whether any kernel since the
+ * last call hit a bounded-wait timeout (NBODY_ETIMEOUT) -- the flag is then
+ * cleared -- or a CUDA error (NBODY_ECUDA); NBODY_OK otherwise. */
+int nbody_last_device_error(void);
+
+/* The last CUDA runtime error code seen by the library on this thread. */
+int nbody_last_cuda_error(void);
+
+/* Static description of an NBODY_* code. */
+const char* nbody_strerror(int code);
+
+/* Self-test of the bounded device-side wait that every pipelined kernel
+ * uses: one CTA waits on a barrier phase that nothing completes, gives up
+ * after limit_seconds (1e-6 .. 1), records the timeout and returns.
+ * Synchronous; returns NBODY_ETIMEOUT when the timeout path works (the
+ * GPU stays usable), NBODY_EINVAL for a limit out of range. */
+int nbody_selftest_wait(double limit_seconds, const nbody_opts* opts);
+
+/* Benchmark instrumentation.  While enabled, every force-kernel launch is
+ * bracketed by a pair of CUDA events recorded on its own stream.
+ * nbody_profile_read waits for those events and returns the summed device
+ * time of the force kernels (ms) and their number since the previous read,
+ * plus the number of kernels of every kind the library queued; then resets. */
+void nbody_profile_enable(int on);
+int nbody_profile_read(double* force_ms, int64_t* force_launches, int64_t* all_launches);
+
+/* Free every cached workspace on every device (synchronises each device). */
+void nbody_finalize(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int nbody_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBODY_H */

@@ -1,0 +1,638 @@
+// capi.cu -- the C ABI declared in include/nbody.h: argument checks, the
+// per-(device, stream) workspace cache, staging of host arrays, kernel-shape
+// choice and the launch sequences of each call.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "nbody_internal.cuh"
+
+namespace {
+
+thread_local int t_last_cuda = 0;
+
+int cuda_fail(cudaError_t e) {
+    t_last_cuda = (int)e;
+    if (e == cudaErrorMemoryAllocation) return NBODY_ENOMEM;
+    return NBODY_ECUDA;
+}
+#define NB_CUDA(call)                               \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+#define NB_CHECK(expr)           \
+    do {                         \
+        int r_ = (expr);         \
+        if (r_ != NBODY_OK) return r_; \
+    } while (0)
+
+// Host-side fault injection for tests: NBODY_FAULT=alloc makes workspace
+// allocation report NBODY_ENOMEM, NBODY_FAULT=launch makes the launch report
+// NBODY_ECUDA.  Nothing is sent to the GPU in either case.
+bool fault(const char* what) {
+    const char* f = getenv("NBODY_FAULT");
+    return f != nullptr && strcmp(f, what) == 0;
+}
+
+// ---------------------------------------------------------------------------
+// Launch accounting and optional force-kernel timing (for benchmarks).
+// ---------------------------------------------------------------------------
+std::atomic<int64_t> g_launches{0};
+std::atomic<bool> g_prof_on{false};
+std::mutex g_prof_mu;
+struct ProfPair {
+    cudaEvent_t a, b;
+};
+std::vector<ProfPair> g_prof_used, g_prof_free;
+
+bool prof_pair(ProfPair* out) {
+    if (!g_prof_on.load()) return false;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfPair p;
+    if (!g_prof_free.empty()) {
+        p = g_prof_free.back();
+        g_prof_free.pop_back();
+    } else {
+        if (cudaEventCreate(&p.a) != cudaSuccess) return false;
+        if (cudaEventCreate(&p.b) != cudaSuccess) {
+            cudaEventDestroy(p.a);
+            return false;
+        }
+    }
+    g_prof_used.push_back(p);
+    *out = p;
+    return true;
+}
+
+// Queue `launches` kernels' worth of accounting after a successful launch.
+inline void count(int launches) { g_launches += launches; }
+
+struct DeviceInfo {
+    bool checked = false;
+    bool ok = false;
+    int num_sms = 0;
+};
+std::mutex g_dev_mu;
+std::map<int, DeviceInfo> g_dev;
+
+int device_check(int* dev_out, int* sms_out) {
+    int dev = 0;
+    NB_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DeviceInfo& d = g_dev[dev];
+    if (!d.checked) {
+        int major = 0, minor = 0, sms = 0;
+        NB_CUDA(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+        NB_CUDA(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+        NB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        d.ok = (major == 10 && minor == 3);  // the library carries sm_103a code only
+        d.num_sms = sms;
+        d.checked = true;
+    }
+    if (!d.ok) return NBODY_ENOTSUP;
+    *dev_out = dev;
+    *sms_out = d.num_sms;
+    return NBODY_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace: device buffers reused across calls on one (device, stream).
+// ---------------------------------------------------------------------------
+struct Buf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+enum BufId { B_JDUP, B_CENTRES, B_PARTIAL, B_ACC, B_POT, B_RED, B_OUT9, B_ERR, B_STAGE0, NBUF = B_STAGE0 + 8 };
+
+struct Workspace {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    Buf buf[NBUF];
+};
+
+std::mutex g_ws_mu;
+std::map<std::pair<int, cudaStream_t>, Workspace*> g_ws;
+
+Workspace* workspace(int dev, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    auto key = std::make_pair(dev, st);
+    auto it = g_ws.find(key);
+    if (it != g_ws.end()) return it->second;
+    Workspace* w = new Workspace();
+    w->device = dev;
+    w->stream = st;
+    g_ws[key] = w;
+    return w;
+}
+
+// Make buffer `id` hold at least `bytes`; growing waits for the stream's
+// queued work (which may still read the old buffer) before freeing it.
+int ensure(Workspace* w, int id, size_t bytes, void** out) {
+    if (fault("alloc")) return NBODY_ENOMEM;
+    Buf& b = w->buf[id];
+    if (bytes == 0) bytes = 16;
+    if (b.cap < bytes) {
+        if (b.p != nullptr) {
+            NB_CUDA(cudaStreamSynchronize(w->stream));
+            NB_CUDA(cudaFree(b.p));
+            b.p = nullptr;
+            b.cap = 0;
+        }
+        size_t sz = bytes + bytes / 8;
+        sz = (sz + 255) & ~(size_t)255;
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, sz);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            t_last_cuda = (int)e;
+            return NBODY_ENOMEM;
+        }
+        if (id == B_ERR) NB_CUDA(cudaMemset(p, 0, sz));
+        b.p = p;
+        b.cap = sz;
+    }
+    *out = b.p;
+    return NBODY_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Host arrays: detect, copy in, copy back.
+// ---------------------------------------------------------------------------
+bool is_host_ptr(const void* p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeUnregistered || a.type == cudaMemoryTypeHost;
+}
+
+struct Staging {
+    struct Item {
+        void* user;
+        size_t bytes;
+        bool in, out, host;
+        void* dev;
+    };
+    Workspace* ws;
+    std::vector<Item> items;
+    bool any_host = false;
+    explicit Staging(Workspace* w) : ws(w) {}
+    void add(const void* p, size_t bytes, bool in, bool out) {
+        items.push_back(Item{const_cast<void*>(p), bytes, in, out, false, const_cast<void*>(p)});
+    }
+    int prepare() {
+        for (auto& it : items)
+            if (it.user != nullptr) {
+                it.host = is_host_ptr(it.user);
+                any_host |= it.host;
+            }
+        if (!any_host) return NBODY_OK;
+        int k = 0;
+        for (auto& it : items) {
+            if (it.user == nullptr || !it.host) continue;
+            void* d = nullptr;
+            NB_CHECK(ensure(ws, B_STAGE0 + k++, it.bytes, &d));
+            it.dev = d;
+            if (it.in) NB_CUDA(cudaMemcpyAsync(d, it.user, it.bytes, cudaMemcpyHostToDevice, ws->stream));
+        }
+        return NBODY_OK;
+    }
+    int finish() {
+        if (!any_host) return NBODY_OK;
+        for (auto& it : items)
+            if (it.user != nullptr && it.host && it.out)
+                NB_CUDA(cudaMemcpyAsync(it.user, it.dev, it.bytes, cudaMemcpyDeviceToHost, ws->stream));
+        NB_CUDA(cudaStreamSynchronize(ws->stream));
+        return NBODY_OK;
+    }
+    void* dev(int i) const { return items[i].dev; }
+};
+
+// ---------------------------------------------------------------------------
+// Kernel-shape choice.
+// ---------------------------------------------------------------------------
+// Shape measured fastest on GB300 for each size class (plain/mixed alike):
+// with the potential the 2048-body blocks win, without it the 1024-body ones.
+int choose_shape(int64_t n, bool pot) {
+    const char* env = getenv("NBODY_SHAPE");
+    if (env != nullptr) {
+        int k = atoi(env);
+        if (k >= 0 && k < nbk::force_num_shapes()) return k;
+    }
+    if (n >= (1 << 14)) return pot ? 0 : 1;
+    if (n >= (1 << 11)) return 3;
+    return 4;
+}
+
+struct Opts {
+    cudaStream_t stream = nullptr;
+    int precision = NBODY_PREC_MIXED;
+    int accumulate = NBODY_ACC_COMPENSATED;
+    int config = -1;
+};
+
+int read_opts(const nbody_opts* o, Opts* r) {
+    if (o == nullptr) return NBODY_OK;
+    if (o->precision != NBODY_PREC_MIXED && o->precision != NBODY_PREC_PLAIN) return NBODY_EINVAL;
+    if (o->accumulate != NBODY_ACC_COMPENSATED && o->accumulate != NBODY_ACC_FP32) return NBODY_EINVAL;
+    if (o->config < -1 || o->config >= nbk::force_num_shapes()) return NBODY_EINVAL;
+    if (o->reserved != 0) return NBODY_EINVAL;
+    r->stream = (cudaStream_t)o->stream;
+    r->precision = o->precision;
+    r->accumulate = o->accumulate;
+    r->config = o->config;
+    return NBODY_OK;
+}
+
+bool finite_nonneg(double x) { return isfinite(x) && x >= 0.0; }
+
+// Everything one force evaluation needs, sized for n on this workspace.
+struct ForcePlan {
+    int shape;
+    int block;
+    int64_t npad;
+    float* jdup;
+    double* centres;
+    double* partial;
+    int* err;
+    int num_sms;
+};
+
+int plan_force(Workspace* ws, int64_t n, int shape, int num_sms, ForcePlan* fp) {
+    fp->shape = shape;
+    fp->block = nbk::force_shape(shape).block;
+    const int64_t nblk = (n + fp->block - 1) / fp->block;
+    fp->npad = nblk * fp->block;
+    fp->num_sms = num_sms;
+    void* p;
+    NB_CHECK(ensure(ws, B_JDUP, (size_t)fp->npad * nbk::kJdupFloats * sizeof(float), &p));
+    fp->jdup = (float*)p;
+    NB_CHECK(ensure(ws, B_CENTRES, (size_t)nblk * 3 * sizeof(double), &p));
+    fp->centres = (double*)p;
+    NB_CHECK(ensure(ws, B_PARTIAL, nbk::force_partial_doubles(shape, num_sms) * sizeof(double), &p));
+    fp->partial = (double*)p;
+    NB_CHECK(ensure(ws, B_ERR, sizeof(int), &p));
+    fp->err = (int*)p;
+    return NBODY_OK;
+}
+
+int run_force(const ForcePlan& fp, int64_t n, float eps2, bool mixed, bool compensated, float* acc, float* pot,
+              cudaStream_t st) {
+    if (fault("launch")) return NBODY_ECUDA;
+    nbk::ForceArgs a;
+    a.jdup = fp.jdup;
+    a.centres = mixed ? fp.centres : nullptr;
+    a.eps2 = eps2;
+    a.n = n;
+    a.npad = fp.npad;
+    a.acc = acc;
+    a.pot = pot;
+    a.partial = fp.partial;
+    a.err = fp.err;
+    a.compensated = compensated;
+    ProfPair pp;
+    const bool timed = prof_pair(&pp);
+    int launched = 0;
+    cudaError_t e = nbk::force_launch(fp.shape, a, fp.num_sms, st, &launched, timed ? pp.a : nullptr,
+                                      timed ? pp.b : nullptr);
+    count(launched);
+    NB_CUDA(e);
+    return NBODY_OK;
+}
+
+struct Ctx {
+    int dev, sms;
+    Opts o;
+    Workspace* ws;
+};
+
+int begin(const nbody_opts* opts, Ctx* c) {
+    NB_CHECK(read_opts(opts, &c->o));
+    NB_CHECK(device_check(&c->dev, &c->sms));
+    c->ws = workspace(c->dev, c->o.stream);
+    return NBODY_OK;
+}
+
+int shape_for(const Ctx& c, int64_t n, bool pot) { return c.o.config >= 0 ? c.o.config : choose_shape(n, pot); }
+
+int check_opts_only(const nbody_opts* opts) {
+    Opts o;
+    return read_opts(opts, &o);
+}
+
+// ---- force evaluation on device arrays ----
+int accel_f64_dev(Ctx& c, int64_t n, const double* pos, const float* mass, double eps, float* acc, float* pot) {
+    ForcePlan fp;
+    NB_CHECK(plan_force(c.ws, n, shape_for(c, n, pot != nullptr), c.sms, &fp));
+    const bool plain = c.o.precision == NBODY_PREC_PLAIN;
+    count(1);
+    NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, const_cast<double*>(pos), nullptr, nullptr, mass, 0.0, 0.0, plain,
+                          fp.jdup, fp.centres, c.o.stream));
+    return run_force(fp, n, (float)(eps * eps), !plain, c.o.accumulate == NBODY_ACC_COMPENSATED, acc, pot,
+                     c.o.stream);
+}
+
+int accel_f32_dev(Ctx& c, int64_t n, const float* pos, const float* mass, float eps, float* acc, float* pot) {
+    ForcePlan fp;
+    NB_CHECK(plan_force(c.ws, n, shape_for(c, n, pot != nullptr), c.sms, &fp));
+    count(1);
+    NB_CUDA(nbk::pack_f32(n, fp.npad, const_cast<float*>(pos), nullptr, nullptr, mass, 0.0f, 0.0f, fp.jdup,
+                          c.o.stream));
+    return run_force(fp, n, eps * eps, false, c.o.accumulate == NBODY_ACC_COMPENSATED, acc, pot, c.o.stream);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void nbody_opts_default(nbody_opts* o) {
+    if (o == nullptr) return;
+    o->stream = nullptr;
+    o->precision = NBODY_PREC_MIXED;
+    o->accumulate = NBODY_ACC_COMPENSATED;
+    o->config = -1;
+    o->reserved = 0;
+}
+
+int nbody_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+int nbody_num_configs(void) { return nbk::force_num_shapes(); }
+
+int nbody_config_block(int k) {
+    if (k < 0 || k >= nbk::force_num_shapes()) return 0;
+    return nbk::force_shape(k).block;
+}
+
+const char* nbody_strerror(int code) {
+    switch (code) {
+        case NBODY_OK: return "success";
+        case NBODY_EINVAL: return "invalid argument";
+        case NBODY_ENOMEM: return "out of memory";
+        case NBODY_ECUDA: return "CUDA runtime error";
+        case NBODY_ETIMEOUT: return "bounded device wait expired";
+        case NBODY_ENOTSUP: return "unsupported device or option";
+        default: return "unknown error code";
+    }
+}
+
+int nbody_last_cuda_error(void) { return t_last_cuda; }
+
+int nbody_accel(int64_t n, const double* pos, const float* mass, double eps, float* acc, float* pot,
+                const nbody_opts* opts) {
+    if (n < 0 || !finite_nonneg(eps)) return NBODY_EINVAL;
+    if (n > 0 && (pos == nullptr || mass == nullptr || acc == nullptr)) return NBODY_EINVAL;
+    NB_CHECK(check_opts_only(opts));
+    if (n == 0) return NBODY_OK;
+    Ctx c;
+    NB_CHECK(begin(opts, &c));
+    Staging sg(c.ws);
+    sg.add(pos, (size_t)n * 3 * sizeof(double), true, false);
+    sg.add(mass, (size_t)n * sizeof(float), true, false);
+    sg.add(acc, (size_t)n * 3 * sizeof(float), false, true);
+    sg.add(pot, (size_t)n * sizeof(float), false, true);
+    NB_CHECK(sg.prepare());
+    NB_CHECK(accel_f64_dev(c, n, (const double*)sg.dev(0), (const float*)sg.dev(1), eps, (float*)sg.dev(2),
+                           pot ? (float*)sg.dev(3) : nullptr));
+    return sg.finish();
+}
+
+int nbody_accel_f32(int64_t n, const float* pos, const float* mass, float eps, float* acc, float* pot,
+                    const nbody_opts* opts) {
+    if (n < 0 || !finite_nonneg((double)eps)) return NBODY_EINVAL;
+    if (n > 0 && (pos == nullptr || mass == nullptr || acc == nullptr)) return NBODY_EINVAL;
+    NB_CHECK(check_opts_only(opts));
+    if (n == 0) return NBODY_OK;
+    Ctx c;
+    NB_CHECK(begin(opts, &c));
+    Staging sg(c.ws);
+    sg.add(pos, (size_t)n * 3 * sizeof(float), true, false);
+    sg.add(mass, (size_t)n * sizeof(float), true, false);
+    sg.add(acc, (size_t)n * 3 * sizeof(float), false, true);
+    sg.add(pot, (size_t)n * sizeof(float), false, true);
+    NB_CHECK(sg.prepare());
+    NB_CHECK(accel_f32_dev(c, n, (const float*)sg.dev(0), (const float*)sg.dev(1), eps, (float*)sg.dev(2),
+                           pot ? (float*)sg.dev(3) : nullptr));
+    return sg.finish();
+}
+
+int nbody_leapfrog(int64_t n, double* pos, double* vel, const float* mass, double eps, double dt, int64_t steps,
+                   const nbody_opts* opts) {
+    if (n < 0 || steps < 0 || !finite_nonneg(eps) || !isfinite(dt)) return NBODY_EINVAL;
+    if (n > 0 && (pos == nullptr || vel == nullptr || mass == nullptr)) return NBODY_EINVAL;
+    NB_CHECK(check_opts_only(opts));
+    if (n == 0 || steps == 0) return NBODY_OK;
+    Ctx c;
+    NB_CHECK(begin(opts, &c));
+    Staging sg(c.ws);
+    sg.add(pos, (size_t)n * 3 * sizeof(double), true, true);
+    sg.add(vel, (size_t)n * 3 * sizeof(double), true, true);
+    sg.add(mass, (size_t)n * sizeof(float), true, false);
+    NB_CHECK(sg.prepare());
+    double* x = (double*)sg.dev(0);
+    double* v = (double*)sg.dev(1);
+    const float* m = (const float*)sg.dev(2);
+    ForcePlan fp;
+    NB_CHECK(plan_force(c.ws, n, shape_for(c, n, false), c.sms, &fp));
+    void* p;
+    NB_CHECK(ensure(c.ws, B_ACC, (size_t)n * 3 * sizeof(float), &p));
+    float* a = (float*)p;
+    const bool plain = c.o.precision == NBODY_PREC_PLAIN;
+    const bool comp = c.o.accumulate == NBODY_ACC_COMPENSATED;
+    const float eps2 = (float)(eps * eps);
+    cudaStream_t st = c.o.stream;
+    count(1);
+    NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, x, nullptr, nullptr, m, 0.0, 0.0, plain, fp.jdup, fp.centres, st));
+    NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, st));
+    for (int64_t s = 0; s < steps; ++s) {
+        const double kick = (s == 0) ? 0.5 * dt : dt;  // merged closing + opening half kicks
+        count(1);
+    NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, x, v, a, m, kick, dt, plain, fp.jdup, fp.centres, st));
+        NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, st));
+    }
+    count(1);
+    NB_CUDA(nbk::kick_f64(n, v, a, 0.5 * dt, st));
+    return sg.finish();
+}
+
+int nbody_leapfrog_f32(int64_t n, float* pos, float* vel, const float* mass, float eps, float dt, int64_t steps,
+                       const nbody_opts* opts) {
+    if (n < 0 || steps < 0 || !finite_nonneg((double)eps) || !isfinite(dt)) return NBODY_EINVAL;
+    if (n > 0 && (pos == nullptr || vel == nullptr || mass == nullptr)) return NBODY_EINVAL;
+    NB_CHECK(check_opts_only(opts));
+    if (n == 0 || steps == 0) return NBODY_OK;
+    Ctx c;
+    NB_CHECK(begin(opts, &c));
+    Staging sg(c.ws);
+    sg.add(pos, (size_t)n * 3 * sizeof(float), true, true);
+    sg.add(vel, (size_t)n * 3 * sizeof(float), true, true);
+    sg.add(mass, (size_t)n * sizeof(float), true, false);
+    NB_CHECK(sg.prepare());
+    float* x = (float*)sg.dev(0);
+    float* v = (float*)sg.dev(1);
+    const float* m = (const float*)sg.dev(2);
+    ForcePlan fp;
+    NB_CHECK(plan_force(c.ws, n, shape_for(c, n, false), c.sms, &fp));
+    void* p;
+    NB_CHECK(ensure(c.ws, B_ACC, (size_t)n * 3 * sizeof(float), &p));
+    float* a = (float*)p;
+    const bool comp = c.o.accumulate == NBODY_ACC_COMPENSATED;
+    cudaStream_t st = c.o.stream;
+    count(1);
+    NB_CUDA(nbk::pack_f32(n, fp.npad, x, nullptr, nullptr, m, 0.0f, 0.0f, fp.jdup, st));
+    NB_CHECK(run_force(fp, n, eps * eps, false, comp, a, nullptr, st));
+    for (int64_t s = 0; s < steps; ++s) {
+        const float kick = (s == 0) ? 0.5f * dt : dt;
+        count(1);
+    NB_CUDA(nbk::pack_f32(n, fp.npad, x, v, a, m, kick, dt, fp.jdup, st));
+        NB_CHECK(run_force(fp, n, eps * eps, false, comp, a, nullptr, st));
+    }
+    count(1);
+    NB_CUDA(nbk::kick_f32(n, v, a, 0.5f * dt, st));
+    return sg.finish();
+}
+
+static int energy_common(int64_t n, const void* pos, const void* vel, const float* mass, double eps, double* out,
+                         const nbody_opts* opts, bool f64) {
+    if (n < 0 || !finite_nonneg(eps) || out == nullptr) return NBODY_EINVAL;
+    if (n > 0 && (pos == nullptr || vel == nullptr || mass == nullptr)) return NBODY_EINVAL;
+    NB_CHECK(check_opts_only(opts));
+    if (n == 0) {
+        for (int k = 0; k < 9; ++k) out[k] = 0.0;
+        return NBODY_OK;
+    }
+    Ctx c;
+    NB_CHECK(begin(opts, &c));
+    const size_t vb = f64 ? sizeof(double) : sizeof(float);
+    Staging sg(c.ws);
+    sg.add(pos, (size_t)n * 3 * vb, true, false);
+    sg.add(vel, (size_t)n * 3 * vb, true, false);
+    sg.add(mass, (size_t)n * sizeof(float), true, false);
+    NB_CHECK(sg.prepare());
+    void *pa, *pp, *pr, *po;
+    NB_CHECK(ensure(c.ws, B_ACC, (size_t)n * 3 * sizeof(float), &pa));
+    NB_CHECK(ensure(c.ws, B_POT, (size_t)n * sizeof(float), &pp));
+    NB_CHECK(ensure(c.ws, B_RED, nbk::reduce_scratch_doubles() * sizeof(double), &pr));
+    NB_CHECK(ensure(c.ws, B_OUT9, 9 * sizeof(double), &po));
+    if (f64) {
+        NB_CHECK(accel_f64_dev(c, n, (const double*)sg.dev(0), (const float*)sg.dev(2), eps, (float*)pa, (float*)pp));
+        count(2);
+        NB_CUDA(nbk::energy_reduce_f64(n, (const double*)sg.dev(1), (const float*)sg.dev(2), (const float*)pa,
+                                       (const float*)pp, (double*)pr, (double*)po, c.o.stream));
+    } else {
+        NB_CHECK(accel_f32_dev(c, n, (const float*)sg.dev(0), (const float*)sg.dev(2), (float)eps, (float*)pa,
+                               (float*)pp));
+        count(2);
+        NB_CUDA(nbk::energy_reduce_f32(n, (const float*)sg.dev(1), (const float*)sg.dev(2), (const float*)pa,
+                                       (const float*)pp, (double*)pr, (double*)po, c.o.stream));
+    }
+    NB_CUDA(cudaMemcpyAsync(out, po, 9 * sizeof(double), cudaMemcpyDeviceToHost, c.o.stream));
+    NB_CUDA(cudaStreamSynchronize(c.o.stream));
+    return sg.finish();
+}
+
+int nbody_energy(int64_t n, const double* pos, const double* vel, const float* mass, double eps, double* out,
+                 const nbody_opts* opts) {
+    return energy_common(n, pos, vel, mass, eps, out, opts, true);
+}
+
+int nbody_energy_f32(int64_t n, const float* pos, const float* vel, const float* mass, float eps, double* out,
+                     const nbody_opts* opts) {
+    return energy_common(n, pos, vel, mass, (double)eps, out, opts, false);
+}
+
+int nbody_last_device_error(void) {
+    int dev = 0;
+    NB_CUDA(cudaGetDevice(&dev));
+    NB_CUDA(cudaDeviceSynchronize());
+    int result = NBODY_OK;
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    for (auto& kv : g_ws) {
+        Workspace* w = kv.second;
+        if (w->device != dev || w->buf[B_ERR].p == nullptr) continue;
+        int flag = 0;
+        NB_CUDA(cudaMemcpy(&flag, w->buf[B_ERR].p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag != 0) {
+            result = NBODY_ETIMEOUT;
+            NB_CUDA(cudaMemset(w->buf[B_ERR].p, 0, sizeof(int)));
+        }
+    }
+    return result;
+}
+
+int nbody_selftest_wait(double limit_seconds, const nbody_opts* opts) {
+    if (!(limit_seconds >= 1e-6 && limit_seconds <= 1.0)) return NBODY_EINVAL;
+    NB_CHECK(check_opts_only(opts));
+    Ctx c;
+    NB_CHECK(begin(opts, &c));
+    void* p;
+    NB_CHECK(ensure(c.ws, B_ERR, sizeof(int), &p));
+    count(1);
+    NB_CUDA(nbk::selftest_wait((uint64_t)(limit_seconds * 1e9), (int*)p, c.o.stream));
+    NB_CUDA(cudaStreamSynchronize(c.o.stream));
+    int flag = 0;
+    NB_CUDA(cudaMemcpy(&flag, p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag != 0) {
+        NB_CUDA(cudaMemset(p, 0, sizeof(int)));
+        return NBODY_ETIMEOUT;
+    }
+    return NBODY_OK;
+}
+
+void nbody_profile_enable(int on) { g_prof_on.store(on != 0); }
+
+int nbody_profile_read(double* force_ms, int64_t* force_launches, int64_t* all_launches) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    double ms = 0.0;
+    int64_t k = 0;
+    for (auto& p : g_prof_used) {
+        NB_CUDA(cudaEventSynchronize(p.b));
+        float t = 0.0f;
+        NB_CUDA(cudaEventElapsedTime(&t, p.a, p.b));
+        ms += t;
+        ++k;
+        g_prof_free.push_back(p);
+    }
+    g_prof_used.clear();
+    if (force_ms) *force_ms = ms;
+    if (force_launches) *force_launches = k;
+    if (all_launches) *all_launches = g_launches.exchange(0);
+    return NBODY_OK;
+}
+
+void nbody_finalize(void) {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        (void)cudaGetLastError();
+        cur = 0;
+    }
+    for (auto& kv : g_ws) {
+        Workspace* w = kv.second;
+        if (cudaSetDevice(w->device) == cudaSuccess) {
+            (void)cudaDeviceSynchronize();
+            for (int k = 0; k < NBUF; ++k)
+                if (w->buf[k].p) (void)cudaFree(w->buf[k].p);
+        }
+        delete w;
+    }
+    g_ws.clear();
+    (void)cudaSetDevice(cur);
+    (void)cudaGetLastError();
+}
+
+}  // extern "C"

@@ -1,0 +1,418 @@
+// force.cu -- the all-pairs softened force and potential (Eq. 1 of Miki &
+// Hanawa, Sec. III.A, with the per-pair arithmetic of their Listing 4).
+//
+// Decomposition.  Bodies are grouped in i-blocks ("cells") of
+// block = 2 * IP * T bodies; the j-range is cut into tiles of J bodies.  The
+// work is the grid of units (i-block, j-tile), flattened i-block-major, and a
+// persistent grid of P CTAs takes equal contiguous slices of it ("stream-K"):
+// CTA c owns units [c*U/P, (c+1)*U/P).  Every SM therefore gets the same
+// number of pair interactions whatever n is, with no tail wave.  A CTA that
+// covers a whole i-block writes the result; the i-blocks cut by a slice
+// boundary get per-CTA partial sums that a small fixup kernel adds in CTA
+// order (deterministic, no atomics).
+//
+// Inside a CTA.  Each thread holds IP packed pairs of i-bodies in registers:
+// pair q holds bodies 2q*T + t and (2q+1)*T + t of the i-block.  j-tiles
+// stream global -> shared through a two-stage ring of 1-D bulk copies (TMA)
+// completing on mbarriers; the single issuing thread refills a stage after the
+// CTA barrier that ends its use.  Each j-body is one broadcast 32-byte shared
+// load of (x,x,y,y,z,z,m,m), then per i-pair 13 packed f32x2 instructions and
+// two MUFU reciprocal square roots: the same operation sequence Listing 4
+// performs per pair (difference, FMA chain seeded with eps^2, rsqrt cubed,
+// times m_j, FMA accumulation, and r2*w for the potential).
+//
+// Accumulation.  Per tile the sums are plain FP32; with compensation on, each
+// tile's partial is folded into a running sum by Kahan summation (four packed
+// adds per component per tile, amortised over J pairs), so the per-body sum
+// over n terms keeps FP32 pair errors instead of an O(sqrt(n)) FP32 running-sum
+// error.
+//
+// Self term.  The diagonal tiles (j-tile inside the thread's own i-block) run
+// a masked variant that zeroes the pair whose j equals i, so j = i is excluded
+// exactly (Eq. 1) and eps = 0 is valid for distinct positions.
+#include <algorithm>
+#include <mutex>
+
+#include "nbody_internal.cuh"
+
+namespace nbk {
+namespace {
+
+struct KParams {
+    const float* jdup;
+    const double* centres;
+    float eps2;
+    int64_t n;
+    int64_t nblk;
+    int64_t ntile;  // j-tiles over the padded array
+    int64_t units;  // nblk * ntile
+    int64_t nctas;
+    float* acc;
+    float* pot;
+    double* partial;  // [nctas][2][block][4]
+    int* err;
+};
+
+// One j-tile against the thread's IP i-pairs.
+template <int T, int IP, int J, bool POT, bool DIAG>
+__device__ __forceinline__ void tile_pass(const unsigned char* tile, const f2 (&xi)[IP], const f2 (&yi)[IP],
+                                          const f2 (&zi)[IP], f2 eps2, f2 (&ax)[IP], f2 (&ay)[IP], f2 (&az)[IP],
+                                          f2 (&ap)[IP], int jl0, int tid) {
+    const ulonglong2* tj = reinterpret_cast<const ulonglong2*>(tile);
+#pragma unroll 2
+    for (int j = 0; j < J; ++j) {
+        const ulonglong2 A = tj[2 * j];
+        const ulonglong2 B = tj[2 * j + 1];
+        const f2 xj = A.x, yj = A.y, zj = B.x, mj = B.y;
+#pragma unroll
+        for (int q = 0; q < IP; ++q) {
+            const f2 dx = sub2(xj, xi[q]);
+            const f2 dy = sub2(yj, yi[q]);
+            const f2 dz = sub2(zj, zi[q]);
+            f2 r2 = fma2(dx, dx, eps2);
+            r2 = fma2(dy, dy, r2);
+            r2 = fma2(dz, dz, r2);
+            float s0, s1;
+            upk(r2, s0, s1);
+            float q0 = rsqrt_approx(s0);
+            float q1 = rsqrt_approx(s1);
+            if (DIAG) {
+                const int jl = jl0 + j;
+                if (jl == 2 * q * T + tid) q0 = 0.0f;
+                if (jl == (2 * q + 1) * T + tid) q1 = 0.0f;
+            }
+            const f2 ri = pk(q0, q1);
+            f2 w = mul2(ri, mul2(ri, ri));  // rsqrt cubed
+            w = mul2(w, mj);                // times m_j
+            ax[q] = fma2(dx, w, ax[q]);
+            ay[q] = fma2(dy, w, ay[q]);
+            az[q] = fma2(dz, w, az[q]);
+            if (POT) ap[q] = fma2(r2, w, ap[q]);  // r2 * m_j / r^3 = m_j / r
+        }
+    }
+}
+
+__device__ __forceinline__ void kahan2(f2& sum, f2& comp, f2& part) {
+    const f2 y = sub2(part, comp);
+    const f2 t = add2(sum, y);
+    comp = sub2(sub2(t, sum), y);
+    sum = t;
+    part = 0ull;
+}
+
+template <int T, int IP, int J, bool POT, bool MIXED, bool KAHAN>
+__global__ void __launch_bounds__(T) force_kernel(const KParams p) {
+    constexpr int C = 2 * IP * T;
+    constexpr uint32_t TILE_BYTES = J * 32u;
+    static_assert(C % J == 0, "a j-tile must not straddle two cells");
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+
+    const int tid = threadIdx.x;
+    const int64_t cta = blockIdx.x;
+    const int64_t u_begin = cta * p.units / p.nctas;
+    const int64_t u_end = (cta + 1) * p.units / p.nctas;
+    unsigned char* tiles = smem;
+    f2* xsave = reinterpret_cast<f2*>(smem + 2 * TILE_BYTES);  // MIXED: [IP][3][T]
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int s, int64_t unit) {
+        const int64_t tile = unit % p.ntile;
+        mbar_expect_tx(&bar[s], TILE_BYTES);
+        bulk_g2s(tiles + s * TILE_BYTES, p.jdup + tile * (int64_t)J * kJdupFloats, TILE_BYTES, &bar[s]);
+    };
+    if (tid == 0) {
+        if (u_begin < u_end) issue(0, u_begin);
+        if (u_begin + 1 < u_end) issue(1, u_begin + 1);
+    }
+
+    const f2 eps2 = pk(p.eps2, p.eps2);
+    uint32_t parity = 0;
+    int s = 0;
+    int64_t u = u_begin;
+    bool failed = false;
+
+    while (u < u_end) {
+        const int64_t b = u / p.ntile;
+        const int64_t t0 = u - b * p.ntile;
+        const int64_t t1 = min(p.ntile, t0 + (u_end - u));
+        const int64_t base = b * C;
+
+        f2 xi[IP], yi[IP], zi[IP];
+#pragma unroll
+        for (int q = 0; q < IP; ++q) {
+            const float* a0 = p.jdup + (base + (2 * q) * T + tid) * kJdupFloats;
+            const float* a1 = p.jdup + (base + (2 * q + 1) * T + tid) * kJdupFloats;
+            xi[q] = pk(a0[0], a1[0]);
+            yi[q] = pk(a0[2], a1[2]);
+            zi[q] = pk(a0[4], a1[4]);
+            if (MIXED) {
+                xsave[(q * 3 + 0) * T + tid] = xi[q];
+                xsave[(q * 3 + 1) * T + tid] = yi[q];
+                xsave[(q * 3 + 2) * T + tid] = zi[q];
+            }
+        }
+        f2 ax[IP], ay[IP], az[IP], ap[IP];
+        f2 sx[IP], sy[IP], sz[IP], sp[IP], cx[IP], cy[IP], cz[IP], cp[IP];
+#pragma unroll
+        for (int q = 0; q < IP; ++q) {
+            ax[q] = ay[q] = az[q] = ap[q] = 0ull;
+            sx[q] = sy[q] = sz[q] = sp[q] = 0ull;
+            cx[q] = cy[q] = cz[q] = cp[q] = 0ull;
+        }
+        int64_t cur_cell = b;
+
+        for (int64_t tt = t0; tt < t1; ++tt, ++u) {
+            const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u, kWaitLimitNs);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            parity ^= (1u << s);
+            const int64_t cell = (tt * J) / C;
+            if (MIXED && cell != cur_cell) {
+                // i-coordinates relative to the j-cell's centre: x_i - c_J =
+                // (x_i - c_I) - (c_J - c_I), the centre difference in FP64.
+                cur_cell = cell;
+                const double* cj = p.centres + 3 * cell;
+                const double* ci = p.centres + 3 * b;
+                const float dx = (float)(cj[0] - ci[0]);
+                const float dy = (float)(cj[1] - ci[1]);
+                const float dz = (float)(cj[2] - ci[2]);
+                const f2 dx2 = pk(dx, dx), dy2 = pk(dy, dy), dz2 = pk(dz, dz);
+#pragma unroll
+                for (int q = 0; q < IP; ++q) {
+                    xi[q] = sub2(xsave[(q * 3 + 0) * T + tid], dx2);
+                    yi[q] = sub2(xsave[(q * 3 + 1) * T + tid], dy2);
+                    zi[q] = sub2(xsave[(q * 3 + 2) * T + tid], dz2);
+                }
+            }
+            const unsigned char* tile = tiles + s * TILE_BYTES;
+            if (cell == b) {
+                tile_pass<T, IP, J, POT, true>(tile, xi, yi, zi, eps2, ax, ay, az, ap,
+                                               (int)(tt * J - base), tid);
+            } else {
+                tile_pass<T, IP, J, POT, false>(tile, xi, yi, zi, eps2, ax, ay, az, ap, 0, tid);
+            }
+            if (KAHAN) {
+#pragma unroll
+                for (int q = 0; q < IP; ++q) {
+                    kahan2(sx[q], cx[q], ax[q]);
+                    kahan2(sy[q], cy[q], ay[q]);
+                    kahan2(sz[q], cz[q], az[q]);
+                    if (POT) kahan2(sp[q], cp[q], ap[q]);
+                }
+            }
+            __syncthreads();  // every thread is done with stage s
+            if (tid == 0 && u + 2 < u_end) issue(s, u + 2);
+            s ^= 1;
+        }
+        if (failed) break;
+
+        // ---- results of i-block b from this CTA's slice ----
+        const bool full = (t0 == 0 && t1 == p.ntile);
+        const int slot = (b == u_begin / p.ntile) ? 0 : 1;
+#pragma unroll
+        for (int q = 0; q < IP; ++q) {
+            float v[2][4];
+            double d[2][4];
+            if (KAHAN) {
+                float s0, s1, c0, c1;
+                upk(sx[q], s0, s1); upk(cx[q], c0, c1);
+                d[0][0] = (double)s0 - (double)c0; d[1][0] = (double)s1 - (double)c1;
+                upk(sy[q], s0, s1); upk(cy[q], c0, c1);
+                d[0][1] = (double)s0 - (double)c0; d[1][1] = (double)s1 - (double)c1;
+                upk(sz[q], s0, s1); upk(cz[q], c0, c1);
+                d[0][2] = (double)s0 - (double)c0; d[1][2] = (double)s1 - (double)c1;
+                upk(sp[q], s0, s1); upk(cp[q], c0, c1);
+                d[0][3] = (double)s0 - (double)c0; d[1][3] = (double)s1 - (double)c1;
+            } else {
+                float a0, a1;
+                upk(ax[q], a0, a1); d[0][0] = a0; d[1][0] = a1;
+                upk(ay[q], a0, a1); d[0][1] = a0; d[1][1] = a1;
+                upk(az[q], a0, a1); d[0][2] = a0; d[1][2] = a1;
+                upk(ap[q], a0, a1); d[0][3] = a0; d[1][3] = a1;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int lb = (2 * q + h) * T + tid;
+                const int64_t g = base + lb;
+                if (full) {
+                    if (g < p.n) {
+                        for (int k = 0; k < 4; ++k) v[h][k] = (float)d[h][k];
+                        p.acc[3 * g + 0] = v[h][0];
+                        p.acc[3 * g + 1] = v[h][1];
+                        p.acc[3 * g + 2] = v[h][2];
+                        if (POT) p.pot[g] = -v[h][3];
+                    }
+                } else {
+                    double4* dst = reinterpret_cast<double4*>(p.partial) + ((cta * 2 + slot) * C + lb);
+                    *dst = make_double4(d[h][0], d[h][1], d[h][2], d[h][3]);
+                }
+            }
+        }
+    }
+
+    if (failed) {
+        if (tid == 0) {
+            atomicExch(p.err, kErrTimeout);
+            // Let copies still in flight land before shared memory goes away.
+            const int64_t inflight = (u_end - u) < 2 ? (u_end - u) : 2;
+            for (int k = 0; k < inflight; ++k) {
+                const int st = (s + k) & 1;
+                (void)mbar_wait_bounded(&bar[st], (parity >> st) & 1u, kWaitLimitNs / 4);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Adds the per-CTA partial sums of every i-block that a slice boundary cut,
+// in CTA order.  One CTA per i-block; blocks covered by one CTA return at once.
+__global__ void fixup_kernel(const KParams p, int C, int pot_on) {
+    const int64_t b = blockIdx.x;
+    const int64_t u0 = b * p.ntile, u1 = u0 + p.ntile - 1;
+    const int64_t c_lo = ((u0 + 1) * p.nctas - 1) / p.units;
+    const int64_t c_hi = ((u1 + 1) * p.nctas - 1) / p.units;
+    if (c_lo == c_hi) return;
+    for (int lb = threadIdx.x; lb < C; lb += blockDim.x) {
+        const int64_t g = b * C + lb;
+        if (g >= p.n) break;
+        double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0;
+        for (int64_t c = c_lo; c <= c_hi; ++c) {
+            const int64_t ub = c * p.units / p.nctas;
+            const int slot = (ub / p.ntile == b) ? 0 : 1;
+            const double4 v = reinterpret_cast<const double4*>(p.partial)[(c * 2 + slot) * C + lb];
+            sx += v.x;
+            sy += v.y;
+            sz += v.z;
+            sp += v.w;
+        }
+        p.acc[3 * g + 0] = (float)sx;
+        p.acc[3 * g + 1] = (float)sy;
+        p.acc[3 * g + 2] = (float)sz;
+        if (pot_on) p.pot[g] = -(float)sp;
+    }
+}
+
+typedef void (*KernelFn)(const KParams);
+
+struct ShapeEntry {
+    ForceShape shape;
+    KernelFn fn[2][2][2];  // [pot][mixed][kahan]
+    size_t smem(bool mixed) const {
+        return 2u * shape.jtile * 32u + (mixed ? (size_t)shape.ipairs * 3 * shape.threads * 8 : 0);
+    }
+};
+
+template <int T, int IP, int J>
+ShapeEntry make_entry() {
+    ShapeEntry e;
+    e.shape = ForceShape{T, IP, J, 2 * IP * T};
+    e.fn[0][0][0] = force_kernel<T, IP, J, false, false, false>;
+    e.fn[0][0][1] = force_kernel<T, IP, J, false, false, true>;
+    e.fn[0][1][0] = force_kernel<T, IP, J, false, true, false>;
+    e.fn[0][1][1] = force_kernel<T, IP, J, false, true, true>;
+    e.fn[1][0][0] = force_kernel<T, IP, J, true, false, false>;
+    e.fn[1][0][1] = force_kernel<T, IP, J, true, false, true>;
+    e.fn[1][1][0] = force_kernel<T, IP, J, true, true, false>;
+    e.fn[1][1][1] = force_kernel<T, IP, J, true, true, true>;
+    return e;
+}
+
+const ShapeEntry* shapes() {
+    static const ShapeEntry table[] = {
+        make_entry<256, 4, 256>(),  // 0: 2048-body blocks
+        make_entry<256, 2, 256>(),  // 1: 1024
+        make_entry<128, 4, 256>(),  // 2: 1024
+        make_entry<128, 2, 128>(),  // 3: 512
+        make_entry<128, 1, 64>(),   // 4: 256 (small n)
+    };
+    return table;
+}
+constexpr int kNumShapes = 5;
+
+// Resident CTAs per SM for each kernel variant, queried once.
+std::mutex g_occ_mu;
+int g_occ[kNumShapes][2][2][2];
+bool g_occ_init = false;
+
+int occupancy(int k, int pot, int mixed, int kahan) {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    if (!g_occ_init) {
+        for (int a = 0; a < kNumShapes; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int c = 0; c < 2; ++c)
+                    for (int d = 0; d < 2; ++d) g_occ[a][b][c][d] = -1;
+        g_occ_init = true;
+    }
+    int& o = g_occ[k][pot][mixed][kahan];
+    if (o < 0) {
+        const ShapeEntry& e = shapes()[k];
+        const size_t sm = e.smem(mixed);
+        cudaFuncSetAttribute(e.fn[pot][mixed][kahan], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, e.fn[pot][mixed][kahan], e.shape.threads, sm) !=
+                cudaSuccess ||
+            nb < 1)
+            nb = 1;
+        o = nb;
+    }
+    return o;
+}
+
+}  // namespace
+
+int force_num_shapes() { return kNumShapes; }
+ForceShape force_shape(int k) { return shapes()[k].shape; }
+
+size_t force_partial_doubles(int k, int num_sms) {
+    // Upper bound over variants: at most 4 resident CTAs of any shape fit the
+    // register file at the shapes compiled here; 8 leaves margin.
+    const ForceShape s = shapes()[k].shape;
+    return (size_t)num_sms * 8u * 2u * (size_t)s.block * 4u;
+}
+
+cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st, int* launched, cudaEvent_t ev0,
+                         cudaEvent_t ev1) {
+    const ShapeEntry& e = shapes()[k];
+    const int C = e.shape.block;
+    const int pot = a.pot != nullptr, mixed = a.centres != nullptr, kahan = a.compensated ? 1 : 0;
+    KParams p;
+    p.jdup = a.jdup;
+    p.centres = a.centres;
+    p.eps2 = a.eps2;
+    p.n = a.n;
+    p.nblk = a.npad / C;
+    p.ntile = a.npad / e.shape.jtile;
+    p.units = p.nblk * p.ntile;
+    int occ = occupancy(k, pot, mixed, kahan);
+    occ = std::min(occ, 8);
+    p.nctas = std::min<int64_t>((int64_t)num_sms * occ, p.units);
+    p.acc = a.acc;
+    p.pot = a.pot;
+    p.partial = a.partial;
+    p.err = a.err;
+    const size_t sm = e.smem(mixed);
+    *launched = 0;
+    if (ev0 != nullptr) cudaEventRecord(ev0, st);
+    e.fn[pot][mixed][kahan]<<<(unsigned)p.nctas, e.shape.threads, sm, st>>>(p);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    *launched = 1;
+    if (ev1 != nullptr) cudaEventRecord(ev1, st);
+    if (p.nctas > 1) {  // a single CTA covers every i-block whole
+        fixup_kernel<<<(unsigned)p.nblk, 256, 0, st>>>(p, C, pot);
+        err = cudaGetLastError();
+        if (err == cudaSuccess) *launched = 2;
+    }
+    return err;
+}
+
+}  // namespace nbk

@@ -1,0 +1,210 @@
+// nbody_internal.cuh -- device helpers and launch interfaces shared by the
+// library's translation units (not installed, not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nbody.h"
+
+namespace nbk {
+
+// ---------------------------------------------------------------------------
+// Layout of the packed j-array ("jdup"), written by the pack kernels and read
+// by the force kernel through shared memory:
+//   jdup[k] = (x, x, y, y, z, z, m, m)  (8 floats = 32 bytes per body)
+// Each coordinate appears twice so that one 64-bit shared load yields the
+// broadcast operand of a packed f32x2 instruction acting on two i-bodies.
+// Coordinates are relative to the FP64 centre of the body's cell (mixed
+// precision) or absolute (plain).  Padding bodies beyond n sit at kPadPos with
+// zero mass: their contribution underflows to exactly zero.
+// ---------------------------------------------------------------------------
+constexpr float kPadPos = 1.0e15f;
+constexpr int kJdupFloats = 8;
+
+// ---------------------------------------------------------------------------
+// Packed FP32 pairs (PTX f32x2 arithmetic, sm_100 and later).  A pair is a
+// 64-bit register holding (lo, hi); every op is round-to-nearest with
+// flush-to-zero, the fast-math setting the paper's N-body runs use.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+#ifndef NBODY_SCALAR_PAIRS
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 r;
+    asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+#else
+// The same operations as two scalar instructions each (for comparison runs).
+#define NBK_SCALAR2(name, op)                                                  \
+    __device__ __forceinline__ f2 name(f2 a, f2 b) {                           \
+        float a0, a1, b0, b1, r0, r1;                                          \
+        upk(a, a0, a1);                                                        \
+        upk(b, b0, b1);                                                        \
+        asm(op ".rn.ftz.f32 %0, %1, %2;" : "=f"(r0) : "f"(a0), "f"(b0));       \
+        asm(op ".rn.ftz.f32 %0, %1, %2;" : "=f"(r1) : "f"(a1), "f"(b1));       \
+        return pk(r0, r1);                                                     \
+    }
+NBK_SCALAR2(add2, "add")
+NBK_SCALAR2(sub2, "sub")
+NBK_SCALAR2(mul2, "mul")
+#undef NBK_SCALAR2
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    float a0, a1, b0, b1, c0, c1, r0, r1;
+    upk(a, a0, a1);
+    upk(b, b0, b1);
+    upk(c, c0, c1);
+    asm("fma.rn.ftz.f32 %0, %1, %2, %3;" : "=f"(r0) : "f"(a0), "f"(b0), "f"(c0));
+    asm("fma.rn.ftz.f32 %0, %1, %2, %3;" : "=f"(r1) : "f"(a1), "f"(b1), "f"(c1));
+    return pk(r0, r1);
+}
+#endif
+
+// Hardware approximate reciprocal square root (MUFU), flush-to-zero.
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier + 1-D bulk copy (TMA) helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Global copy of `bytes` (multiple of 16, both addresses 16-byte aligned) into
+// shared memory, completing on `bar` by transaction count.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Every device-side wait gives up after this long, sets the error word and
+// lets the kernel return (no trap, no endless spin).
+constexpr uint64_t kWaitLimitNs = 4000000000ull;
+constexpr int kErrTimeout = 1;
+
+// Wait for phase `parity` of `bar`; false if the limit expired.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 0 && globaltimer_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launch interfaces (implemented in force.cu / pack.cu / reduce.cu).
+// ---------------------------------------------------------------------------
+struct ForceShape {
+    int threads;    // threads per CTA
+    int ipairs;     // packed i-pairs per thread (2*ipairs bodies)
+    int jtile;      // j-bodies per shared-memory stage
+    int block;      // bodies per i-block = cell = 2*ipairs*threads
+};
+
+int force_num_shapes();
+ForceShape force_shape(int k);
+
+struct ForceArgs {
+    const float* jdup;      // [npad][8]
+    const double* centres;  // [nblk][3] cell centres (mixed) or nullptr (plain)
+    float eps2;
+    int64_t n;
+    int64_t npad;           // nblk * block
+    float* acc;             // [n][3]
+    float* pot;             // [n] or nullptr
+    double* partial;        // scratch, force_partial_doubles(...) doubles
+    int* err;               // device error word
+    bool compensated;
+};
+
+// Scratch doubles needed for the split i-block partial sums of shape k.
+size_t force_partial_doubles(int k, int num_sms);
+// Launch the force kernel (stream-K over i-block x j-tile units) and the fixup
+// that combines split i-blocks; *launched gets the number of kernels queued.
+// ev0/ev1 (optional) are recorded on `st` just before and after the force
+// kernel itself.  Returns a cudaError_t.
+cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st, int* launched,
+                         cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
+
+// Pack kernels: build jdup (and cell centres) from the state, optionally
+// applying a kick (vel += kick * acc) and a drift (pos += drift * vel) first.
+// All FP64 state arithmetic for the mixed path happens here.
+cudaError_t pack_f64(int64_t n, int64_t npad, int block, double* pos, double* vel, const float* acc,
+                     const float* mass, double kick, double drift, bool plain, float* jdup,
+                     double* centres, cudaStream_t st);
+cudaError_t pack_f32(int64_t n, int64_t npad, float* pos, float* vel, const float* acc,
+                     const float* mass, float kick, float drift, float* jdup, cudaStream_t st);
+// vel += kick * acc (the closing half kick of a leapfrog call).
+cudaError_t kick_f64(int64_t n, double* vel, const float* acc, double kick, cudaStream_t st);
+cudaError_t kick_f32(int64_t n, float* vel, const float* acc, float kick, cudaStream_t st);
+
+// FP64 diagnostics reduction: out9 (device, 9 doubles) = T, W, E, P[3], F[3].
+// `scratch` holds reduce_scratch_doubles() doubles.
+size_t reduce_scratch_doubles();
+cudaError_t energy_reduce_f64(int64_t n, const double* vel, const float* mass, const float* acc,
+                              const float* pot, double* scratch, double* out9, cudaStream_t st);
+cudaError_t energy_reduce_f32(int64_t n, const float* vel, const float* mass, const float* acc,
+                              const float* pot, double* scratch, double* out9, cudaStream_t st);
+
+// One CTA waits on an mbarrier nothing completes, for limit_ns, then sets *err.
+cudaError_t selftest_wait(uint64_t limit_ns, int* err, cudaStream_t st);
+
+}  // namespace nbk

@@ -1,0 +1,176 @@
+// pack.cu -- O(n) kernels around the force evaluation: the leapfrog's kick
+// and drift (the integrator is not in the paper; the force it drives is
+// Eq. 1 of Miki & Hanawa, Sec. III.A) fused with the build of the packed
+// j-array the force kernel streams.
+//
+// Mixed precision: positions and velocities stay FP64; each cell of `block`
+// bodies gets an FP64 centre (the mean of its bodies' positions) and the
+// packed array holds FP32 offsets from that centre, so the FP32 pair math
+// never sees a large absolute coordinate.  Plain precision: FP32 absolute
+// coordinates.
+#include "nbody_internal.cuh"
+
+namespace nbk {
+namespace {
+
+__device__ __forceinline__ void store_jdup(float* jdup, int64_t k, float x, float y, float z, float m) {
+    float4* d = reinterpret_cast<float4*>(jdup + k * kJdupFloats);
+    d[0] = make_float4(x, x, y, y);
+    d[1] = make_float4(z, z, m, m);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One CTA per cell.  Kick (vel += kick*acc), drift (pos += drift*vel), cell
+// centre, packed offsets.  kick/drift == 0 or vel/acc == nullptr skip them.
+__global__ void __launch_bounds__(256) pack_f64_kernel(int64_t n, int block, double* __restrict__ pos,
+                                                       double* __restrict__ vel, const float* __restrict__ acc,
+                                                       const float* __restrict__ mass, double kick, double drift,
+                                                       int plain, float* __restrict__ jdup,
+                                                       double* __restrict__ centres) {
+    __shared__ double red[3][8];
+    __shared__ double cen[3];
+    const int64_t base = (int64_t)blockIdx.x * block;
+    const int tid = threadIdx.x;
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int lb = tid; lb < block; lb += blockDim.x) {
+        const int64_t g = base + lb;
+        if (g >= n) break;
+        double x = pos[3 * g + 0], y = pos[3 * g + 1], z = pos[3 * g + 2];
+        if (vel != nullptr && (kick != 0.0 || drift != 0.0)) {
+            double vx = vel[3 * g + 0], vy = vel[3 * g + 1], vz = vel[3 * g + 2];
+            if (acc != nullptr && kick != 0.0) {
+                vx += kick * (double)acc[3 * g + 0];
+                vy += kick * (double)acc[3 * g + 1];
+                vz += kick * (double)acc[3 * g + 2];
+                vel[3 * g + 0] = vx;
+                vel[3 * g + 1] = vy;
+                vel[3 * g + 2] = vz;
+            }
+            if (drift != 0.0) {
+                x += drift * vx;
+                y += drift * vy;
+                z += drift * vz;
+                pos[3 * g + 0] = x;
+                pos[3 * g + 1] = y;
+                pos[3 * g + 2] = z;
+            }
+        }
+        sx += x;
+        sy += y;
+        sz += z;
+    }
+    if (!plain) {
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        sz = warp_sum(sz);
+        const int w = tid >> 5, l = tid & 31;
+        if (l == 0) {
+            red[0][w] = sx;
+            red[1][w] = sy;
+            red[2][w] = sz;
+        }
+        __syncthreads();
+        if (tid < 3) {
+            double t = 0.0;
+            const int nw = (blockDim.x + 31) >> 5;
+            for (int k = 0; k < nw; ++k) t += red[tid][k];
+            const int64_t cnt = (n - base) < block ? (n - base) : (int64_t)block;
+            cen[tid] = t / (double)cnt;
+            centres[3 * blockIdx.x + tid] = cen[tid];
+        }
+        __syncthreads();
+    } else {
+        if (tid < 3) cen[tid] = 0.0;
+        __syncthreads();
+    }
+    const double cx = cen[0], cy = cen[1], cz = cen[2];
+    for (int lb = tid; lb < block; lb += blockDim.x) {
+        const int64_t g = base + lb;
+        if (g < n) {
+            store_jdup(jdup, g, (float)(pos[3 * g + 0] - cx), (float)(pos[3 * g + 1] - cy),
+                       (float)(pos[3 * g + 2] - cz), mass[g]);
+        } else {
+            store_jdup(jdup, g, kPadPos, kPadPos, kPadPos, 0.0f);
+        }
+    }
+}
+
+__global__ void pack_f32_kernel(int64_t n, int64_t npad, float* __restrict__ pos, float* __restrict__ vel,
+                                const float* __restrict__ acc, const float* __restrict__ mass, float kick,
+                                float drift, float* __restrict__ jdup) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < npad;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        if (g < n) {
+            float x = pos[3 * g + 0], y = pos[3 * g + 1], z = pos[3 * g + 2];
+            if (vel != nullptr && (kick != 0.0f || drift != 0.0f)) {
+                float vx = vel[3 * g + 0], vy = vel[3 * g + 1], vz = vel[3 * g + 2];
+                if (acc != nullptr && kick != 0.0f) {
+                    vx = fmaf(kick, acc[3 * g + 0], vx);
+                    vy = fmaf(kick, acc[3 * g + 1], vy);
+                    vz = fmaf(kick, acc[3 * g + 2], vz);
+                    vel[3 * g + 0] = vx;
+                    vel[3 * g + 1] = vy;
+                    vel[3 * g + 2] = vz;
+                }
+                if (drift != 0.0f) {
+                    x = fmaf(drift, vx, x);
+                    y = fmaf(drift, vy, y);
+                    z = fmaf(drift, vz, z);
+                    pos[3 * g + 0] = x;
+                    pos[3 * g + 1] = y;
+                    pos[3 * g + 2] = z;
+                }
+            }
+            store_jdup(jdup, g, x, y, z, mass[g]);
+        } else {
+            store_jdup(jdup, g, kPadPos, kPadPos, kPadPos, 0.0f);
+        }
+    }
+}
+
+template <typename V>
+__global__ void kick_kernel(int64_t n3, V* __restrict__ vel, const float* __restrict__ acc, V kick) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n3; k += (int64_t)gridDim.x * blockDim.x)
+        vel[k] += kick * (V)acc[k];
+}
+
+unsigned grid_for(int64_t work, int threads) {
+    int64_t g = (work + threads - 1) / threads;
+    if (g > 152 * 32) g = 152 * 32;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+}  // namespace
+
+cudaError_t pack_f64(int64_t n, int64_t npad, int block, double* pos, double* vel, const float* acc,
+                     const float* mass, double kick, double drift, bool plain, float* jdup, double* centres,
+                     cudaStream_t st) {
+    const unsigned nblk = (unsigned)(npad / block);
+    pack_f64_kernel<<<nblk, 256, 0, st>>>(n, block, pos, vel, acc, mass, kick, drift, plain ? 1 : 0, jdup,
+                                          centres);
+    return cudaGetLastError();
+}
+
+cudaError_t pack_f32(int64_t n, int64_t npad, float* pos, float* vel, const float* acc, const float* mass,
+                     float kick, float drift, float* jdup, cudaStream_t st) {
+    pack_f32_kernel<<<grid_for(npad, 256), 256, 0, st>>>(n, npad, pos, vel, acc, mass, kick, drift, jdup);
+    return cudaGetLastError();
+}
+
+cudaError_t kick_f64(int64_t n, double* vel, const float* acc, double kick, cudaStream_t st) {
+    kick_kernel<double><<<grid_for(3 * n, 256), 256, 0, st>>>(3 * n, vel, acc, kick);
+    return cudaGetLastError();
+}
+
+cudaError_t kick_f32(int64_t n, float* vel, const float* acc, float kick, cudaStream_t st) {
+    kick_kernel<float><<<grid_for(3 * n, 256), 256, 0, st>>>(3 * n, vel, acc, kick);
+    return cudaGetLastError();
+}
+
+}  // namespace nbk

@@ -1,0 +1,90 @@
+"""The C-ABI library builds, loads without a GPU, exports every function the
+header declares, and validates its arguments before touching the GPU."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2411_18889_gb300 import _lib
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_2411_18889_gb300 import build
+        build.build()
+    return _lib.load()
+
+
+def test_header_symbols_exported(lib):
+    from paper_2411_18889_gb300 import _lib
+    names = _lib.header_functions()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in nbody.h but not exported"
+        assert name in _lib.SIGNATURES, f"{name} has no ctypes signature in the binding"
+
+
+def test_static_queries(lib):
+    assert lib.nbody_version() >= 10000
+    k = lib.nbody_num_configs()
+    assert k >= 1
+    for i in range(k):
+        b = lib.nbody_config_block(i)
+        assert b > 0 and b % 64 == 0
+    assert lib.nbody_config_block(-1) == 0 and lib.nbody_config_block(k) == 0
+    assert lib.nbody_strerror(0) == b"success"
+    assert lib.nbody_strerror(-1) == b"invalid argument"
+    assert lib.nbody_strerror(-4) == b"bounded device wait expired"
+
+
+def test_argument_validation_without_gpu(lib):
+    from paper_2411_18889_gb300._lib import NBODY_EINVAL, NBODY_OK, NbodyOpts
+    p = np.zeros((4, 3))
+    pf = np.zeros((4, 3), dtype=np.float32)
+    m = np.ones(4, dtype=np.float32)
+    a = np.zeros((4, 3), dtype=np.float32)
+    vp = lambda x: ctypes.c_void_p(x.ctypes.data)
+    nul = None
+    # n == 0 is a no-op
+    assert lib.nbody_accel(0, nul, nul, 0.1, nul, nul, nul) == NBODY_OK
+    assert lib.nbody_leapfrog(0, nul, nul, nul, 0.1, 0.01, 5, nul) == NBODY_OK
+    assert lib.nbody_leapfrog_f32(4, vp(pf), vp(pf), vp(m), 0.1, 0.01, 0, nul) == NBODY_OK  # zero steps
+    # bad sizes, pointers, softening, time step
+    assert lib.nbody_accel(-1, vp(p), vp(m), 0.1, vp(a), nul, nul) == NBODY_EINVAL
+    assert lib.nbody_accel(4, nul, vp(m), 0.1, vp(a), nul, nul) == NBODY_EINVAL
+    assert lib.nbody_accel(4, vp(p), nul, 0.1, vp(a), nul, nul) == NBODY_EINVAL
+    assert lib.nbody_accel(4, vp(p), vp(m), 0.1, nul, nul, nul) == NBODY_EINVAL
+    assert lib.nbody_accel(4, vp(p), vp(m), -0.1, vp(a), nul, nul) == NBODY_EINVAL
+    assert lib.nbody_accel(4, vp(p), vp(m), float("nan"), vp(a), nul, nul) == NBODY_EINVAL
+    assert lib.nbody_accel_f32(4, vp(pf), vp(m), float("inf"), vp(a), nul, nul) == NBODY_EINVAL
+    assert lib.nbody_leapfrog(4, vp(p), vp(p), vp(m), 0.1, float("nan"), 1, nul) == NBODY_EINVAL
+    assert lib.nbody_leapfrog(4, vp(p), vp(p), vp(m), 0.1, 0.01, -1, nul) == NBODY_EINVAL
+    assert lib.nbody_leapfrog_f32(4, vp(pf), nul, vp(m), 0.1, 0.01, 1, nul) == NBODY_EINVAL
+    out = np.zeros(9)
+    assert lib.nbody_energy(4, vp(p), vp(p), vp(m), 0.1, nul, nul) == NBODY_EINVAL
+    assert lib.nbody_energy(0, nul, nul, nul, 0.1, vp(out), nul) == NBODY_OK
+    # options
+    o = NbodyOpts()
+    lib.nbody_opts_default(ctypes.byref(o))
+    assert (o.precision, o.accumulate, o.config, o.reserved) == (0, 0, -1, 0)
+    for field, bad in (("precision", 7), ("accumulate", 3), ("config", 999), ("config", -2), ("reserved", 1)):
+        o2 = NbodyOpts()
+        lib.nbody_opts_default(ctypes.byref(o2))
+        setattr(o2, field, bad)
+        assert lib.nbody_accel(4, vp(p), vp(m), 0.1, vp(a), nul, ctypes.byref(o2)) == NBODY_EINVAL
+
+
+def test_python_binding_checks_arrays():
+    import paper_2411_18889_gb300 as nb
+    p = np.zeros((4, 3), dtype=np.float32)  # wrong dtype for nbody_accel
+    m = np.ones(4, dtype=np.float32)
+    a = np.zeros((4, 3), dtype=np.float32)
+    with pytest.raises(TypeError):
+        nb.nbody_accel(p, m, 0.1, a)
+    with pytest.raises(ValueError):
+        nb.nbody_accel_f32(p, m[:3], 0.1, a)
+    with pytest.raises(ValueError):
+        nb.nbody_accel_f32(np.zeros((3, 4), dtype=np.float32).T, m[:3], 0.1, a)

@@ -1,0 +1,117 @@
+"""GPU leapfrog against the oracle's leapfrog, and one-step checks from the
+GPU's own state where a full oracle trajectory would be too slow."""
+import numpy as np
+import pytest
+
+import nbody_inputs as ni
+
+pytestmark = pytest.mark.gpu
+
+
+def t(x, dtype):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=dtype)).cuda()
+
+
+def test_small_plain_16_steps(nb, oracle_mod):
+    """N=1024 equal-mass Plummer, eps=dt=2^-7, 16 KDK steps with FP32 state:
+    positions track the FP64 oracle and the energy agrees to 1e-5."""
+    import torch
+    w = ni.small_plain()
+    m32 = w.mass.astype(np.float32)
+    P, V = t(w.pos, np.float32), t(w.vel, np.float32)
+    nb.nbody_leapfrog_f32(P, V, t(m32, np.float32), np.float32(w.eps), np.float32(w.dt), w.steps)
+    torch.cuda.synchronize()
+    assert nb.nbody_last_device_error() == 0
+    p_ref, v_ref, _ = oracle_mod.leapfrog(w.pos, w.vel, w.mass, w.eps, w.dt, w.steps)
+    pg, vg = P.cpu().numpy().astype(np.float64), V.cpu().numpy().astype(np.float64)
+    assert np.abs(pg - p_ref).max() <= 2e-5
+    assert np.abs(vg - v_ref).max() <= 2e-4
+    e0 = oracle_mod.energy(w.pos, w.vel, w.mass, w.eps)["E"]
+    e_ref = oracle_mod.energy(p_ref, v_ref, w.mass, w.eps)["E"]
+    e_gpu = oracle_mod.energy(pg, vg, w.mass, w.eps)["E"]
+    assert abs(e_gpu - e_ref) <= 1e-5 * abs(e0)
+    e_dev = nb.nbody_energy_f32(P, V, t(m32, np.float32), np.float32(w.eps))["E"]
+    assert abs(e_dev - e_ref) <= 1e-5 * abs(e0)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "plain"])
+def test_fp64_state_trajectory(nb, oracle_mod, prec):
+    import torch
+    p, v, m = ni.plummer(3000, 12, masses="loguniform")
+    m32 = m.astype(np.float32)
+    eps, dt, steps = 2.0 ** -7, 2.0 ** -8, 8
+    P, V = t(p, np.float64), t(v, np.float64)
+    pr = nb.NBODY_PREC_MIXED if prec == "mixed" else nb.NBODY_PREC_PLAIN
+    nb.nbody_leapfrog(P, V, t(m32, np.float32), eps, dt, steps, precision=pr)
+    torch.cuda.synchronize()
+    p_ref, v_ref, _ = oracle_mod.leapfrog(p, v, m32.astype(np.float64), eps, dt, steps)
+    vs = np.abs(v_ref).max()
+    assert np.abs(P.cpu().numpy() - p_ref).max() <= 1e-8 * 8
+    assert np.abs(V.cpu().numpy() - v_ref).max() <= 1e-6 * vs
+
+
+def test_steps_compose(nb):
+    """One call of k steps equals k calls of one step (FP64 state; the merged
+    kick differs only by rounding)."""
+    import torch
+    p, v, m = ni.plummer(2000, 13)
+    m32 = t(m.astype(np.float32), np.float32)
+    P1, V1 = t(p, np.float64), t(v, np.float64)
+    P2, V2 = t(p, np.float64), t(v, np.float64)
+    nb.nbody_leapfrog(P1, V1, m32, 0.01, 2.0 ** -8, 4)
+    for _ in range(4):
+        nb.nbody_leapfrog(P2, V2, m32, 0.01, 2.0 ** -8, 1)
+    torch.cuda.synchronize()
+    assert torch.allclose(P1, P2, rtol=0, atol=1e-13)
+    assert torch.allclose(V1, V2, rtol=0, atol=1e-12)
+
+
+def test_zero_steps_and_momentum(nb):
+    import torch
+    p, v, m = ni.plummer(1500, 14, masses="loguniform")
+    m32 = m.astype(np.float32)
+    P, V = t(p, np.float64), t(v, np.float64)
+    nb.nbody_leapfrog(P, V, t(m32, np.float32), 0.01, 0.01, 0)
+    torch.cuda.synchronize()
+    assert np.array_equal(P.cpu().numpy(), p) and np.array_equal(V.cpu().numpy(), v)
+    mom0 = (m32[:, None].astype(np.float64) * v).sum(0)
+    nb.nbody_leapfrog(P, V, t(m32, np.float32), 0.01, 2.0 ** -8, 16)
+    torch.cuda.synchronize()
+    mom1 = (m32[:, None].astype(np.float64) * V.cpu().numpy()).sum(0)
+    # sum m a vanishes up to FP32 pair rounding: drift stays tiny
+    assert np.abs(mom1 - mom0).max() <= 1e-7
+
+
+def test_host_state_roundtrip(nb):
+    """Host (numpy) state is staged through the device and written back."""
+    import torch
+    p, v, m = ni.plummer(1024, 15)
+    m32 = m.astype(np.float32)
+    ph, vh = p.copy(), v.copy()
+    nb.nbody_leapfrog(ph, vh, m32, 0.01, 2.0 ** -8, 3)
+    P, V = t(p, np.float64), t(v, np.float64)
+    nb.nbody_leapfrog(P, V, t(m32, np.float32), 0.01, 2.0 ** -8, 3)
+    torch.cuda.synchronize()
+    assert np.array_equal(ph, P.cpu().numpy()) and np.array_equal(vh, V.cpu().numpy())
+
+
+def test_kepler_orbit_second_order(nb):
+    """Eccentric binary (e=0.5, FP64 state) after 0.37 of a period matches
+    Kepler's equation, with the error falling ~4x per halving of dt: the FP32
+    force error stays far below the integrator's."""
+    import math
+    import torch
+    from test_oracle_integrator import kepler_initial, kepler_state
+    pos0, vel0, m = kepler_initial(0.5)
+    T = 2 * math.pi
+    errs = []
+    for nsteps in (2000, 4000):
+        dt = T / nsteps
+        k = int(round(0.37 * T / dt))
+        P, V = t(pos0, np.float64), t(vel0, np.float64)
+        nb.nbody_leapfrog(P, V, t(m.astype(np.float32), np.float32), 1e-9, dt, k)
+        torch.cuda.synchronize()
+        errs.append(np.abs(P.cpu().numpy() - kepler_state(0.5, k * dt)).max())
+    assert errs[0] < 2e-3
+    assert 3.5 < errs[0] / errs[1] < 4.5
