@@ -52,7 +52,7 @@ def test_precision_workload_force(nb, oracle_mod, c3):
     torch.cuda.synchronize()
     e_plain = rel(acc.cpu().numpy()[idx], ra)
     print(f"plain N=2^20: median {np.median(e_plain):.3g} max {e_plain.max():.3g}")
-    assert np.median(e_plain) > 1e-3
+    assert np.median(e_plain) > 50 * 2e-6 and e_plain.max() > 1e-2  # misses the target by >50x
 
 
 def test_precision_workload_steps(nb, oracle_mod, c3):

@@ -147,7 +147,7 @@ def test_offset_sphere_mixed_vs_plain(nb, oracle_mod):
     acc, pot = gpu_accel(nb, "mixed", p, m32, eps)
     check(acc, pot, ra, rp)
     acc_p, _ = gpu_accel(nb, "plain", p, m32, eps, with_pot=False)
-    assert np.median(rel_err(acc_p, ra)) > 1e-3
+    assert np.median(rel_err(acc_p, ra)) > 50 * ACC_MED  # misses the target by >50x
 
 
 def test_deterministic(nb):
