@@ -191,6 +191,24 @@ def workload_config(w):
             "(256 MiB write); the force kernel's 32 MiB j-array is L2-resident by design"}
 
 
+def profile_case(n: int) -> int:
+    """Two force evaluations (mixed precision, no potential) for ncu captures."""
+    import torch
+    import nbody_inputs as ni
+    import paper_2411_18889_gb300 as nb
+    nb.load()
+    p, _, m = ni.plummer(n, 3, masses="loguniform", offset=ni.plummer_offset())
+    P = torch.from_numpy(p).cuda()
+    M = torch.from_numpy(m.astype(np.float32)).cuda()
+    acc = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        nb.nbody_accel(P, M, 2.0 ** -9, acc, None)
+    torch.cuda.synchronize()
+    assert nb.nbody_last_device_error() == 0
+    print(f"profile case n={n}: sum|a| = {float(acc.abs().sum()):.6e}")
+    return 0
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -201,10 +219,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--profile-case", type=int, default=0, metavar="N",
+                    help="only run nbody_accel twice on the precision workload's recipe at N bodies "
+                         "(mixed, no potential: the leapfrog's force variant), for profilers")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.profile_case:
+        return profile_case(args.profile_case)
 
     import torch
     import nbody_inputs as ni
@@ -292,11 +315,14 @@ def main():
                 "kernel": "nbk::force_kernel (stream-K all-pairs; mixed precision, compensated, no potential)",
                 "launches": klaunch, "ms_per_launch": per_launch_s * 1e3,
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {SM_MAX_MHZ_DEFAULT:.0f} MHz"}
-    traffic_file = os.path.join(ROOT, "profiles", "force_traffic.json")
+    traffic_file = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
     if os.path.exists(traffic_file):
+        import hashlib
         try:
             tr = json.load(open(traffic_file))
-            if tr.get("n") == n:
+            src = os.path.join(ROOT, "paper_2411_18889_gb300", "csrc", "force.cu")
+            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+            if tr.get("n") == n and tr.get("force_cu_sha256") == sha:  # counters of this very kernel
                 roofline["traffic"] = tr.get("dram_bytes_per_launch")
         except Exception:
             pass

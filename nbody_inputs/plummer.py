@@ -177,6 +177,11 @@ def throughput_plain(n: int = 65536, seed: int = 2) -> Workload:
 OFFSET_CENTRE = (1.0e4, -3.0e3, 7.0e2)
 
 
+def plummer_offset():
+    """Centre of the precision workload's sphere."""
+    return OFFSET_CENTRE
+
+
 def precision_offset(n: int = 1 << 20, seed: int = 3) -> Workload:
     """N=2^20 Plummer offset to (1e4,-3e3,7e2), log-uniform masses in [1e-3,1]
     renormalised to 1, eps=2^-9, dt=2^-9, 1 force evaluation + 4 steps, FP64
