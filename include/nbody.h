@@ -143,6 +143,46 @@ const char* nbody_strerror(int code);
  * GPU stays usable), NBODY_EINVAL for a limit out of range. */
 int nbody_selftest_wait(double limit_seconds, const nbody_opts* opts);
 
+/*
+ * nbody_accel_noalloc -- nbody_accel (mixed precision, compensated sums, the
+ * potential when pot != NULL) for callers that cannot allocate GPU memory.
+ * The paper has no counterpart; this is a deployment variant of the same
+ * force evaluation.
+ *
+ * Who needs it: code running where cudaMalloc is not allowed or not safe --
+ * inside another framework's allocator or memory-pool callback, in a
+ * real-time loop that must never wait on the driver's allocator, or in a
+ * process that has reserved all device memory up front.  nbody_accel grows a
+ * cached workspace with cudaMalloc; this call never allocates or frees
+ * anything (no cudaMalloc, cudaFree or allocating library routine).
+ *
+ * Its scratch is one fixed array in the library's device module,
+ * 22 MiB + 4.25 KiB, which every GPU that loads the library holds until the
+ * process exits.  Limits: n <= NBODY_NOALLOC_MAX_N (65536); larger n returns
+ * NBODY_EINVAL without queuing work.  If the device needs more partial-sum
+ * scratch than the array holds (a GPU with more SMs than it was sized for),
+ * the call returns NBODY_ENOMEM.
+ *
+ *  pos [n][3] double, mass [n] float, acc [n][3] float (written), pot [n]
+ *  float or NULL: device (or managed) memory only -- host arrays would need
+ *  staging buffers, so they return NBODY_EINVAL.
+ *  status: NULL, or a device int the call sets to 0 and its kernels set to 1
+ *  if a bounded device-side wait expired (results then incomplete).
+ *  stream: cudaStream_t to run on (NULL = legacy default stream); the call
+ *  is asynchronous.
+ *
+ * The first call on each device performs the set-up: it looks up the
+ * device address of the scratch array (cudaGetSymbolAddress, with that
+ * device current), which can load the library's device module.  Make that
+ * first call before any stream capture.  Every call shares the one array and
+ * it keeps the last call's contents, so calls that overlap on the GPU (two
+ * streams, or two host threads without ordering) race and corrupt each
+ * other: order them on one stream or synchronise between them.
+ */
+#define NBODY_NOALLOC_MAX_N 65536
+int nbody_accel_noalloc(int64_t n, const double* pos, const float* mass, double eps, float* acc, float* pot,
+                        int* status, void* stream);
+
 /* Benchmark instrumentation.  While enabled, every force-kernel launch is
  * bracketed by a pair of CUDA events recorded on its own stream.
  * nbody_profile_read waits for those events and returns the summed device

@@ -54,6 +54,7 @@ SIGNATURES = {
     "nbody_last_cuda_error": (_int, []),
     "nbody_strerror": (ctypes.c_char_p, [_int]),
     "nbody_selftest_wait": (_int, [_dbl, _OPTS]),
+    "nbody_accel_noalloc": (_int, [_i64, _vp, _vp, _dbl, _vp, _vp, _vp, _vp]),
     "nbody_profile_enable": (None, [_int]),
     "nbody_profile_read": (_int, [ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "nbody_finalize": (None, []),

@@ -379,6 +379,14 @@ size_t force_partial_doubles(int k, int num_sms) {
     return (size_t)num_sms * 8u * 2u * (size_t)s.block * 4u;
 }
 
+size_t force_partial_doubles_for(int k, bool pot, bool mixed, bool compensated, int64_t npad, int num_sms) {
+    const ShapeEntry& e = shapes()[k];
+    const int occ = std::min(occupancy(k, pot ? 1 : 0, mixed ? 1 : 0, compensated ? 1 : 0), 8);
+    const int64_t units = (npad / e.shape.block) * (npad / e.shape.jtile);
+    const int64_t nctas = std::min<int64_t>((int64_t)num_sms * occ, units);
+    return (size_t)nctas * 2u * (size_t)e.shape.block * 4u;
+}
+
 cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st, int* launched, cudaEvent_t ev0,
                          cudaEvent_t ev1) {
     const ShapeEntry& e = shapes()[k];

@@ -177,6 +177,9 @@ struct ForceArgs {
 
 // Scratch doubles needed for the split i-block partial sums of shape k.
 size_t force_partial_doubles(int k, int num_sms);
+// Exact scratch doubles force_launch needs for this variant and padded size
+// (its grid: resident CTAs on num_sms SMs, capped by the work units).
+size_t force_partial_doubles_for(int k, bool pot, bool mixed, bool compensated, int64_t npad, int num_sms);
 // Launch the force kernel (stream-K over i-block x j-tile units) and the fixup
 // that combines split i-blocks; *launched gets the number of kernels queued.
 // ev0/ev1 (optional) are recorded on `st` just before and after the force
