@@ -209,6 +209,57 @@ def profile_case(n: int) -> int:
     return 0
 
 
+def batched_leg(nb, dev, sms, peak_int_s, args):
+    """Ragged workload: 4096 Plummer systems, N_s log-uniform in [64,4096],
+    eps_s = 4/sqrt(N_s), dt = 2^-8, 64 KDK steps in one persistent launch;
+    against the same systems advanced one nbody_leapfrog_f32 call (and its
+    195 kernel launches) per system."""
+    import torch
+    import nbody_inputs as ni
+    off, pos, vel, mass, eps = ni.ragged_batch()
+    sizes = np.diff(off)
+    steps, dt = 64, 2.0 ** -8
+    inter = float((steps + 1) * np.sum(sizes.astype(np.float64) ** 2))
+    O = torch.from_numpy(off).to(dev)
+    P0 = torch.from_numpy(pos.astype(np.float32)).to(dev)
+    V0 = torch.from_numpy(vel.astype(np.float32)).to(dev)
+    M = torch.from_numpy(mass.astype(np.float32)).to(dev)
+    E = torch.from_numpy(eps.astype(np.float32)).to(dev)
+    P, V = P0.clone(), V0.clone()
+    nb.nbody_leapfrog_batched(O, P, V, M, E, dt, steps)  # warm-up
+    torch.cuda.synchronize()
+    reps = max(1, min(args.steps, 3))
+    ts = []
+    for _ in range(reps):
+        P.copy_(P0)
+        V.copy_(V0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        nb.nbody_leapfrog_batched(O, P, V, M, E, dt, steps)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    t_b = statistics.median(ts)
+    # one launch sequence per system
+    P.copy_(P0)
+    V.copy_(V0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(len(sizes)):
+        lo, hi = int(off[s]), int(off[s + 1])
+        nb.nbody_leapfrog_f32(P[lo:hi], V[lo:hi], M[lo:hi], float(eps[s]), dt, steps)
+    torch.cuda.synchronize()
+    t_s = time.perf_counter() - t0
+    value = inter / t_b / 1e9
+    return {"workload": "ragged_4096_systems_n64_4096_loguniform_eps4_over_sqrtn_kdk64_dt2^-8",
+            "value": value, "unit": UNIT, "pct_fp32_peak": value * 1e9 / peak_int_s * 100,
+            "ms_per_call": t_b * 1e3, "interactions_per_call": inter,
+            "per_system_calls_value": inter / t_s / 1e9, "per_system_calls_ms": t_s * 1e3,
+            "speedup_vs_per_system_calls": t_s / t_b, "launches_per_call": 1,
+            "per_system_launches": int(len(sizes) * (3 * (steps + 1) + 1))}
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -329,6 +380,8 @@ def main():
     if clocks.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved_tflops / (peak_tflops * clocks["sm_mhz"] / SM_MAX_MHZ_DEFAULT)
 
+    batched = batched_leg(nb, dev, sms, peak_int_s, args)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         rate, k, dt, cores = oracle_rate(w, 12.0)
@@ -343,7 +396,7 @@ def main():
         "plain": {"value": plain_value, "unit": UNIT, "pct_fp32_peak": plain_value * 1e9 / peak_int_s * 100,
                   "precision": "FP32 absolute coordinates (fails the accuracy target at this offset by design)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+        "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "batched": batched,
         "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
         "wall_s_timed_region": wall_s, "step_ms": [s * 1e3 for s in per_step],
     }

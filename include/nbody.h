@@ -120,6 +120,29 @@ int nbody_energy(int64_t n, const double* pos, const double* vel, const float* m
 int nbody_energy_f32(int64_t n, const float* pos, const float* vel, const float* mass, float eps,
                      double* out, const nbody_opts* opts);
 
+/*
+ * Ragged batches: nsys independent systems in one persistent launch.  System s
+ * owns bodies [offsets[s], offsets[s+1]) of the concatenated arrays; each has
+ * its own softening eps[s] and interacts only with itself (Eq. 1 per system).
+ *  offsets [nsys+1] int64, offsets[0] == 0, non-decreasing, every system at
+ *          most NBODY_BATCH_MAX_N bodies (else NBODY_EINVAL); read on the host
+ *          (a device array is copied back, which waits for the stream)
+ *  pos [N][3] float, mass [N] float, eps [nsys] float (>= 0, finite)
+ *  acc [N][3] float written; pot [N] float or NULL.
+ * FP32 state and pair arithmetic; per-body sums in two levels (64-pair blocks).
+ * opts->config selects the batched kernel shape (0 .. 3), -1 = default;
+ * precision and accumulate are ignored.
+ */
+#define NBODY_BATCH_MAX_N 12288
+int nbody_accel_batched(int64_t nsys, const int64_t* offsets, const float* pos, const float* mass, const float* eps,
+                        float* acc, float* pot, const nbody_opts* opts);
+
+/* Kick-drift-kick leapfrog of every system of a ragged batch, all steps inside
+ * one persistent kernel (steps + 1 force evaluations per system); pos, vel
+ * [N][3] float updated in place. */
+int nbody_leapfrog_batched(int64_t nsys, const int64_t* offsets, float* pos, float* vel, const float* mass,
+                           const float* eps, float dt, int64_t steps, const nbody_opts* opts);
+
 /* Number of force-kernel shapes compiled in (for opts->config) and the
  * bodies per i-block of shape k (0 if k is out of range). */
 int nbody_num_configs(void);

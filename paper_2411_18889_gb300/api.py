@@ -109,6 +109,42 @@ def nbody_leapfrog_f32(pos, vel, mass, eps, dt, steps, **kw):
           "nbody_leapfrog_f32")
 
 
+def _i64ptr(a, shape, name):
+    if _is_torch(a):
+        if str(a.dtype) != "torch.int64" or not a.is_contiguous() or tuple(a.shape) != tuple(shape):
+            raise ValueError(f"{name}: expected contiguous torch.int64 of shape {tuple(shape)}")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.int64 or not a.flags["C_CONTIGUOUS"] or tuple(a.shape) != tuple(shape):
+            raise ValueError(f"{name}: expected C-contiguous int64 of shape {tuple(shape)}")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError(f"{name}: expected a torch tensor or numpy array")
+
+
+def nbody_accel_batched(offsets, pos, mass, eps, acc, pot=None, **kw):
+    """nbody_accel_batched: offsets (nsys+1,) int64, pos (N,3) f32, mass (N,) f32, eps (nsys,) f32,
+    acc (N,3) f32 out, pot (N,) f32 out or None."""
+    nsys = int(offsets.shape[0]) - 1
+    n = int(pos.shape[0])
+    o = make_opts((pos, mass, acc, pot), **kw)
+    check(load().nbody_accel_batched(nsys, _i64ptr(offsets, (nsys + 1,), "offsets"), _ptr(pos, "f32", (n, 3), "pos"),
+                                     _ptr(mass, "f32", (n,), "mass"), _ptr(eps, "f32", (nsys,), "eps"),
+                                     _ptr(acc, "f32", (n, 3), "acc"), _ptr(pot, "f32", (n,), "pot"), ctypes.byref(o)),
+          "nbody_accel_batched")
+
+
+def nbody_leapfrog_batched(offsets, pos, vel, mass, eps, dt, steps, **kw):
+    """nbody_leapfrog_batched: pos, vel (N,3) f32 updated in place."""
+    nsys = int(offsets.shape[0]) - 1
+    n = int(pos.shape[0])
+    o = make_opts((pos, vel, mass), **kw)
+    check(load().nbody_leapfrog_batched(nsys, _i64ptr(offsets, (nsys + 1,), "offsets"),
+                                        _ptr(pos, "f32", (n, 3), "pos"), _ptr(vel, "f32", (n, 3), "vel"),
+                                        _ptr(mass, "f32", (n,), "mass"), _ptr(eps, "f32", (nsys,), "eps"),
+                                        float(dt), int(steps), ctypes.byref(o)),
+          "nbody_leapfrog_batched")
+
+
 def _energy(fn, name, dt, pos, vel, mass, eps, **kw):
     n = _n(pos)
     o = make_opts((pos, vel, mass), **kw)

@@ -1,0 +1,289 @@
+// batched.cu -- many independent systems of uneven size in one persistent
+// launch: the force of Eq. 1 (Miki & Hanawa, Sec. III.A, per-pair arithmetic of
+// Listing 4) for each system, optionally driving a whole kick-drift-kick
+// leapfrog inside the kernel (the integrator is not in the paper).
+//
+// Scheduling.  A persistent grid of CTAs pulls systems from an atomic queue in
+// longest-processing-time-first order (the host sorts by n_s^2), so the few
+// large systems start first and the many small ones fill the tail.  One CTA
+// owns one system for the whole call: its bodies live in shared memory, and
+// every force evaluation and every kick and drift of all steps happen without
+// another launch.
+//
+// Layout.  Shared memory holds the system as j-pairs (x0,x1,y0,y1,z0,z1,m0,m1):
+// 16 bytes per body, so a 4096-body system takes 64 KiB and three CTAs fit an
+// SM.  Each thread keeps I i-bodies with their coordinates duplicated in f32x2
+// registers (x_i, x_i); one pair of 16-byte broadcast loads gives two j-bodies
+// and each i-body then takes the 12 (13 with the potential) packed f32x2
+// instructions and two MUFU reciprocal square roots of Listing 4's sequence,
+// for two interactions.  The two halves of each accumulator (even and odd j)
+// are added at the end.
+//
+// Accumulation.  FP32 partial sums over blocks of 64 j-pairs are folded into
+// an FP32 total (two-level summation), so a 4096-term sum carries the rounding
+// of two 64-term sums instead of one 4096-term running sum.
+//
+// Self term.  With eps > 0 the pair j = i adds exactly 0 to the acceleration
+// (its difference vector is exactly zero) and a known m_i/eps to the potential,
+// which is subtracted in the same FP32 arithmetic.  Systems with eps == 0 take
+// a masked loop that skips j = i.
+#include <algorithm>
+#include <mutex>
+
+#include "nbody_internal.cuh"
+
+namespace nbk {
+namespace {
+
+constexpr int kJBlock = 64;  // j-pairs per partial sum
+
+struct BParams {
+    int64_t nsys;
+    const int64_t* offsets;  // [nsys+1] device
+    const int* order;        // [nsys] LPT order
+    int* queue;              // atomic counter, zeroed before the launch
+    float* pos;              // [N][3]
+    float* vel;              // [N][3] (leapfrog)
+    const float* mass;       // [N]
+    const float* eps;        // [nsys]
+    float* acc;              // [N][3] (force only)
+    float* pot;              // [N] or nullptr (force only)
+    float dt;
+    int64_t steps;           // 0: force only
+};
+
+template <int T, int I, bool POT, bool MASK>
+__device__ __forceinline__ void eval_pass(const float* __restrict__ sj, int npair, int ns, int base, f2 eps2,
+                                          const BParams& p, int64_t off, int64_t ev, float kick, bool drift,
+                                          float eps2s) {
+    const int tid = threadIdx.x;
+    f2 xi[I], yi[I], zi[I];
+    int ib[I];
+#pragma unroll
+    for (int k = 0; k < I; ++k) {
+        ib[k] = base + k * T + tid;
+        const int b = ib[k] < ns ? ib[k] : 0;  // threads past the end repeat body 0 and write nothing
+        const float* s = sj + (b >> 1) * 8 + (b & 1);
+        xi[k] = pk(s[0], s[0]);
+        yi[k] = pk(s[2], s[2]);
+        zi[k] = pk(s[4], s[4]);
+    }
+    f2 tx[I], ty[I], tz[I], tp[I];
+#pragma unroll
+    for (int k = 0; k < I; ++k) tx[k] = ty[k] = tz[k] = tp[k] = 0ull;
+    const ulonglong2* sp = reinterpret_cast<const ulonglong2*>(sj);
+    for (int jb = 0; jb < npair; jb += kJBlock) {
+        const int je = min(npair, jb + kJBlock);
+        f2 ax[I], ay[I], az[I], ap[I];
+#pragma unroll
+        for (int k = 0; k < I; ++k) ax[k] = ay[k] = az[k] = ap[k] = 0ull;
+#pragma unroll 4
+        for (int jp = jb; jp < je; ++jp) {
+            const ulonglong2 A = sp[2 * jp];
+            const ulonglong2 B = sp[2 * jp + 1];
+            const f2 xj = A.x, yj = A.y, zj = B.x, mj = B.y;
+#pragma unroll
+            for (int k = 0; k < I; ++k) {
+                const f2 dx = sub2(xj, xi[k]);
+                const f2 dy = sub2(yj, yi[k]);
+                const f2 dz = sub2(zj, zi[k]);
+                f2 r2 = fma2(dx, dx, eps2);
+                r2 = fma2(dy, dy, r2);
+                r2 = fma2(dz, dz, r2);
+                float s0, s1;
+                upk(r2, s0, s1);
+                float q0 = rsqrt_approx(s0);
+                float q1 = rsqrt_approx(s1);
+                if (MASK) {
+                    if (2 * jp == ib[k]) q0 = 0.0f;
+                    if (2 * jp + 1 == ib[k]) q1 = 0.0f;
+                }
+                const f2 ri = pk(q0, q1);
+                f2 w = mul2(ri, mul2(ri, ri));
+                w = mul2(w, mj);
+                ax[k] = fma2(dx, w, ax[k]);
+                ay[k] = fma2(dy, w, ay[k]);
+                az[k] = fma2(dz, w, az[k]);
+                if (POT) ap[k] = fma2(r2, w, ap[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < I; ++k) {
+            tx[k] = add2(tx[k], ax[k]);
+            ty[k] = add2(ty[k], ay[k]);
+            tz[k] = add2(tz[k], az[k]);
+            if (POT) tp[k] = add2(tp[k], ap[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < I; ++k) {
+        if (ib[k] >= ns) continue;
+        float a0, a1;
+        upk(tx[k], a0, a1);
+        const float ax_ = a0 + a1;
+        upk(ty[k], a0, a1);
+        const float ay_ = a0 + a1;
+        upk(tz[k], a0, a1);
+        const float az_ = a0 + a1;
+        const int64_t g = off + ib[k];
+        if (p.steps == 0) {
+            p.acc[3 * g + 0] = ax_;
+            p.acc[3 * g + 1] = ay_;
+            p.acc[3 * g + 2] = az_;
+            if (POT) {
+                upk(tp[k], a0, a1);
+                float s = a0 + a1;
+                if (!MASK) {  // remove the self pair's m_i/eps, computed as the loop did
+                    const int b = ib[k];
+                    const float mi = sj[(b >> 1) * 8 + 6 + (b & 1)];
+                    const float r = rsqrt_approx(eps2s);
+                    float w;
+                    asm("mul.rn.ftz.f32 %0, %1, %2;" : "=f"(w) : "f"(r), "f"(r));
+                    asm("mul.rn.ftz.f32 %0, %1, %2;" : "=f"(w) : "f"(r), "f"(w));
+                    asm("mul.rn.ftz.f32 %0, %1, %2;" : "=f"(w) : "f"(w), "f"(mi));
+                    asm("mul.rn.ftz.f32 %0, %1, %2;" : "=f"(w) : "f"(eps2s), "f"(w));
+                    s -= w;
+                }
+                p.pot[g] = -s;
+            }
+        } else {
+            float vx = p.vel[3 * g + 0], vy = p.vel[3 * g + 1], vz = p.vel[3 * g + 2];
+            vx = fmaf(kick, ax_, vx);
+            vy = fmaf(kick, ay_, vy);
+            vz = fmaf(kick, az_, vz);
+            p.vel[3 * g + 0] = vx;
+            p.vel[3 * g + 1] = vy;
+            p.vel[3 * g + 2] = vz;
+            if (drift) {
+                p.pos[3 * g + 0] = fmaf(p.dt, vx, p.pos[3 * g + 0]);
+                p.pos[3 * g + 1] = fmaf(p.dt, vy, p.pos[3 * g + 1]);
+                p.pos[3 * g + 2] = fmaf(p.dt, vz, p.pos[3 * g + 2]);
+            }
+        }
+    }
+    (void)ev;
+}
+
+// Shared-memory image of system s: j-pairs, an odd count padded with a
+// massless body far away.
+__device__ __forceinline__ void load_system(float* sj, const BParams& p, int64_t off, int ns) {
+    const int nb = (ns + 1) & ~1;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        float x = kPadPos, y = kPadPos, z = kPadPos, m = 0.0f;
+        if (b < ns) {
+            const int64_t g = off + b;
+            x = p.pos[3 * g + 0];
+            y = p.pos[3 * g + 1];
+            z = p.pos[3 * g + 2];
+            m = p.mass[g];
+        }
+        float* d = sj + (b >> 1) * 8 + (b & 1);
+        d[0] = x;
+        d[2] = y;
+        d[4] = z;
+        d[6] = m;
+    }
+}
+
+template <int T, int I, bool POT>
+__global__ void __launch_bounds__(T) batched_kernel(const BParams p) {
+    extern __shared__ __align__(16) float sj[];
+    __shared__ int s_next;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(p.queue, 1);
+        __syncthreads();
+        const int k = s_next;
+        __syncthreads();
+        if (k >= p.nsys) break;
+        const int s = p.order[k];
+        const int64_t off = p.offsets[s];
+        const int ns = (int)(p.offsets[s + 1] - off);
+        if (ns <= 0) continue;
+        const float e = p.eps[s];
+        const float eps2s = e * e;
+        const f2 eps2 = pk(eps2s, eps2s);
+        const int npair = (ns + 1) >> 1;
+        load_system(sj, p, off, ns);
+        __syncthreads();
+        for (int64_t ev = 0; ev <= p.steps; ++ev) {
+            const float kick = (p.steps == 0) ? 0.0f : ((ev == 0 || ev == p.steps) ? 0.5f * p.dt : p.dt);
+            const bool drift = ev < p.steps;
+            for (int base = 0; base < ns; base += T * I) {
+                if (eps2s == 0.0f)
+                    eval_pass<T, I, POT, true>(sj, npair, ns, base, eps2, p, off, ev, kick, drift, eps2s);
+                else
+                    eval_pass<T, I, POT, false>(sj, npair, ns, base, eps2, p, off, ev, kick, drift, eps2s);
+            }
+            __syncthreads();
+            if (drift) {
+                load_system(sj, p, off, ns);  // the drifted positions of this step
+                __syncthreads();
+            }
+        }
+    }
+}
+
+typedef void (*BFn)(const BParams);
+struct BShapeEntry {
+    BatchShape shape;
+    BFn fn[2];  // [pot]
+};
+
+template <int T, int I>
+BShapeEntry make_bentry() {
+    BShapeEntry e;
+    e.shape = BatchShape{T, I};
+    e.fn[0] = batched_kernel<T, I, false>;
+    e.fn[1] = batched_kernel<T, I, true>;
+    return e;
+}
+
+const BShapeEntry* bshapes() {
+    static const BShapeEntry table[] = {
+        make_bentry<256, 2>(),  // 0
+        make_bentry<128, 4>(),  // 1
+        make_bentry<256, 4>(),  // 2
+        make_bentry<128, 2>(),  // 3
+    };
+    return table;
+}
+constexpr int kNumBShapes = 4;
+
+}  // namespace
+
+int batched_num_shapes() { return kNumBShapes; }
+BatchShape batched_shape(int k) { return bshapes()[k].shape; }
+
+size_t batched_smem_bytes(int max_ns) { return (size_t)((max_ns + 1) / 2) * 8 * sizeof(float); }
+
+cudaError_t batched_launch(int k, const BatchArgs& a, int num_sms, cudaStream_t st) {
+    const BShapeEntry& e = bshapes()[k];
+    const int pot = a.pot != nullptr ? 1 : 0;
+    const size_t smem = std::max<size_t>(batched_smem_bytes(a.max_ns), 16);
+    cudaError_t err = cudaFuncSetAttribute(e.fn[pot], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int occ = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, e.fn[pot], e.shape.threads, smem);
+    if (err != cudaSuccess) return err;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    BParams p;
+    p.nsys = a.nsys;
+    p.offsets = a.offsets;
+    p.order = a.order;
+    p.queue = a.queue;
+    p.pos = a.pos;
+    p.vel = a.vel;
+    p.mass = a.mass;
+    p.eps = a.eps;
+    p.acc = a.acc;
+    p.pot = a.pot;
+    p.dt = a.dt;
+    p.steps = a.steps;
+    const int64_t grid = std::min<int64_t>((int64_t)num_sms * occ, std::max<int64_t>(a.nsys, 1));
+    err = cudaMemsetAsync(a.queue, 0, sizeof(int), st);
+    if (err != cudaSuccess) return err;
+    e.fn[pot]<<<(unsigned)grid, e.shape.threads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace nbk

@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -112,7 +113,20 @@ struct Buf {
     size_t cap = 0;
 };
 
-enum BufId { B_JDUP, B_CENTRES, B_PARTIAL, B_ACC, B_POT, B_RED, B_OUT9, B_ERR, B_STAGE0, NBUF = B_STAGE0 + 8 };
+enum BufId {
+    B_JDUP,
+    B_CENTRES,
+    B_PARTIAL,
+    B_ACC,
+    B_POT,
+    B_RED,
+    B_OUT9,
+    B_ERR,
+    B_ORDER,
+    B_QUEUE,
+    B_STAGE0,
+    NBUF = B_STAGE0 + 8
+};
 
 struct Workspace {
     int device = 0;
@@ -223,15 +237,16 @@ struct Staging {
 // ---------------------------------------------------------------------------
 // Kernel-shape choice.
 // ---------------------------------------------------------------------------
-// Shape measured fastest on GB300 for each size class (plain/mixed alike):
-// with the potential the 2048-body blocks win, without it the 1024-body ones.
+// Shape measured fastest on GB300 for each size class (plain/mixed alike, with
+// or without the potential).
 int choose_shape(int64_t n, bool pot) {
     const char* env = getenv("NBODY_SHAPE");
     if (env != nullptr) {
         int k = atoi(env);
         if (k >= 0 && k < nbk::force_num_shapes()) return k;
     }
-    if (n >= (1 << 14)) return pot ? 0 : 1;
+    (void)pot;
+    if (n >= (1 << 14)) return 1;
     if (n >= (1 << 11)) return 3;
     return 4;
 }
@@ -504,6 +519,98 @@ int nbody_leapfrog_f32(int64_t n, float* pos, float* vel, const float* mass, flo
     count(1);
     NB_CUDA(nbk::kick_f32(n, v, a, 0.5f * dt, st));
     return sg.finish();
+}
+
+// Ragged batches: validate offsets and softenings on the host, order the
+// systems largest first, stage host arrays, one persistent launch.
+static int batched_common(int64_t nsys, const int64_t* offsets, float* pos, float* vel, const float* mass,
+                          const float* eps, float* acc, float* pot, float dt, int64_t steps, const nbody_opts* opts,
+                          bool leapfrog) {
+    if (nsys < 0 || steps < 0 || !isfinite(dt)) return NBODY_EINVAL;
+    if (nsys > 0 && (offsets == nullptr || pos == nullptr || mass == nullptr || eps == nullptr)) return NBODY_EINVAL;
+    if (nsys > 0 && leapfrog && vel == nullptr) return NBODY_EINVAL;
+    if (nsys > 0 && !leapfrog && acc == nullptr) return NBODY_EINVAL;
+    NB_CHECK(check_opts_only(opts));
+    if (opts != nullptr && opts->config >= nbk::batched_num_shapes()) return NBODY_EINVAL;
+    if (nsys == 0 || (leapfrog && steps == 0)) return NBODY_OK;
+    if (nsys > (int64_t)1 << 30) return NBODY_EINVAL;
+    Ctx c;
+    NB_CHECK(begin(opts, &c));
+    cudaStream_t st = c.o.stream;
+    // host copies of the offsets and softenings
+    std::vector<int64_t> off((size_t)nsys + 1);
+    std::vector<float> ep((size_t)nsys);
+    const bool off_host = is_host_ptr(offsets), eps_host = is_host_ptr(eps);
+    if (off_host) {
+        memcpy(off.data(), offsets, off.size() * sizeof(int64_t));
+    } else {
+        NB_CUDA(cudaMemcpyAsync(off.data(), offsets, off.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    }
+    if (eps_host) {
+        memcpy(ep.data(), eps, ep.size() * sizeof(float));
+    } else {
+        NB_CUDA(cudaMemcpyAsync(ep.data(), eps, ep.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
+    }
+    if (!off_host || !eps_host) NB_CUDA(cudaStreamSynchronize(st));
+    if (off[0] != 0) return NBODY_EINVAL;
+    int64_t max_ns = 0;
+    for (int64_t s = 0; s < nsys; ++s) {
+        const int64_t ns = off[s + 1] - off[s];
+        if (ns < 0 || ns > NBODY_BATCH_MAX_N) return NBODY_EINVAL;
+        if (!(isfinite(ep[s]) && ep[s] >= 0.0f)) return NBODY_EINVAL;
+        max_ns = ns > max_ns ? ns : max_ns;
+    }
+    const int64_t ntot = off[nsys];
+    if (ntot == 0) return NBODY_OK;
+    std::vector<int> order((size_t)nsys);
+    for (int64_t s = 0; s < nsys; ++s) order[s] = (int)s;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+
+    Staging sg(c.ws);
+    sg.add(offsets, off.size() * sizeof(int64_t), true, false);
+    sg.add(pos, (size_t)ntot * 3 * sizeof(float), true, leapfrog);
+    sg.add(vel, leapfrog ? (size_t)ntot * 3 * sizeof(float) : 0, leapfrog, leapfrog);
+    sg.add(mass, (size_t)ntot * sizeof(float), true, false);
+    sg.add(eps, ep.size() * sizeof(float), true, false);
+    sg.add(acc, leapfrog ? 0 : (size_t)ntot * 3 * sizeof(float), false, !leapfrog);
+    sg.add(pot, (leapfrog || pot == nullptr) ? 0 : (size_t)ntot * sizeof(float), false, !leapfrog);
+    NB_CHECK(sg.prepare());
+    void *po, *pq;
+    NB_CHECK(ensure(c.ws, B_ORDER, order.size() * sizeof(int), &po));
+    NB_CHECK(ensure(c.ws, B_QUEUE, sizeof(int), &pq));
+    NB_CUDA(cudaMemcpyAsync(po, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (fault("launch")) return NBODY_ECUDA;
+    nbk::BatchArgs a;
+    a.nsys = nsys;
+    a.offsets = (const int64_t*)sg.dev(0);
+    a.order = (const int*)po;
+    a.queue = (int*)pq;
+    a.pos = (float*)sg.dev(1);
+    a.vel = leapfrog ? (float*)sg.dev(2) : nullptr;
+    a.mass = (const float*)sg.dev(3);
+    a.eps = (const float*)sg.dev(4);
+    a.acc = leapfrog ? nullptr : (float*)sg.dev(5);
+    a.pot = (leapfrog || pot == nullptr) ? nullptr : (float*)sg.dev(6);
+    a.dt = dt;
+    a.steps = leapfrog ? steps : 0;
+    a.max_ns = (int)max_ns;
+    const int shape = c.o.config >= 0 ? c.o.config : 0;
+    count(1);
+    NB_CUDA(nbk::batched_launch(shape, a, c.sms, st));
+    // (a pageable-to-device copy has read `order` before cudaMemcpyAsync returns)
+    return sg.finish();
+}
+
+int nbody_accel_batched(int64_t nsys, const int64_t* offsets, const float* pos, const float* mass, const float* eps,
+                        float* acc, float* pot, const nbody_opts* opts) {
+    return batched_common(nsys, offsets, const_cast<float*>(pos), nullptr, mass, eps, acc, pot, 0.0f, 0, opts,
+                          false);
+}
+
+int nbody_leapfrog_batched(int64_t nsys, const int64_t* offsets, float* pos, float* vel, const float* mass,
+                           const float* eps, float dt, int64_t steps, const nbody_opts* opts) {
+    return batched_common(nsys, offsets, pos, vel, mass, eps, nullptr, nullptr, dt, steps, opts, true);
 }
 
 static int energy_common(int64_t n, const void* pos, const void* vel, const float* mass, double eps, double* out,

@@ -54,12 +54,12 @@ struct KParams {
 };
 
 // One j-tile against the thread's IP i-pairs.
-template <int T, int IP, int J, bool POT, bool DIAG>
+template <int T, int IP, int J, int UNROLL, bool POT, bool DIAG>
 __device__ __forceinline__ void tile_pass(const unsigned char* tile, const f2 (&xi)[IP], const f2 (&yi)[IP],
                                           const f2 (&zi)[IP], f2 eps2, f2 (&ax)[IP], f2 (&ay)[IP], f2 (&az)[IP],
                                           f2 (&ap)[IP], int jl0, int tid) {
     const ulonglong2* tj = reinterpret_cast<const ulonglong2*>(tile);
-#pragma unroll 2
+#pragma unroll UNROLL
     for (int j = 0; j < J; ++j) {
         const ulonglong2 A = tj[2 * j];
         const ulonglong2 B = tj[2 * j + 1];
@@ -100,8 +100,8 @@ __device__ __forceinline__ void kahan2(f2& sum, f2& comp, f2& part) {
     part = 0ull;
 }
 
-template <int T, int IP, int J, bool POT, bool MIXED, bool KAHAN>
-__global__ void __launch_bounds__(T) force_kernel(const KParams p) {
+template <int T, int IP, int J, int UNROLL, int MINB, bool POT, bool MIXED, bool KAHAN>
+__global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
     constexpr int C = 2 * IP * T;
     constexpr uint32_t TILE_BYTES = J * 32u;
     static_assert(C % J == 0, "a j-tile must not straddle two cells");
@@ -195,10 +195,10 @@ __global__ void __launch_bounds__(T) force_kernel(const KParams p) {
             }
             const unsigned char* tile = tiles + s * TILE_BYTES;
             if (cell == b) {
-                tile_pass<T, IP, J, POT, true>(tile, xi, yi, zi, eps2, ax, ay, az, ap,
+                tile_pass<T, IP, J, UNROLL, POT, true>(tile, xi, yi, zi, eps2, ax, ay, az, ap,
                                                (int)(tt * J - base), tid);
             } else {
-                tile_pass<T, IP, J, POT, false>(tile, xi, yi, zi, eps2, ax, ay, az, ap, 0, tid);
+                tile_pass<T, IP, J, UNROLL, POT, false>(tile, xi, yi, zi, eps2, ax, ay, az, ap, 0, tid);
             }
             if (KAHAN) {
 #pragma unroll
@@ -311,32 +311,57 @@ struct ShapeEntry {
     }
 };
 
-template <int T, int IP, int J>
+template <int T, int IP, int J, int UNROLL, int MINB>
 ShapeEntry make_entry() {
     ShapeEntry e;
     e.shape = ForceShape{T, IP, J, 2 * IP * T};
-    e.fn[0][0][0] = force_kernel<T, IP, J, false, false, false>;
-    e.fn[0][0][1] = force_kernel<T, IP, J, false, false, true>;
-    e.fn[0][1][0] = force_kernel<T, IP, J, false, true, false>;
-    e.fn[0][1][1] = force_kernel<T, IP, J, false, true, true>;
-    e.fn[1][0][0] = force_kernel<T, IP, J, true, false, false>;
-    e.fn[1][0][1] = force_kernel<T, IP, J, true, false, true>;
-    e.fn[1][1][0] = force_kernel<T, IP, J, true, true, false>;
-    e.fn[1][1][1] = force_kernel<T, IP, J, true, true, true>;
+    e.fn[0][0][0] = force_kernel<T, IP, J, UNROLL, MINB, false, false, false>;
+    e.fn[0][0][1] = force_kernel<T, IP, J, UNROLL, MINB, false, false, true>;
+    e.fn[0][1][0] = force_kernel<T, IP, J, UNROLL, MINB, false, true, false>;
+    e.fn[0][1][1] = force_kernel<T, IP, J, UNROLL, MINB, false, true, true>;
+    e.fn[1][0][0] = force_kernel<T, IP, J, UNROLL, MINB, true, false, false>;
+    e.fn[1][0][1] = force_kernel<T, IP, J, UNROLL, MINB, true, false, true>;
+    e.fn[1][1][0] = force_kernel<T, IP, J, UNROLL, MINB, true, true, false>;
+    e.fn[1][1][1] = force_kernel<T, IP, J, UNROLL, MINB, true, true, true>;
     return e;
 }
 
 const ShapeEntry* shapes() {
     static const ShapeEntry table[] = {
-        make_entry<256, 4, 256>(),  // 0: 2048-body blocks
-        make_entry<256, 2, 256>(),  // 1: 1024
-        make_entry<128, 4, 256>(),  // 2: 1024
-        make_entry<128, 2, 128>(),  // 3: 512
-        make_entry<128, 1, 64>(),   // 4: 256 (small n)
+        make_entry<256, 4, 256, 2, 0>(),  // 0: 2048-body blocks
+        make_entry<256, 2, 256, 4, 0>(),  // 1: 1024 (fastest at large n, with or without potential)
+        make_entry<512, 2, 256, 2, 0>(),  // 2: 2048
+        make_entry<128, 2, 128, 2, 0>(),  // 3: 512
+        make_entry<128, 1, 64, 2, 0>(),   // 4: 256 (small n)
+#ifdef NBODY_EXTRA_SHAPES
+        make_entry<256, 2, 256, 2, 0>(),  // 5
+        make_entry<256, 2, 256, 2, 3>(),  // 6
+        make_entry<256, 2, 256, 1, 0>(),  // 7
+        make_entry<512, 2, 256, 2, 0>(),  // 8
+        make_entry<128, 2, 256, 2, 0>(),  // 9
+        make_entry<256, 3, 256, 2, 0>(),  // 10
+        make_entry<384, 2, 256, 2, 0>(),  // 11
+        make_entry<256, 2, 512, 2, 0>(),  // 12
+        make_entry<256, 1, 256, 4, 0>(),  // 13
+        make_entry<256, 2, 128, 2, 0>(),  // 14
+        make_entry<256, 2, 256, 2, 2>(),  // 15
+        make_entry<256, 2, 256, 8, 0>(),  // 16
+        make_entry<512, 2, 256, 4, 0>(),  // 17
+        make_entry<256, 2, 512, 4, 0>(),  // 18
+        make_entry<256, 4, 256, 4, 0>(),  // 19
+        make_entry<256, 2, 256, 4, 2>(),  // 20
+        make_entry<128, 2, 128, 4, 0>(),  // 21
+        make_entry<128, 1, 64, 4, 0>(),   // 22
+        make_entry<64, 2, 128, 4, 0>(),   // 23
+#endif
     };
     return table;
 }
+#ifdef NBODY_EXTRA_SHAPES
+constexpr int kNumShapes = 24;
+#else
 constexpr int kNumShapes = 5;
+#endif
 
 // Resident CTAs per SM for each kernel variant, queried once.
 std::mutex g_occ_mu;

@@ -207,6 +207,31 @@ cudaError_t energy_reduce_f64(int64_t n, const double* vel, const float* mass, c
 cudaError_t energy_reduce_f32(int64_t n, const float* vel, const float* mass, const float* acc,
                               const float* pot, double* scratch, double* out9, cudaStream_t st);
 
+// ---- ragged batches (batched.cu) ----
+struct BatchShape {
+    int threads;  // threads per CTA
+    int ibodies;  // i-bodies per thread per pass
+};
+struct BatchArgs {
+    int64_t nsys;
+    const int64_t* offsets;  // device [nsys+1]
+    const int* order;        // device [nsys], largest system first
+    int* queue;              // device counter (zeroed by the launch)
+    float* pos;
+    float* vel;
+    const float* mass;
+    const float* eps;
+    float* acc;
+    float* pot;
+    float dt;
+    int64_t steps;  // 0: force only (acc, pot); > 0: leapfrog in place
+    int max_ns;     // largest system (sizes the shared-memory image)
+};
+int batched_num_shapes();
+BatchShape batched_shape(int k);
+size_t batched_smem_bytes(int max_ns);
+cudaError_t batched_launch(int k, const BatchArgs& a, int num_sms, cudaStream_t st);
+
 // One CTA waits on an mbarrier nothing completes, for limit_ns, then sets *err.
 cudaError_t selftest_wait(uint64_t limit_ns, int* err, cudaStream_t st);
 

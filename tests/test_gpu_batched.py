@@ -1,0 +1,154 @@
+"""Ragged batches (many independent systems in one persistent launch) against
+the FP64 oracle applied system by system."""
+import numpy as np
+import pytest
+
+import nbody_inputs as ni
+
+pytestmark = pytest.mark.gpu
+
+ACC_MED, ACC_MAX, POT_MAX = 2e-6, 1e-4, 1e-5
+
+
+def t(x, dtype):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=dtype)).cuda()
+
+
+def rel(a, ref):
+    if ref.ndim == 2:
+        return np.linalg.norm(np.asarray(a, np.float64) - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    return np.abs(np.asarray(a, np.float64) - ref) / np.abs(ref)
+
+
+def make_batch(sizes, seed, eps_rule="4/sqrt(n)"):
+    P, V, M, E = [], [], [], []
+    for s, n in enumerate(sizes):
+        p, v, m = ni.plummer(int(n), seed * 7919 + s, masses="loguniform" if s % 2 else "equal")
+        P.append(p); V.append(v); M.append(m)
+        E.append(4.0 / np.sqrt(max(n, 1)) if eps_rule == "4/sqrt(n)" else eps_rule)
+    off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)
+    cat = lambda L: np.concatenate(L) if L else np.zeros((0, 3))
+    pos = cat(P).astype(np.float32).astype(np.float64)
+    vel = cat(V).astype(np.float32).astype(np.float64)
+    mass = np.concatenate(M).astype(np.float32).astype(np.float64)
+    eps = np.asarray(E, dtype=np.float32).astype(np.float64)
+    return off, pos, vel, mass, eps
+
+
+def gpu_accel_batched(nb, off, pos, mass, eps, with_pot=True, **kw):
+    import torch
+    n = pos.shape[0]
+    acc = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    pot = torch.empty((n,), dtype=torch.float32, device="cuda") if with_pot else None
+    nb.nbody_accel_batched(t(off, np.int64), t(pos, np.float32), t(mass, np.float32), t(eps, np.float32), acc, pot,
+                           **kw)
+    torch.cuda.synchronize()
+    return acc.cpu().numpy(), (pot.cpu().numpy() if with_pot else None)
+
+
+SIZES = [1, 2, 3, 0, 63, 64, 65, 127, 511, 513, 1000, 2049, 4096, 5, 0, 777]
+
+
+@pytest.mark.parametrize("shape", range(4))
+def test_accel_batched_matches_oracle(nb, oracle_mod, shape):
+    off, pos, vel, mass, eps = make_batch(SIZES, 11 + shape)
+    acc, pot = gpu_accel_batched(nb, off, pos, mass, eps, config=shape)
+    for s in range(len(SIZES)):
+        a, b = off[s], off[s + 1]
+        if b - a == 0:
+            continue
+        ra, rp = oracle_mod.accel(pos[a:b], mass[a:b], eps[s])
+        if b - a == 1:
+            assert np.all(acc[a:b] == 0) and np.all(pot[a:b] == 0)
+            continue
+        e = rel(acc[a:b], ra)
+        assert np.median(e) <= ACC_MED and e.max() <= ACC_MAX, (s, b - a, np.median(e), e.max())
+        assert rel(pot[a:b], rp).max() <= POT_MAX, (s, b - a)
+
+
+def test_accel_batched_zero_softening(nb, oracle_mod):
+    off, pos, vel, mass, eps = make_batch([300, 1, 77, 1024], 21, eps_rule=0.0)
+    acc, pot = gpu_accel_batched(nb, off, pos, mass, eps)
+    for s in range(4):
+        a, b = off[s], off[s + 1]
+        ra, rp = oracle_mod.accel(pos[a:b], mass[a:b], 0.0)
+        if b - a == 1:
+            assert np.all(acc[a:b] == 0) and np.all(pot[a:b] == 0)
+            continue
+        e = rel(acc[a:b], ra)
+        assert np.all(np.isfinite(acc[a:b]))
+        assert np.median(e) <= 1e-5 and e.max() <= 1e-3
+        assert rel(pot[a:b], rp).max() <= 1e-4
+
+
+def test_leapfrog_batched_matches_oracle(nb, oracle_mod):
+    import torch
+    sizes = [64, 200, 1, 1024, 3000]
+    off, pos, vel, mass, eps = make_batch(sizes, 31)
+    P, V = t(pos, np.float32), t(vel, np.float32)
+    dt, steps = 2.0 ** -8, 16
+    nb.nbody_leapfrog_batched(t(off, np.int64), P, V, t(mass, np.float32), t(eps, np.float32), dt, steps)
+    torch.cuda.synchronize()
+    pg, vg = P.cpu().numpy().astype(np.float64), V.cpu().numpy().astype(np.float64)
+    for s in range(len(sizes)):
+        a, b = off[s], off[s + 1]
+        pr, vr, _ = oracle_mod.leapfrog(pos[a:b], vel[a:b], mass[a:b], eps[s], dt, steps)
+        assert np.abs(pg[a:b] - pr).max() <= 2e-5, s
+        assert np.abs(vg[a:b] - vr).max() <= 2e-4, s
+        if b - a > 1:
+            e0 = oracle_mod.energy(pos[a:b], vel[a:b], mass[a:b], eps[s])["E"]
+            er = oracle_mod.energy(pr, vr, mass[a:b], eps[s])["E"]
+            eg = oracle_mod.energy(pg[a:b], vg[a:b], mass[a:b], eps[s])["E"]
+            assert abs(eg - er) <= 1e-5 * abs(e0), s
+
+
+def test_batched_deterministic_and_host_arrays(nb):
+    off, pos, vel, mass, eps = make_batch([100, 2000, 3, 700], 41)
+    a1, p1 = gpu_accel_batched(nb, off, pos, mass, eps)
+    a2, p2 = gpu_accel_batched(nb, off, pos, mass, eps)
+    assert np.array_equal(a1, a2) and np.array_equal(p1, p2)
+    acc_h = np.zeros((pos.shape[0], 3), np.float32)
+    pot_h = np.zeros(pos.shape[0], np.float32)
+    nb.nbody_accel_batched(off, pos.astype(np.float32), mass.astype(np.float32), eps.astype(np.float32), acc_h, pot_h)
+    assert np.array_equal(acc_h, a1) and np.array_equal(pot_h, p1)
+
+
+def test_batched_rejects_bad_offsets(nb):
+    import torch
+    pos = torch.zeros((10, 3), dtype=torch.float32, device="cuda")
+    m = torch.ones(10, dtype=torch.float32, device="cuda")
+    acc = torch.empty((10, 3), dtype=torch.float32, device="cuda")
+    for off in ([1, 5, 10], [0, 6, 5], [0, 10]):
+        o = np.asarray(off, dtype=np.int64)
+        e = torch.full((len(off) - 1,), 0.1, dtype=torch.float32, device="cuda")
+        if off == [0, 10]:
+            e = torch.full((1,), -0.1, dtype=torch.float32, device="cuda")  # negative softening
+        with pytest.raises(nb.NbodyError) as ei:
+            nb.nbody_accel_batched(o, pos, m, e, acc)
+        assert ei.value.code == nb.NBODY_EINVAL
+
+
+def test_ragged_workload_sampled_systems(nb, oracle_mod):
+    """The ragged workload (4096 systems, N_s log-uniform in [64,4096],
+    eps_s = 4/sqrt(N_s), dt = 2^-8, 64 steps) in one launch; 32 seeded systems
+    checked against the oracle's leapfrog: energy to 1e-5 of |E0|."""
+    import torch
+    off, pos, vel, mass, eps = ni.ragged_batch()
+    nsys = len(off) - 1
+    P, V = t(pos, np.float32), t(vel, np.float32)
+    dt, steps = 2.0 ** -8, 64
+    nb.nbody_leapfrog_batched(t(off, np.int64), P, V, t(mass, np.float32), t(eps, np.float32), dt, steps)
+    torch.cuda.synchronize()
+    assert nb.nbody_last_device_error() == 0
+    pg, vg = P.cpu().numpy().astype(np.float64), V.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(pg))
+    for s in ni.subsample(nsys, 32, 404):
+        a, b = off[s], off[s + 1]
+        pr, vr, _ = oracle_mod.leapfrog(pos[a:b], vel[a:b], mass[a:b], eps[s], dt, steps)
+        e0 = oracle_mod.energy(pos[a:b], vel[a:b], mass[a:b], eps[s])["E"]
+        er = oracle_mod.energy(pr, vr, mass[a:b], eps[s])["E"]
+        eg = oracle_mod.energy(pg[a:b], vg[a:b], mass[a:b], eps[s])["E"]
+        assert abs(eg - er) <= 1e-5 * abs(e0), (s, b - a)
+        assert np.abs(pg[a:b] - pr).max() <= 1e-4, (s, b - a)
