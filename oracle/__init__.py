@@ -43,6 +43,8 @@ def _load():
         lib.oracle_accel_subset.argtypes = [i64, vp, vp, dbl, i64, vp, vp, vp]
         lib.oracle_leapfrog.argtypes = [i64, vp, vp, vp, dbl, dbl, i64, vp]
         lib.oracle_energy.argtypes = [i64, vp, vp, vp, dbl, vp]
+        lib.oracle_accel_vjp.argtypes = [i64, vp, vp, dbl, vp, vp, vp, vp]
+        lib.oracle_leapfrog_vjp.argtypes = [i64, vp, vp, vp, dbl, dbl, i64, vp, vp, vp, vp, vp]
         _lib = lib
     return _lib
 
@@ -113,3 +115,33 @@ def energy(pos, vel, mass, eps):
     out = np.zeros(9)
     _load().oracle_energy(n, _p(pos), _p(vel), _p(mass), float(eps), _p(out))
     return {"T": out[0], "W": out[1], "E": out[2], "P": out[3:6].copy(), "F": out[6:9].copy()}
+
+
+def accel_vjp(pos, mass, eps, lam, mu=None):
+    """Reverse mode of Eq. 1: (g_pos (n,3), g_mass (n,)) = gradients of
+    sum_i lam_i.a_i (+ mu_i phi_i) with respect to positions and masses."""
+    pos = _c(pos)
+    n = pos.shape[0]
+    mass = _c(mass, shape=(n,))
+    lam = _c(lam, shape=(n, 3))
+    mu = _c(mu, shape=(n,)) if mu is not None else None
+    g = np.zeros((n, 3))
+    gm = np.zeros(n)
+    _load().oracle_accel_vjp(n, _p(pos), _p(mass), float(eps), _p(lam), _p(mu), _p(g), _p(gm))
+    return g, gm
+
+
+def leapfrog_vjp(pos0, vel0, mass, eps, dt, steps, gx_T, gv_T):
+    """Reverse mode of ``leapfrog``: (dL/dx0, dL/dv0, dL/dm through the dynamics)."""
+    pos0 = _c(pos0)
+    n = pos0.shape[0]
+    vel0 = _c(vel0, shape=(n, 3))
+    mass = _c(mass, shape=(n,))
+    gx_T = _c(gx_T, shape=(n, 3))
+    gv_T = _c(gv_T, shape=(n, 3))
+    gx0 = np.zeros((n, 3))
+    gv0 = np.zeros((n, 3))
+    gm = np.zeros(n)
+    _load().oracle_leapfrog_vjp(n, _p(pos0), _p(vel0), _p(mass), float(eps), float(dt), int(steps), _p(gx_T),
+                                _p(gv_T), _p(gx0), _p(gv0), _p(gm))
+    return gx0, gv0, gm

@@ -23,6 +23,14 @@
  * The integrator, the energy and the adjoint are not in the paper; they follow
  * the kick-drift-kick leapfrog the library implements:
  *       v <- v + (dt/2) a(x);  x <- x + dt v;  v <- v + (dt/2) a(x)
+ *
+ * Adjoint (reverse-mode derivative) of the force and of the leapfrog: the
+ * chain rule applied to every pair term of Eq. 1.  A term
+ *       m_j f(d),  f(d) = d s^{-3/2},  d = r_j - r_i,  s = |d|^2 + eps^2
+ * has Jacobian  T(d) = s^{-3/2} I - 3 s^{-5/2} d d^T  with respect to d, so
+ * it moves with r_j through +m_j T(d), with r_i through -m_j T(d), and with
+ * m_j through f(d).  The potential term -m_j s^{-1/2} has gradient
+ * m_j s^{-3/2} d with respect to r_j (minus that for r_i) and -s^{-1/2} for m_j.
  */
 #include <math.h>
 #include <stdint.h>
@@ -138,4 +146,112 @@ void oracle_energy(int64_t n, const double* pos, const double* vel, const double
     out[8] = fz;
     free(a);
     free(phi);
+}
+
+/* T(d) = s^{-3/2} I - 3 s^{-5/2} d d^T for d with softening eps2. */
+static void pair_jacobian(const double d[3], double eps2, double T[3][3], double* s_m32, double* s_m12) {
+    const double s = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + eps2;
+    const double r = 1.0 / sqrt(s);
+    const double s32 = r * r * r;
+    const double s52 = s32 * r * r;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) T[a][b] = (a == b ? s32 : 0.0) - 3.0 * s52 * d[a] * d[b];
+    *s_m32 = s32;
+    *s_m12 = r;
+}
+
+/* Cotangents lam (n,3) of the accelerations and mu (n, or NULL) of the
+ * potentials: g_pos[k] = d(sum_i lam_i.a_i + mu_i phi_i)/d r_k and
+ * g_mass[k] = the same derivative with respect to m_k.  Gathered per k:
+ * body k enters the sums as the source of every pair (i, k), i != k, and as the
+ * sink of every pair (k, i). */
+void oracle_accel_vjp(int64_t n, const double* pos, const double* mass, double eps, const double* lam,
+                      const double* mu, double* g_pos, double* g_mass) {
+    const double eps2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t k = 0; k < n; ++k) {
+        double g[3] = {0.0, 0.0, 0.0}, gm = 0.0;
+        const double* lk = lam + 3 * k;
+        for (int64_t i = 0; i < n; ++i) {
+            if (i == k) continue;
+            const double* li = lam + 3 * i;
+            /* as the source of sink i: the term m_k f(r_k - r_i) of a_i */
+            const double d[3] = {pos[3 * k] - pos[3 * i], pos[3 * k + 1] - pos[3 * i + 1],
+                                 pos[3 * k + 2] - pos[3 * i + 2]};
+            double T[3][3], s32, s12;
+            pair_jacobian(d, eps2, T, &s32, &s12);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) g[a] += mass[k] * T[a][b] * li[b];
+            gm += (li[0] * d[0] + li[1] * d[1] + li[2] * d[2]) * s32;
+            /* as the sink of source i: the term m_i f(r_i - r_k) of a_k, T(-d) = T(d) */
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) g[a] -= mass[i] * T[a][b] * lk[b];
+            if (mu) {
+                /* -m_k s^{-1/2} in phi_i and -m_i s^{-1/2} in phi_k */
+                for (int a = 0; a < 3; ++a) g[a] += s32 * d[a] * (mu[i] * mass[k] + mu[k] * mass[i]);
+                gm -= mu[i] * s12;
+            }
+        }
+        g_pos[3 * k + 0] = g[0];
+        g_pos[3 * k + 1] = g[1];
+        g_pos[3 * k + 2] = g[2];
+        g_mass[k] = gm;
+    }
+}
+
+/* Reverse mode of oracle_leapfrog: given gx_T = dL/dx(T) and gv_T = dL/dv(T),
+ * returns dL/dx(0), dL/dv(0) and the dynamics' part of dL/dm (a loss that also
+ * depends on m directly adds its own term).  The forward trajectory is kept in
+ * full and every half kick is undone by its own force adjoint. */
+void oracle_leapfrog_vjp(int64_t n, const double* pos0, const double* vel0, const double* mass, double eps,
+                         double dt, int64_t steps, const double* gx_T, const double* gv_T, double* gx0,
+                         double* gv0, double* gm) {
+    const size_t n3 = 3 * (size_t)(n > 0 ? n : 1);
+    double* X = (double*)malloc(sizeof(double) * n3 * (size_t)(steps + 1));
+    double* x = (double*)malloc(sizeof(double) * n3);
+    double* v = (double*)malloc(sizeof(double) * n3);
+    double* a = (double*)malloc(sizeof(double) * n3);
+    double* lv = (double*)malloc(sizeof(double) * n3);
+    double* gxk = (double*)malloc(sizeof(double) * n3);
+    double* gmk = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    const double h = 0.5 * dt;
+    memcpy(x, pos0, sizeof(double) * 3 * (size_t)n);
+    memcpy(v, vel0, sizeof(double) * 3 * (size_t)n);
+    memcpy(X, x, sizeof(double) * 3 * (size_t)n);
+    oracle_accel(n, x, mass, eps, a, NULL);
+    for (int64_t s = 0; s < steps; ++s) {
+        for (int64_t k = 0; k < 3 * n; ++k) v[k] += h * a[k];
+        for (int64_t k = 0; k < 3 * n; ++k) x[k] += dt * v[k];
+        oracle_accel(n, x, mass, eps, a, NULL);
+        for (int64_t k = 0; k < 3 * n; ++k) v[k] += h * a[k];
+        memcpy(X + n3 * (size_t)(s + 1), x, sizeof(double) * 3 * (size_t)n);
+    }
+    /* reverse sweep: (gx0, lv) hold dL/dx and dL/dv of the current state */
+    memcpy(gx0, gx_T, sizeof(double) * 3 * (size_t)n);
+    memcpy(lv, gv_T, sizeof(double) * 3 * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) gm[i] = 0.0;
+    for (int64_t s = steps - 1; s >= 0; --s) {
+        const double* x1 = X + n3 * (size_t)(s + 1);
+        const double* x0 = X + n3 * (size_t)s;
+        /* v_{s+1} = v_half + h a(x_{s+1}) */
+        for (int64_t k = 0; k < 3 * n; ++k) a[k] = h * lv[k];
+        oracle_accel_vjp(n, x1, mass, eps, a, NULL, gxk, gmk);
+        for (int64_t k = 0; k < 3 * n; ++k) gx0[k] += gxk[k];
+        for (int64_t i = 0; i < n; ++i) gm[i] += gmk[i];
+        /* x_{s+1} = x_s + dt v_half */
+        for (int64_t k = 0; k < 3 * n; ++k) lv[k] += dt * gx0[k];
+        /* v_half = v_s + h a(x_s) */
+        for (int64_t k = 0; k < 3 * n; ++k) a[k] = h * lv[k];
+        oracle_accel_vjp(n, x0, mass, eps, a, NULL, gxk, gmk);
+        for (int64_t k = 0; k < 3 * n; ++k) gx0[k] += gxk[k];
+        for (int64_t i = 0; i < n; ++i) gm[i] += gmk[i];
+    }
+    memcpy(gv0, lv, sizeof(double) * 3 * (size_t)n);
+    free(X);
+    free(x);
+    free(v);
+    free(a);
+    free(lv);
+    free(gxk);
+    free(gmk);
 }

@@ -2,7 +2,8 @@
 
 Each case copies oracle.c to a temporary directory, plants one mistake in the
 copy (on the CPU, never in the committed file), rebuilds it and runs the pin
-tests against the mutant; every mutant must fail at least one pin.
+tests (forward, integrator and adjoint) against the mutant; every mutant must
+fail at least one pin.
 """
 import os
 import shutil
@@ -19,10 +20,16 @@ MUTANTS = {
     "potential_sign": ("p -= mass[j] * rinv;", "p += mass[j] * rinv;"),
     "transposed_coordinate": ("pos[3 * j + 1] - yi", "pos[3 * j + 0] - yi"),
     "softening_dropped": ("+ dz * dz + eps2", "+ dz * dz"),
-    "full_kick_instead_of_half": ("const double h = 0.5 * dt;", "const double h = dt;"),
+    "full_kick_instead_of_half": ("oracle_accel(n, pos, mass, eps, a, NULL);\n    const double h = 0.5 * dt;",
+                                  "oracle_accel(n, pos, mass, eps, a, NULL);\n    const double h = dt;"),
     "sink_mass_instead_of_source": ("const double w = mass[j] *", "const double w = mass[i] *"),
     "drift_uses_old_velocity_sign": ("pos[k] += dt * vel[k];", "pos[k] -= dt * vel[k];"),
     "energy_half_missing": ("w += 0.5 * mass[i] * phi[i];", "w += mass[i] * phi[i];"),
+    "vjp_tidal_factor_3_dropped": ("- 3.0 * s52 * d[a] * d[b]", "- s52 * d[a] * d[b]"),
+    "vjp_sink_term_dropped": ("g[a] -= mass[i] * T[a][b] * lk[b];", "g[a] -= 0.0 * lk[b];"),
+    "vjp_mass_gradient_sign": ("gm += (li[0] * d[0]", "gm -= (li[0] * d[0]"),
+    "vjp_potential_masses_swapped": ("(mu[i] * mass[k] + mu[k] * mass[i])", "(mu[k] * mass[k] + mu[i] * mass[i])"),
+    "adjoint_drift_uses_half_step": ("lv[k] += dt * gx0[k];", "lv[k] += h * gx0[k];"),
 }
 
 
@@ -37,9 +44,10 @@ def test_mutant_is_caught(tmp_path, name):
     shutil.copytree(os.path.join(ROOT, "nbody_inputs"), tmp_path / "nbody_inputs",
                     ignore=shutil.ignore_patterns("__pycache__"))
     os.makedirs(tmp_path / "tests")
-    for f in ("conftest.py", "test_oracle_pins.py", "test_oracle_integrator.py"):
+    for f in ("conftest.py", "test_oracle_pins.py", "test_oracle_integrator.py", "test_oracle_adjoint.py"):
         shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        "tests/test_oracle_pins.py", "tests/test_oracle_integrator.py"],
+                        "tests/test_oracle_pins.py", "tests/test_oracle_integrator.py",
+                        "tests/test_oracle_adjoint.py"],
                        cwd=tmp_path, capture_output=True, text=True, timeout=300)
     assert r.returncode == 1, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
