@@ -260,6 +260,49 @@ def batched_leg(nb, dev, sms, peak_int_s, args):
             "per_system_launches": int(len(sizes) * (3 * (steps + 1) + 1))}
 
 
+def adjoint_leg(nb, dev, args):
+    """Adjoint workload: N = 16384 Plummer, eps = 2^-7, dt = 2^-8, K = 64 KDK
+    steps, checkpoints every 8 steps.  Forward = nbody_leapfrog_record (the run
+    that produces x(T) and the tape); gradient = nbody_leapfrog_vjp (replay of
+    each segment from its checkpoint + one force VJP per force evaluation)."""
+    import torch
+    import nbody_inputs as ni
+    w = ni.adjoint_case()
+    n, K, ckpt = w.n, w.steps, w.extra["ckpt_every"]
+    M = torch.from_numpy(w.mass.astype(np.float32)).to(dev)
+    y = torch.from_numpy(w.extra["target"]).to(dev)
+    tape = torch.empty(nb.nbody_tape_bytes(n, K, ckpt), dtype=torch.uint8, device=dev)
+    gx0 = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    gv0 = torch.empty_like(gx0)
+    gm = torch.empty((n,), dtype=torch.float64, device=dev)
+    zero = torch.zeros_like(gx0)
+    fw, bw = [], []
+    for it in range(1 + max(1, min(args.steps, 3))):
+        P = torch.from_numpy(w.pos).to(dev)
+        V = torch.from_numpy(w.vel).to(dev)
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        nb.nbody_leapfrog_record(P, V, M, w.eps, w.dt, K, ckpt, tape)
+        e1.record()
+        gxT = 2.0 * M.double()[:, None] * (P - y)
+        torch.cuda.synchronize()
+        e1b = torch.cuda.Event(enable_timing=True)
+        e1b.record()
+        nb.nbody_leapfrog_vjp(M, w.eps, w.dt, K, ckpt, tape, gxT, zero, gx0, gv0, gm)
+        e2.record()
+        torch.cuda.synchronize()
+        if it > 0:
+            fw.append(e0.elapsed_time(e1) / 1e3)
+            bw.append(e1b.elapsed_time(e2) / 1e3)
+    f, g = statistics.median(fw), statistics.median(bw)
+    inter = (K + 1) * n * n
+    return {"workload": "plummer_n16384_eps2^-7_kdk64_dt2^-8_ckpt8_loss_sum_m_x_minus_y_sq",
+            "forward_ms": f * 1e3, "gradient_ms": g * 1e3, "adjoint_to_forward": g / f,
+            "forward_gints": inter / f / 1e9,
+            "note": "gradient = replay of 48 force evaluations from 8 checkpoints + 65 force VJPs"}
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -381,6 +424,7 @@ def main():
         roofline["frac_at_measured_clock"] = achieved_tflops / (peak_tflops * clocks["sm_mhz"] / SM_MAX_MHZ_DEFAULT)
 
     batched = batched_leg(nb, dev, sms, peak_int_s, args)
+    adjoint = adjoint_leg(nb, dev, args)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -396,7 +440,7 @@ def main():
         "plain": {"value": plain_value, "unit": UNIT, "pct_fp32_peak": plain_value * 1e9 / peak_int_s * 100,
                   "precision": "FP32 absolute coordinates (fails the accuracy target at this offset by design)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "batched": batched,
+        "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "batched": batched, "adjoint": adjoint,
         "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
         "wall_s_timed_region": wall_s, "step_ms": [s * 1e3 for s in per_step],
     }

@@ -143,6 +143,45 @@ int nbody_accel_batched(int64_t nsys, const int64_t* offsets, const float* pos, 
 int nbody_leapfrog_batched(int64_t nsys, const int64_t* offsets, float* pos, float* vel, const float* mass,
                            const float* eps, float dt, int64_t steps, const nbody_opts* opts);
 
+/*
+ * Reverse mode of Eq. 1 (not in the paper; the derivative of the force it
+ * defines).  For cotangents g_acc of the accelerations and g_pot of the
+ * potentials (NULL = none), with d = r_j - r_k, s = |d|^2 + eps^2 and the tidal
+ * tensor T(d) = s^{-3/2} I - 3 s^{-5/2} d d^T:
+ *   g_pos[k]  = sum_{j != k} T(d) (m_k g_acc[j] - m_j g_acc[k])
+ *               - sum_{j != k} s^{-3/2} d (g_pot[j] m_k + g_pot[k] m_j)
+ *   g_mass[k] = -sum_{j != k} [ s^{-3/2} (g_acc[j] . d) + g_pot[j] s^{-1/2} ]
+ * i.e. the gradients of sum_i g_acc[i].a_i + g_pot[i] phi_i.  A second
+ * all-pairs pass (30 FP32 operations per pair); mixed precision as nbody_accel.
+ *  pos [n][3] double, mass [n] float, g_acc [n][3] float, g_pot [n] float or
+ *  NULL; g_pos [n][3] float and g_mass [n] float are overwritten.
+ * opts->config selects the VJP kernel shape (0 .. 3), -1 = default.
+ */
+int nbody_accel_vjp(int64_t n, const double* pos, const float* mass, double eps, const float* g_acc,
+                    const float* g_pot, float* g_pos, float* g_mass, const nbody_opts* opts);
+
+/*
+ * Differentiating a leapfrog trajectory, checkpointed:
+ * nbody_leapfrog_record runs nbody_leapfrog (FP64 state, in place) and writes
+ * a tape: for every checkpoint step k = 0, c, 2c, ... < steps (c = ckpt_every)
+ * the positions x_k and half-step velocities v_{k+1/2}, then x_steps
+ * (nbody_tape_bytes(n, steps, c) bytes of device memory, caller-owned).
+ * nbody_leapfrog_vjp then returns, for cotangents g_posT = dL/dx(T) and
+ * g_velT = dL/dv(T), the gradients dL/dx(0), dL/dv(0) and the dynamics' part
+ * of dL/dm (FP64).  It is the exact discrete adjoint of the recorded steps:
+ * the sweep runs newest segment first, replays each segment's positions from
+ * its checkpoint (the same kernels, so the same bits), and applies one force
+ * VJP per force evaluation of the forward run.  The tape and mass must be
+ * device memory; the cotangent and gradient arrays may be host or device.
+ * nbody_tape_bytes returns -1 for invalid sizes.
+ */
+int64_t nbody_tape_bytes(int64_t n, int64_t steps, int64_t ckpt_every);
+int nbody_leapfrog_record(int64_t n, double* pos, double* vel, const float* mass, double eps, double dt,
+                          int64_t steps, int64_t ckpt_every, void* tape, const nbody_opts* opts);
+int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, double dt, int64_t steps, int64_t ckpt_every,
+                       const void* tape, const double* g_posT, const double* g_velT, double* g_pos0, double* g_vel0,
+                       double* g_mass, const nbody_opts* opts);
+
 /* Number of force-kernel shapes compiled in (for opts->config) and the
  * bodies per i-block of shape k (0 if k is out of range). */
 int nbody_num_configs(void);

@@ -50,6 +50,10 @@ SIGNATURES = {
     "nbody_energy_f32": (_int, [_i64, _vp, _vp, _vp, _flt, _vp, _OPTS]),
     "nbody_accel_batched": (_int, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _OPTS]),
     "nbody_leapfrog_batched": (_int, [_i64, _vp, _vp, _vp, _vp, _vp, _flt, _i64, _OPTS]),
+    "nbody_accel_vjp": (_int, [_i64, _vp, _vp, _dbl, _vp, _vp, _vp, _vp, _OPTS]),
+    "nbody_tape_bytes": (_i64, [_i64, _i64, _i64]),
+    "nbody_leapfrog_record": (_int, [_i64, _vp, _vp, _vp, _dbl, _dbl, _i64, _i64, _vp, _OPTS]),
+    "nbody_leapfrog_vjp": (_int, [_i64, _vp, _dbl, _dbl, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _OPTS]),
     "nbody_num_configs": (_int, []),
     "nbody_config_block": (_int, [_int]),
     "nbody_last_device_error": (_int, []),

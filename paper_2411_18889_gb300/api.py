@@ -145,6 +145,57 @@ def nbody_leapfrog_batched(offsets, pos, vel, mass, eps, dt, steps, **kw):
           "nbody_leapfrog_batched")
 
 
+def nbody_accel_vjp(pos, mass, eps, g_acc, g_pot, g_pos, g_mass, **kw):
+    """nbody_accel_vjp: pos (n,3) f64, mass (n,) f32, g_acc (n,3) f32, g_pot (n,) f32 or None;
+    g_pos (n,3) f32 and g_mass (n,) f32 are overwritten."""
+    n = _n(pos)
+    o = make_opts((pos, mass, g_acc, g_pos), **kw)
+    check(load().nbody_accel_vjp(n, _ptr(pos, "f64", (n, 3), "pos"), _ptr(mass, "f32", (n,), "mass"), float(eps),
+                                 _ptr(g_acc, "f32", (n, 3), "g_acc"), _ptr(g_pot, "f32", (n,), "g_pot"),
+                                 _ptr(g_pos, "f32", (n, 3), "g_pos"), _ptr(g_mass, "f32", (n,), "g_mass"),
+                                 ctypes.byref(o)),
+          "nbody_accel_vjp")
+
+
+def nbody_tape_bytes(n, steps, ckpt_every):
+    b = int(load().nbody_tape_bytes(int(n), int(steps), int(ckpt_every)))
+    if b < 0:
+        raise ValueError("invalid tape size arguments")
+    return b
+
+
+def _tape_ptr(tape):
+    if not (_is_torch(tape) and tape.is_cuda and tape.is_contiguous()):
+        raise TypeError("tape: expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(tape.data_ptr())
+
+
+def nbody_leapfrog_record(pos, vel, mass, eps, dt, steps, ckpt_every, tape, **kw):
+    """nbody_leapfrog_record: pos, vel (n,3) f64 on the device, in place; tape: CUDA byte tensor of
+    nbody_tape_bytes(n, steps, ckpt_every) bytes."""
+    n = _n(pos)
+    if tape.numel() * tape.element_size() < nbody_tape_bytes(n, steps, ckpt_every):
+        raise ValueError("tape too small")
+    o = make_opts((pos, vel, mass), **kw)
+    check(load().nbody_leapfrog_record(n, _ptr(pos, "f64", (n, 3), "pos"), _ptr(vel, "f64", (n, 3), "vel"),
+                                       _ptr(mass, "f32", (n,), "mass"), float(eps), float(dt), int(steps),
+                                       int(ckpt_every), _tape_ptr(tape), ctypes.byref(o)),
+          "nbody_leapfrog_record")
+
+
+def nbody_leapfrog_vjp(mass, eps, dt, steps, ckpt_every, tape, g_posT, g_velT, g_pos0, g_vel0, g_mass, **kw):
+    """nbody_leapfrog_vjp: cotangents g_posT, g_velT (n,3) f64; outputs g_pos0, g_vel0 (n,3) f64 and
+    g_mass (n,) f64 (the dynamics' part of dL/dm)."""
+    n = int(mass.shape[0])
+    o = make_opts((mass, g_posT, g_pos0), **kw)
+    check(load().nbody_leapfrog_vjp(n, _ptr(mass, "f32", (n,), "mass"), float(eps), float(dt), int(steps),
+                                    int(ckpt_every), _tape_ptr(tape), _ptr(g_posT, "f64", (n, 3), "g_posT"),
+                                    _ptr(g_velT, "f64", (n, 3), "g_velT"), _ptr(g_pos0, "f64", (n, 3), "g_pos0"),
+                                    _ptr(g_vel0, "f64", (n, 3), "g_vel0"), _ptr(g_mass, "f64", (n,), "g_mass"),
+                                    ctypes.byref(o)),
+          "nbody_leapfrog_vjp")
+
+
 def _energy(fn, name, dt, pos, vel, mass, eps, **kw):
     n = _n(pos)
     o = make_opts((pos, vel, mass), **kw)

@@ -124,6 +124,13 @@ enum BufId {
     B_ERR,
     B_ORDER,
     B_QUEUE,
+    B_VJ,
+    B_VCENTRES,
+    B_VPARTIAL,
+    B_VG,
+    B_VGM,
+    B_SEGX,
+    B_SEGV,
     B_STAGE0,
     NBUF = B_STAGE0 + 8
 };
@@ -518,6 +525,236 @@ int nbody_leapfrog_f32(int64_t n, float* pos, float* vel, const float* mass, flo
     }
     count(1);
     NB_CUDA(nbk::kick_f32(n, v, a, 0.5f * dt, st));
+    return sg.finish();
+}
+
+// ---------------------------------------------------------------------------
+// Reverse mode
+// ---------------------------------------------------------------------------
+static int choose_vjp_shape(int64_t n) {
+    if (n >= (1 << 14)) return 0;
+    if (n >= (1 << 11)) return 1;
+    return 3;
+}
+
+struct VjpPlan {
+    int shape, block;
+    int64_t npad;
+    float* jv;
+    double* centres;
+    double* partial;
+    int* err;
+};
+
+static int plan_vjp(Workspace* ws, int64_t n, int shape, int num_sms, VjpPlan* vp) {
+    vp->shape = shape;
+    vp->block = nbk::vjp_shape(shape).block;
+    const int64_t nblk = (n + vp->block - 1) / vp->block;
+    vp->npad = nblk * vp->block;
+    void* p;
+    NB_CHECK(ensure(ws, B_VJ, (size_t)vp->npad * nbk::vjp_floats_per_body() * sizeof(float), &p));
+    vp->jv = (float*)p;
+    NB_CHECK(ensure(ws, B_VCENTRES, (size_t)nblk * 3 * sizeof(double), &p));
+    vp->centres = (double*)p;
+    NB_CHECK(ensure(ws, B_VPARTIAL, nbk::vjp_partial_doubles(shape, num_sms) * sizeof(double), &p));
+    vp->partial = (double*)p;
+    NB_CHECK(ensure(ws, B_ERR, sizeof(int), &p));
+    vp->err = (int*)p;
+    return NBODY_OK;
+}
+
+static int run_vjp(const VjpPlan& vp, int64_t n, float eps2, bool mixed, bool has_mu, float* g_pos, float* g_mass,
+            int num_sms, cudaStream_t st) {
+    if (fault("launch")) return NBODY_ECUDA;
+    nbk::VjpArgs a;
+    a.jv = vp.jv;
+    a.centres = mixed ? vp.centres : nullptr;
+    a.eps2 = eps2;
+    a.n = n;
+    a.npad = vp.npad;
+    a.has_mu = has_mu;
+    a.g_pos = g_pos;
+    a.g_mass = g_mass;
+    a.partial = vp.partial;
+    a.err = vp.err;
+    int launched = 0;
+    cudaError_t e = nbk::vjp_launch(vp.shape, a, num_sms, st, &launched);
+    count(launched);
+    NB_CUDA(e);
+    return NBODY_OK;
+}
+
+int nbody_accel_vjp(int64_t n, const double* pos, const float* mass, double eps, const float* g_acc,
+                    const float* g_pot, float* g_pos, float* g_mass, const nbody_opts* opts) {
+    if (n < 0 || !finite_nonneg(eps)) return NBODY_EINVAL;
+    if (n > 0 && (pos == nullptr || mass == nullptr || g_acc == nullptr || g_pos == nullptr || g_mass == nullptr))
+        return NBODY_EINVAL;
+    NB_CHECK(check_opts_only(opts));
+    if (opts != nullptr && opts->config >= nbk::vjp_num_shapes()) return NBODY_EINVAL;
+    if (n == 0) return NBODY_OK;
+    Ctx c;
+    NB_CHECK(begin(opts, &c));
+    Staging sg(c.ws);
+    sg.add(pos, (size_t)n * 3 * sizeof(double), true, false);
+    sg.add(mass, (size_t)n * sizeof(float), true, false);
+    sg.add(g_acc, (size_t)n * 3 * sizeof(float), true, false);
+    sg.add(g_pot, (size_t)n * sizeof(float), true, false);
+    sg.add(g_pos, (size_t)n * 3 * sizeof(float), false, true);
+    sg.add(g_mass, (size_t)n * sizeof(float), false, true);
+    NB_CHECK(sg.prepare());
+    VjpPlan vp;
+    NB_CHECK(plan_vjp(c.ws, n, c.o.config >= 0 ? c.o.config : choose_vjp_shape(n), c.sms, &vp));
+    const bool plain = c.o.precision == NBODY_PREC_PLAIN;
+    count(1);
+    NB_CUDA(nbk::pack_vjp(n, vp.npad, vp.block, (const double*)sg.dev(0), (const float*)sg.dev(1),
+                          (const float*)sg.dev(2), nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, 1.0,
+                          g_pot ? (const float*)sg.dev(3) : nullptr, plain, vp.jv, vp.centres, c.o.stream));
+    NB_CHECK(run_vjp(vp, n, (float)(eps * eps), !plain, g_pot != nullptr, (float*)sg.dev(4), (float*)sg.dev(5), c.sms,
+                     c.o.stream));
+    return sg.finish();
+}
+
+// Tape of a recorded leapfrog: for each checkpoint k = 0, c, 2c, ... < steps the
+// positions x_k and the half-step velocity v_{k+1/2} (FP64 [n][3] each), then
+// the final positions x_steps.
+int64_t nbody_tape_bytes(int64_t n, int64_t steps, int64_t ckpt_every) {
+    if (n < 0 || steps < 0 || ckpt_every < 1) return -1;
+    const int64_t nck = (steps + ckpt_every - 1) / ckpt_every;
+    return (nck * 2 + 1) * n * 3 * (int64_t)sizeof(double);
+}
+
+static bool device_only(const void* p) { return p != nullptr && !is_host_ptr(p); }
+
+int nbody_leapfrog_record(int64_t n, double* pos, double* vel, const float* mass, double eps, double dt,
+                          int64_t steps, int64_t ckpt_every, void* tape, const nbody_opts* opts) {
+    if (n < 0 || steps < 0 || ckpt_every < 1 || !finite_nonneg(eps) || !isfinite(dt)) return NBODY_EINVAL;
+    if (n > 0 && (pos == nullptr || vel == nullptr || mass == nullptr || tape == nullptr)) return NBODY_EINVAL;
+    NB_CHECK(check_opts_only(opts));
+    if (n == 0) return NBODY_OK;
+    Ctx c;
+    NB_CHECK(begin(opts, &c));
+    if (!device_only(pos) || !device_only(vel) || !device_only(mass) || !device_only(tape)) return NBODY_EINVAL;
+    cudaStream_t st = c.o.stream;
+    const size_t n3b = (size_t)n * 3 * sizeof(double);
+    double* tp = (double*)tape;
+    const int64_t nck = (steps + ckpt_every - 1) / ckpt_every;
+    double* xK = tp + (size_t)nck * 2 * n * 3;
+    if (steps == 0) {
+        NB_CUDA(cudaMemcpyAsync(xK, pos, n3b, cudaMemcpyDeviceToDevice, st));
+        return NBODY_OK;
+    }
+    ForcePlan fp;
+    NB_CHECK(plan_force(c.ws, n, shape_for(c, n, false), c.sms, &fp));
+    void* p;
+    NB_CHECK(ensure(c.ws, B_ACC, (size_t)n * 3 * sizeof(float), &p));
+    float* a = (float*)p;
+    const bool plain = c.o.precision == NBODY_PREC_PLAIN;
+    const bool comp = c.o.accumulate == NBODY_ACC_COMPENSATED;
+    const float eps2 = (float)(eps * eps);
+    count(1);
+    NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, pos, nullptr, nullptr, mass, 0.0, 0.0, plain, fp.jdup, fp.centres,
+                          st));
+    NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, st));
+    for (int64_t s = 0; s < steps; ++s) {
+        const bool ck = (s % ckpt_every) == 0;
+        double* slot = tp + (size_t)(s / ckpt_every) * 2 * n * 3;
+        if (ck) NB_CUDA(cudaMemcpyAsync(slot, pos, n3b, cudaMemcpyDeviceToDevice, st));
+        const double kick = (s == 0) ? 0.5 * dt : dt;
+        count(1);
+        NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, pos, vel, a, mass, kick, dt, plain, fp.jdup, fp.centres, st));
+        if (ck) NB_CUDA(cudaMemcpyAsync(slot + (size_t)n * 3, vel, n3b, cudaMemcpyDeviceToDevice, st));
+        NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, st));
+    }
+    count(1);
+    NB_CUDA(nbk::kick_f64(n, vel, a, 0.5 * dt, st));
+    NB_CUDA(cudaMemcpyAsync(xK, pos, n3b, cudaMemcpyDeviceToDevice, st));
+    return NBODY_OK;
+}
+
+int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, double dt, int64_t steps, int64_t ckpt_every,
+                       const void* tape, const double* g_posT, const double* g_velT, double* g_pos0, double* g_vel0,
+                       double* g_mass, const nbody_opts* opts) {
+    if (n < 0 || steps < 0 || ckpt_every < 1 || !finite_nonneg(eps) || !isfinite(dt)) return NBODY_EINVAL;
+    if (n > 0 && (mass == nullptr || tape == nullptr || g_posT == nullptr || g_velT == nullptr ||
+                  g_pos0 == nullptr || g_vel0 == nullptr || g_mass == nullptr))
+        return NBODY_EINVAL;
+    NB_CHECK(check_opts_only(opts));
+    if (n == 0) return NBODY_OK;
+    Ctx c;
+    NB_CHECK(begin(opts, &c));
+    if (!device_only(tape) || !device_only(mass)) return NBODY_EINVAL;
+    cudaStream_t st = c.o.stream;
+    const size_t n3b = (size_t)n * 3 * sizeof(double);
+    Staging sg(c.ws);
+    sg.add(g_posT, n3b, true, false);
+    sg.add(g_velT, n3b, true, false);
+    sg.add(g_pos0, n3b, false, true);
+    sg.add(g_vel0, n3b, false, true);
+    sg.add(g_mass, (size_t)n * sizeof(double), false, true);
+    NB_CHECK(sg.prepare());
+    double* lamx = (double*)sg.dev(2);
+    double* lamv = (double*)sg.dev(3);
+    double* gm_acc = (double*)sg.dev(4);
+    NB_CUDA(cudaMemcpyAsync(lamx, sg.dev(0), n3b, cudaMemcpyDeviceToDevice, st));
+    NB_CUDA(cudaMemcpyAsync(lamv, sg.dev(1), n3b, cudaMemcpyDeviceToDevice, st));
+    NB_CUDA(cudaMemsetAsync(gm_acc, 0, (size_t)n * sizeof(double), st));
+    if (steps == 0) return sg.finish();
+
+    const bool plain = c.o.precision == NBODY_PREC_PLAIN;
+    const bool comp = c.o.accumulate == NBODY_ACC_COMPENSATED;
+    const float eps2 = (float)(eps * eps);
+    const double h = 0.5 * dt;
+    const double* tp = (const double*)tape;
+    const int64_t nck = (steps + ckpt_every - 1) / ckpt_every;
+    const double* xK = tp + (size_t)nck * 2 * n * 3;
+    VjpPlan vp;
+    NB_CHECK(plan_vjp(c.ws, n, choose_vjp_shape(n), c.sms, &vp));
+    ForcePlan fp;
+    NB_CHECK(plan_force(c.ws, n, shape_for(c, n, false), c.sms, &fp));
+    void *pg, *pgm, *pa, *px, *pv;
+    NB_CHECK(ensure(c.ws, B_VG, (size_t)n * 3 * sizeof(float), &pg));
+    NB_CHECK(ensure(c.ws, B_VGM, (size_t)n * sizeof(float), &pgm));
+    NB_CHECK(ensure(c.ws, B_ACC, (size_t)n * 3 * sizeof(float), &pa));
+    NB_CHECK(ensure(c.ws, B_SEGX, (size_t)ckpt_every * n3b, &px));
+    NB_CHECK(ensure(c.ws, B_SEGV, n3b, &pv));
+    float* g = (float*)pg;
+    float* gm = (float*)pgm;
+    float* a = (float*)pa;
+    double* X = (double*)px;
+    double* v = (double*)pv;
+
+    // v_K = v_{K-1/2} + h a(x_K)
+    count(1);
+    NB_CUDA(nbk::pack_vjp(n, vp.npad, vp.block, xK, mass, nullptr, lamv, lamx, nullptr, nullptr, gm_acc, 0.0, h,
+                          nullptr, plain, vp.jv, vp.centres, st));
+    NB_CHECK(run_vjp(vp, n, eps2, !plain, false, g, gm, c.sms, st));
+    for (int64_t seg = nck - 1; seg >= 0; --seg) {
+        const int64_t c0 = seg * ckpt_every;
+        const int64_t c1 = (c0 + ckpt_every < steps) ? c0 + ckpt_every : steps;
+        const double* slot = tp + (size_t)seg * 2 * n * 3;
+        // replay x_{c0} .. x_{c1-1} from the checkpoint (x_{c0}, v_{c0+1/2})
+        NB_CUDA(cudaMemcpyAsync(X, slot, n3b, cudaMemcpyDeviceToDevice, st));
+        if (c1 - c0 > 1) NB_CUDA(cudaMemcpyAsync(v, slot + (size_t)n * 3, n3b, cudaMemcpyDeviceToDevice, st));
+        for (int64_t k = c0 + 1; k < c1; ++k) {
+            double* xk = X + (size_t)(k - c0) * n * 3;
+            NB_CUDA(cudaMemcpyAsync(xk, xk - (size_t)n * 3, n3b, cudaMemcpyDeviceToDevice, st));
+            // x_k = x_{k-1} + dt v_{k-1/2}; v_{k-1/2} = v_{k-3/2} + dt a(x_{k-1}) for k > c0 + 1
+            count(1);
+            NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, xk, v, k > c0 + 1 ? a : nullptr, mass,
+                                  k > c0 + 1 ? dt : 0.0, dt, plain, fp.jdup, fp.centres, st));
+            if (k + 1 < c1) NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, st));
+        }
+        // reverse over the segment
+        for (int64_t s = c1 - 1; s >= c0; --s) {
+            const double kappa = (s == 0) ? h : dt;
+            count(1);
+            NB_CUDA(nbk::pack_vjp(n, vp.npad, vp.block, X + (size_t)(s - c0) * n * 3, mass, nullptr, lamv, lamx, g,
+                                  gm, gm_acc, dt, kappa, nullptr, plain, vp.jv, vp.centres, st));
+            NB_CHECK(run_vjp(vp, n, eps2, !plain, false, g, gm, c.sms, st));
+        }
+    }
+    count(1);
+    NB_CUDA(nbk::adjoint_accumulate(n, lamx, g, gm_acc, gm, st));
     return sg.finish();
 }
 

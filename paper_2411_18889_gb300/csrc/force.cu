@@ -404,6 +404,25 @@ size_t force_partial_doubles(int k, int num_sms) {
     return (size_t)num_sms * 8u * 2u * (size_t)s.block * 4u;
 }
 
+cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t ntile, int64_t nctas, int block, const double* partial,
+                        float* out3, float* out1, cudaStream_t st) {
+    KParams p;
+    p.jdup = nullptr;
+    p.centres = nullptr;
+    p.eps2 = 0.0f;
+    p.n = n;
+    p.nblk = nblk;
+    p.ntile = ntile;
+    p.units = nblk * ntile;
+    p.nctas = nctas;
+    p.acc = out3;
+    p.pot = out1;
+    p.partial = const_cast<double*>(partial);
+    p.err = nullptr;
+    fixup_kernel<<<(unsigned)nblk, 256, 0, st>>>(p, block, out1 != nullptr ? 1 : 0);
+    return cudaGetLastError();
+}
+
 size_t force_partial_doubles_for(int k, bool pot, bool mixed, bool compensated, int64_t npad, int num_sms) {
     const ShapeEntry& e = shapes()[k];
     const int occ = std::min(occupancy(k, pot ? 1 : 0, mixed ? 1 : 0, compensated ? 1 : 0), 8);

@@ -177,6 +177,12 @@ struct ForceArgs {
 
 // Scratch doubles needed for the split i-block partial sums of shape k.
 size_t force_partial_doubles(int k, int num_sms);
+// Adds the per-CTA partial sums (double4 per body: three vector components and
+// one scalar) of every i-block a stream-K slice boundary cut, in CTA order, and
+// writes out3[3g..3g+2] and out1[g] = -(scalar) for those blocks.
+cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t ntile, int64_t nctas, int block, const double* partial,
+                        float* out3, float* out1, cudaStream_t st);
+
 // Exact scratch doubles force_launch needs for this variant and padded size
 // (its grid: resident CTAs on num_sms SMs, capped by the work units).
 size_t force_partial_doubles_for(int k, bool pot, bool mixed, bool compensated, int64_t npad, int num_sms);
@@ -231,6 +237,40 @@ int batched_num_shapes();
 BatchShape batched_shape(int k);
 size_t batched_smem_bytes(int max_ns);
 cudaError_t batched_launch(int k, const BatchArgs& a, int num_sms, cudaStream_t st);
+
+// ---- reverse mode (vjp.cu) ----
+struct VjpShape {
+    int threads;
+    int ipairs;
+    int jtile;
+    int block;
+};
+struct VjpArgs {
+    const float* jv;        // [npad][16] (pack_vjp)
+    const double* centres;  // [nblk][3] or nullptr (plain)
+    float eps2;
+    int64_t n;
+    int64_t npad;
+    bool has_mu;            // potential cotangent present
+    float* g_pos;           // [n][3]
+    float* g_mass;          // [n]
+    double* partial;
+    int* err;
+};
+int vjp_num_shapes();
+VjpShape vjp_shape(int k);
+int vjp_floats_per_body();
+size_t vjp_partial_doubles(int k, int num_sms);
+// Pack the VJP j-array.  With lam_f64/lamx given (adjoint sweep) it first does
+// lamx += gprev, gm_acc += gmprev, lam_f64 += drift * lamx; the cotangent
+// packed is kappa * lam.
+cudaError_t pack_vjp(int64_t n, int64_t npad, int block, const double* pos, const float* mass, const float* lam_f32,
+                     double* lam_f64, double* lamx, const float* gprev, const float* gmprev, double* gm_acc,
+                     double drift, double kappa, const float* mu, bool plain, float* jv, double* centres,
+                     cudaStream_t st);
+cudaError_t adjoint_accumulate(int64_t n, double* lamx, const float* g, double* gm_acc, const float* gm,
+                               cudaStream_t st);
+cudaError_t vjp_launch(int k, const VjpArgs& a, int num_sms, cudaStream_t st, int* launched);
 
 // One CTA waits on an mbarrier nothing completes, for limit_ns, then sets *err.
 cudaError_t selftest_wait(uint64_t limit_ns, int* err, cudaStream_t st);

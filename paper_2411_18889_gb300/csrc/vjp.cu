@@ -1,0 +1,476 @@
+// vjp.cu -- reverse mode of the all-pairs force (Eq. 1 of Miki & Hanawa,
+// Sec. III.A): the vector-Jacobian product through the tidal tensor, as a
+// second all-pairs pass, plus the O(n) kernels of the leapfrog's adjoint sweep.
+//
+// For cotangents lam_i of the accelerations (and optionally mu_i of the
+// potentials), with d = r_j - r_k, s = |d|^2 + eps^2 and
+// T(d) = s^{-3/2} I - 3 s^{-5/2} d d^T:
+//   dL/dr_k = sum_{j != k} T(d) u_kj,   u_kj = m_k lam_j - m_j lam_k
+//             - sum_j s^{-3/2} d (mu_j m_k + mu_k m_j)               (potential)
+//   dL/dm_k = -sum_{j != k} [ s^{-3/2} (lam_j . d) + mu_j s^{-1/2} ]
+// (body k is the source of every pair (i, k) and the sink of every pair
+// (k, j); T(d) = T(-d) lets both be gathered at k).  Per pair that is 30
+// packed FP32 operations and two MUFU reciprocal square roots, against 12 for
+// the force.
+//
+// The kernel mirrors the force kernel: stream-K persistent grid over
+// (i-block, j-tile) units, i-bodies packed in f32x2 pairs in registers, j-tiles
+// of 64 bytes per body (x, y, z, m, lam, mu, each duplicated) staged by 1-D
+// bulk copies on a two-stage mbarrier ring with bounded waits, masked diagonal
+// tiles for j = k, FP64 cell centres for mixed precision, and per-tile FP32
+// partials folded into FP32 totals (two-level summation).
+#include <algorithm>
+#include <mutex>
+#include <type_traits>
+
+#include "nbody_internal.cuh"
+
+namespace nbk {
+namespace {
+
+constexpr int kVjpFloats = 16;  // x x y y z z m m lx lx ly ly lz lz mu mu
+
+struct VParams {
+    const float* jv;
+    const double* centres;
+    float eps2;
+    int64_t n;
+    int64_t nblk;
+    int64_t ntile;
+    int64_t units;
+    int64_t nctas;
+    float* g_pos;
+    float* g_mass;
+    double* partial;
+    int* err;
+};
+
+template <int T, int IP, int J, int UNROLL, bool MU, bool DIAG>
+__device__ __forceinline__ void vjp_tile(const unsigned char* tile, const f2 (&xi)[IP], const f2 (&yi)[IP],
+                                         const f2 (&zi)[IP], const f2 (&nlx)[IP], const f2 (&nly)[IP],
+                                         const f2 (&nlz)[IP], const f2 (&mi)[IP], const f2 (&nmi)[IP],
+                                         const f2 (&nmui)[IP], f2 eps2,
+                                         f2 (&gx)[IP], f2 (&gy)[IP], f2 (&gz)[IP], f2 (&gm)[IP], int jl0, int tid) {
+    const ulonglong2* tj = reinterpret_cast<const ulonglong2*>(tile);
+    const f2 m3 = pk(-3.0f, -3.0f);
+#pragma unroll UNROLL
+    for (int j = 0; j < J; ++j) {
+        const ulonglong2 A = tj[4 * j + 0];
+        const ulonglong2 B = tj[4 * j + 1];
+        const ulonglong2 Cc = tj[4 * j + 2];
+        const ulonglong2 D = tj[4 * j + 3];
+        const f2 xj = A.x, yj = A.y, zj = B.x, mj = B.y, lxj = Cc.x, lyj = Cc.y, lzj = D.x, muj = D.y;
+#pragma unroll
+        for (int q = 0; q < IP; ++q) {
+            const f2 dx = sub2(xj, xi[q]);
+            const f2 dy = sub2(yj, yi[q]);
+            const f2 dz = sub2(zj, zi[q]);
+            f2 r2 = fma2(dx, dx, eps2);
+            r2 = fma2(dy, dy, r2);
+            r2 = fma2(dz, dz, r2);
+            float s0, s1;
+            upk(r2, s0, s1);
+            float q0 = rsqrt_approx(s0);
+            float q1 = rsqrt_approx(s1);
+            if (DIAG) {
+                const int jl = jl0 + j;
+                if (jl == 2 * q * T + tid) q0 = 0.0f;
+                if (jl == (2 * q + 1) * T + tid) q1 = 0.0f;
+            }
+            const f2 ri = pk(q0, q1);
+            const f2 ri2 = mul2(ri, ri);
+            const f2 r3 = mul2(ri, ri2);
+            const f2 r5m3 = mul2(r3, mul2(ri2, m3));  // -3 s^{-5/2}
+            // u = m_k lam_j - m_j lam_k
+            const f2 ux = fma2(mi[q], lxj, mul2(mj, nlx[q]));
+            const f2 uy = fma2(mi[q], lyj, mul2(mj, nly[q]));
+            const f2 uz = fma2(mi[q], lzj, mul2(mj, nlz[q]));
+            f2 du = mul2(dx, ux);
+            du = fma2(dy, uy, du);
+            du = fma2(dz, uz, du);
+            const f2 c = mul2(r5m3, du);
+            gx[q] = fma2(c, dx, fma2(r3, ux, gx[q]));
+            gy[q] = fma2(c, dy, fma2(r3, uy, gy[q]));
+            gz[q] = fma2(c, dz, fma2(r3, uz, gz[q]));
+            f2 dl = mul2(dx, lxj);
+            dl = fma2(dy, lyj, dl);
+            dl = fma2(dz, lzj, dl);
+            gm[q] = fma2(r3, dl, gm[q]);
+            if (MU) {
+                // -s^{-3/2} d (mu_j m_k + mu_k m_j) with d = r_j - r_k, and mu_j s^{-1/2};
+                // nmi, nmui hold -m_k, -mu_k
+                const f2 cm = mul2(r3, fma2(muj, nmi[q], mul2(nmui[q], mj)));
+                gx[q] = fma2(cm, dx, gx[q]);
+                gy[q] = fma2(cm, dy, gy[q]);
+                gz[q] = fma2(cm, dz, gz[q]);
+                gm[q] = fma2(muj, ri, gm[q]);
+            }
+        }
+    }
+}
+
+template <int T, int IP, int J, int UNROLL, bool MU, bool MIXED>
+__global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
+    constexpr int C = 2 * IP * T;
+    constexpr uint32_t TILE_BYTES = J * kVjpFloats * 4u;
+    static_assert(C % J == 0, "a j-tile must not straddle two cells");
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+
+    const int tid = threadIdx.x;
+    const int64_t cta = blockIdx.x;
+    const int64_t u_begin = cta * p.units / p.nctas;
+    const int64_t u_end = (cta + 1) * p.units / p.nctas;
+    unsigned char* tiles = smem;
+    f2* xsave = reinterpret_cast<f2*>(smem + 2 * TILE_BYTES);  // MIXED: [IP][3][T]
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int s, int64_t unit) {
+        const int64_t tile = unit % p.ntile;
+        mbar_expect_tx(&bar[s], TILE_BYTES);
+        bulk_g2s(tiles + s * TILE_BYTES, p.jv + tile * (int64_t)J * kVjpFloats, TILE_BYTES, &bar[s]);
+    };
+    if (tid == 0) {
+        if (u_begin < u_end) issue(0, u_begin);
+        if (u_begin + 1 < u_end) issue(1, u_begin + 1);
+    }
+    const f2 eps2 = pk(p.eps2, p.eps2);
+    uint32_t parity = 0;
+    int s = 0;
+    int64_t u = u_begin;
+    bool failed = false;
+
+    while (u < u_end) {
+        const int64_t b = u / p.ntile;
+        const int64_t t0 = u - b * p.ntile;
+        const int64_t t1 = min(p.ntile, t0 + (u_end - u));
+        const int64_t base = b * C;
+        f2 xi[IP], yi[IP], zi[IP], nlx[IP], nly[IP], nlz[IP], mi[IP], nmi[IP], nmui[IP];
+#pragma unroll
+        for (int q = 0; q < IP; ++q) {
+            const float* a0 = p.jv + (base + (2 * q) * T + tid) * kVjpFloats;
+            const float* a1 = p.jv + (base + (2 * q + 1) * T + tid) * kVjpFloats;
+            xi[q] = pk(a0[0], a1[0]);
+            yi[q] = pk(a0[2], a1[2]);
+            zi[q] = pk(a0[4], a1[4]);
+            mi[q] = pk(a0[6], a1[6]);
+            nlx[q] = pk(-a0[8], -a1[8]);
+            nly[q] = pk(-a0[10], -a1[10]);
+            nlz[q] = pk(-a0[12], -a1[12]);
+            nmi[q] = pk(-a0[6], -a1[6]);
+            nmui[q] = pk(-a0[14], -a1[14]);
+            if (MIXED) {
+                xsave[(q * 3 + 0) * T + tid] = xi[q];
+                xsave[(q * 3 + 1) * T + tid] = yi[q];
+                xsave[(q * 3 + 2) * T + tid] = zi[q];
+            }
+        }
+        f2 gx[IP], gy[IP], gz[IP], gm[IP], tx[IP], ty[IP], tz[IP], tm[IP];
+#pragma unroll
+        for (int q = 0; q < IP; ++q) gx[q] = gy[q] = gz[q] = gm[q] = tx[q] = ty[q] = tz[q] = tm[q] = 0ull;
+        int64_t cur_cell = b;
+
+        for (int64_t tt = t0; tt < t1; ++tt, ++u) {
+            const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u, kWaitLimitNs);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            parity ^= (1u << s);
+            const int64_t cell = (tt * J) / C;
+            if (MIXED && cell != cur_cell) {
+                cur_cell = cell;
+                const double* cj = p.centres + 3 * cell;
+                const double* ci = p.centres + 3 * b;
+                const float ddx = (float)(cj[0] - ci[0]);
+                const float ddy = (float)(cj[1] - ci[1]);
+                const float ddz = (float)(cj[2] - ci[2]);
+                const f2 dx2 = pk(ddx, ddx), dy2 = pk(ddy, ddy), dz2 = pk(ddz, ddz);
+#pragma unroll
+                for (int q = 0; q < IP; ++q) {
+                    xi[q] = sub2(xsave[(q * 3 + 0) * T + tid], dx2);
+                    yi[q] = sub2(xsave[(q * 3 + 1) * T + tid], dy2);
+                    zi[q] = sub2(xsave[(q * 3 + 2) * T + tid], dz2);
+                }
+            }
+            const unsigned char* tile = tiles + s * TILE_BYTES;
+            if (cell == b)
+                vjp_tile<T, IP, J, UNROLL, MU, true>(tile, xi, yi, zi, nlx, nly, nlz, mi, nmi, nmui, eps2, gx, gy, gz, gm,
+                                                     (int)(tt * J - base), tid);
+            else
+                vjp_tile<T, IP, J, UNROLL, MU, false>(tile, xi, yi, zi, nlx, nly, nlz, mi, nmi, nmui, eps2, gx, gy, gz,
+                                                      gm, 0, tid);
+#pragma unroll
+            for (int q = 0; q < IP; ++q) {
+                tx[q] = add2(tx[q], gx[q]);
+                ty[q] = add2(ty[q], gy[q]);
+                tz[q] = add2(tz[q], gz[q]);
+                tm[q] = add2(tm[q], gm[q]);
+                gx[q] = gy[q] = gz[q] = gm[q] = 0ull;
+            }
+            __syncthreads();
+            if (tid == 0 && u + 2 < u_end) issue(s, u + 2);
+            s ^= 1;
+        }
+        if (failed) break;
+
+        const bool full = (t0 == 0 && t1 == p.ntile);
+        const int slot = (b == u_begin / p.ntile) ? 0 : 1;
+#pragma unroll
+        for (int q = 0; q < IP; ++q) {
+            float v[2][4];
+            upk(tx[q], v[0][0], v[1][0]);
+            upk(ty[q], v[0][1], v[1][1]);
+            upk(tz[q], v[0][2], v[1][2]);
+            upk(tm[q], v[0][3], v[1][3]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int lb = (2 * q + h) * T + tid;
+                const int64_t g = base + lb;
+                if (full) {
+                    if (g < p.n) {
+                        p.g_pos[3 * g + 0] = v[h][0];
+                        p.g_pos[3 * g + 1] = v[h][1];
+                        p.g_pos[3 * g + 2] = v[h][2];
+                        p.g_mass[g] = -v[h][3];
+                    }
+                } else {
+                    double4* dst = reinterpret_cast<double4*>(p.partial) + ((cta * 2 + slot) * C + lb);
+                    *dst = make_double4(v[h][0], v[h][1], v[h][2], v[h][3]);
+                }
+            }
+        }
+    }
+
+    if (failed) {
+        if (tid == 0) {
+            atomicExch(p.err, kErrTimeout);
+            const int64_t inflight = (u_end - u) < 2 ? (u_end - u) : 2;
+            for (int k = 0; k < inflight; ++k) {
+                const int st = (s + k) & 1;
+                (void)mbar_wait_bounded(&bar[st], (parity >> st) & 1u, kWaitLimitNs / 4);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void store_jv(float* jv, int64_t k, float x, float y, float z, float m, float lx, float ly,
+                                         float lz, float mu) {
+    float4* d = reinterpret_cast<float4*>(jv + k * kVjpFloats);
+    d[0] = make_float4(x, x, y, y);
+    d[1] = make_float4(z, z, m, m);
+    d[2] = make_float4(lx, lx, ly, ly);
+    d[3] = make_float4(lz, lz, mu, mu);
+}
+
+// One CTA per cell: the adjoint-sweep updates (when lamx != nullptr)
+//   lamx += g_prev, gm_acc += gm_prev, lam += drift * lamx
+// then the VJP's j-array with cotangent kappa * lam, relative to the FP64
+// cell centre (mixed) or absolute (plain).
+template <typename L>
+__global__ void __launch_bounds__(256) pack_vjp_kernel(int64_t n, int block, const double* __restrict__ pos,
+                                                       const float* __restrict__ mass, L* __restrict__ lam,
+                                                       double* __restrict__ lamx, const float* __restrict__ gprev,
+                                                       const float* __restrict__ gmprev, double* __restrict__ gm_acc,
+                                                       double drift, double kappa, const float* __restrict__ mu,
+                                                       int plain, float* __restrict__ jv, double* __restrict__ centres) {
+    __shared__ double red[3][8];
+    __shared__ double cen[3];
+    const int64_t base = (int64_t)blockIdx.x * block;
+    const int tid = threadIdx.x;
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int lb = tid; lb < block; lb += blockDim.x) {
+        const int64_t g = base + lb;
+        if (g >= n) break;
+        if constexpr (!std::is_const<L>::value) {
+            if (lamx != nullptr) {
+                for (int c = 0; c < 3; ++c) {
+                    double lx = lamx[3 * g + c];
+                    if (gprev != nullptr) lx += (double)gprev[3 * g + c];
+                    lamx[3 * g + c] = lx;
+                    lam[3 * g + c] = (L)((double)lam[3 * g + c] + drift * lx);
+                }
+                if (gmprev != nullptr) gm_acc[g] += (double)gmprev[g];
+            }
+        }
+        sx += pos[3 * g + 0];
+        sy += pos[3 * g + 1];
+        sz += pos[3 * g + 2];
+    }
+    if (!plain) {
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        sz = warp_sum(sz);
+        const int w = tid >> 5, l = tid & 31;
+        if (l == 0) {
+            red[0][w] = sx;
+            red[1][w] = sy;
+            red[2][w] = sz;
+        }
+        __syncthreads();
+        if (tid < 3) {
+            double t = 0.0;
+            for (int k = 0; k < (int)((blockDim.x + 31) >> 5); ++k) t += red[tid][k];
+            const int64_t cnt = (n - base) < block ? (n - base) : (int64_t)block;
+            cen[tid] = t / (double)cnt;
+            centres[3 * blockIdx.x + tid] = cen[tid];
+        }
+        __syncthreads();
+    } else {
+        if (tid < 3) cen[tid] = 0.0;
+        __syncthreads();
+    }
+    const double cx = cen[0], cy = cen[1], cz = cen[2];
+    for (int lb = tid; lb < block; lb += blockDim.x) {
+        const int64_t g = base + lb;
+        if (g < n) {
+            store_jv(jv, g, (float)(pos[3 * g + 0] - cx), (float)(pos[3 * g + 1] - cy), (float)(pos[3 * g + 2] - cz),
+                     mass[g], (float)(kappa * (double)lam[3 * g + 0]), (float)(kappa * (double)lam[3 * g + 1]),
+                     (float)(kappa * (double)lam[3 * g + 2]), mu ? mu[g] : 0.0f);
+        } else {
+            store_jv(jv, g, kPadPos, kPadPos, kPadPos, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f);
+        }
+    }
+}
+
+// lamx += g, gm_acc += gm (the last step of the adjoint sweep).
+__global__ void adjoint_accumulate_kernel(int64_t n, double* __restrict__ lamx, const float* __restrict__ g,
+                                          double* __restrict__ gm_acc, const float* __restrict__ gm) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 3 * n; k += (int64_t)gridDim.x * blockDim.x) {
+        lamx[k] += (double)g[k];
+        if (k < n) gm_acc[k] += (double)gm[k];
+    }
+}
+
+typedef void (*VFn)(const VParams);
+struct VShapeEntry {
+    VjpShape shape;
+    VFn fn[2][2];  // [mu][mixed]
+    size_t smem(bool mixed) const {
+        return 2u * shape.jtile * kVjpFloats * 4u + (mixed ? (size_t)shape.ipairs * 3 * shape.threads * 8 : 0);
+    }
+};
+
+template <int T, int IP, int J, int UNROLL>
+VShapeEntry make_ventry() {
+    VShapeEntry e;
+    e.shape = VjpShape{T, IP, J, 2 * IP * T};
+    e.fn[0][0] = vjp_kernel<T, IP, J, UNROLL, false, false>;
+    e.fn[0][1] = vjp_kernel<T, IP, J, UNROLL, false, true>;
+    e.fn[1][0] = vjp_kernel<T, IP, J, UNROLL, true, false>;
+    e.fn[1][1] = vjp_kernel<T, IP, J, UNROLL, true, true>;
+    return e;
+}
+
+const VShapeEntry* vshapes() {
+    static const VShapeEntry table[] = {
+        make_ventry<256, 2, 128, 2>(),  // 0: 1024-body blocks
+        make_ventry<128, 2, 128, 2>(),  // 1: 512
+        make_ventry<256, 1, 128, 4>(),  // 2: 512
+        make_ventry<128, 1, 64, 2>(),   // 3: 256
+    };
+    return table;
+}
+constexpr int kNumVShapes = 4;
+
+std::mutex g_vocc_mu;
+int g_vocc[kNumVShapes][2][2];
+bool g_vocc_init = false;
+
+int vocc(int k, int mu, int mixed) {
+    std::lock_guard<std::mutex> lk(g_vocc_mu);
+    if (!g_vocc_init) {
+        for (int a = 0; a < kNumVShapes; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int c = 0; c < 2; ++c) g_vocc[a][b][c] = -1;
+        g_vocc_init = true;
+    }
+    int& o = g_vocc[k][mu][mixed];
+    if (o < 0) {
+        const VShapeEntry& e = vshapes()[k];
+        const size_t sm = e.smem(mixed);
+        cudaFuncSetAttribute(e.fn[mu][mixed], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, e.fn[mu][mixed], e.shape.threads, sm) != cudaSuccess ||
+            nb < 1)
+            nb = 1;
+        o = std::min(nb, 8);
+    }
+    return o;
+}
+
+}  // namespace
+
+int vjp_num_shapes() { return kNumVShapes; }
+VjpShape vjp_shape(int k) { return vshapes()[k].shape; }
+int vjp_floats_per_body() { return kVjpFloats; }
+
+size_t vjp_partial_doubles(int k, int num_sms) {
+    return (size_t)num_sms * 8u * 2u * (size_t)vshapes()[k].shape.block * 4u;
+}
+
+cudaError_t pack_vjp(int64_t n, int64_t npad, int block, const double* pos, const float* mass, const float* lam_f32,
+                     double* lam_f64, double* lamx, const float* gprev, const float* gmprev, double* gm_acc,
+                     double drift, double kappa, const float* mu, bool plain, float* jv, double* centres,
+                     cudaStream_t st) {
+    const unsigned nblk = (unsigned)(npad / block);
+    if (lam_f64 != nullptr)
+        pack_vjp_kernel<double><<<nblk, 256, 0, st>>>(n, block, pos, mass, lam_f64, lamx, gprev, gmprev, gm_acc, drift,
+                                                       kappa, mu, plain ? 1 : 0, jv, centres);
+    else
+        pack_vjp_kernel<const float><<<nblk, 256, 0, st>>>(n, block, pos, mass, lam_f32, nullptr, nullptr, nullptr,
+                                                            nullptr, 0.0, kappa, mu, plain ? 1 : 0, jv, centres);
+    return cudaGetLastError();
+}
+
+cudaError_t adjoint_accumulate(int64_t n, double* lamx, const float* g, double* gm_acc, const float* gm,
+                               cudaStream_t st) {
+    int64_t grid = (3 * n + 255) / 256;
+    if (grid > 152 * 16) grid = 152 * 16;
+    if (grid < 1) grid = 1;
+    adjoint_accumulate_kernel<<<(unsigned)grid, 256, 0, st>>>(n, lamx, g, gm_acc, gm);
+    return cudaGetLastError();
+}
+
+cudaError_t vjp_launch(int k, const VjpArgs& a, int num_sms, cudaStream_t st, int* launched) {
+    const VShapeEntry& e = vshapes()[k];
+    const int C = e.shape.block;
+    const int mu = a.has_mu ? 1 : 0, mixed = a.centres != nullptr ? 1 : 0;
+    VParams p;
+    p.jv = a.jv;
+    p.centres = a.centres;
+    p.eps2 = a.eps2;
+    p.n = a.n;
+    p.nblk = a.npad / C;
+    p.ntile = a.npad / e.shape.jtile;
+    p.units = p.nblk * p.ntile;
+    p.nctas = std::min<int64_t>((int64_t)num_sms * vocc(k, mu, mixed), p.units);
+    p.g_pos = a.g_pos;
+    p.g_mass = a.g_mass;
+    p.partial = a.partial;
+    p.err = a.err;
+    *launched = 0;
+    e.fn[mu][mixed]<<<(unsigned)p.nctas, e.shape.threads, e.smem(mixed), st>>>(p);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    *launched = 1;
+    if (p.nctas > 1) {
+        err = split_fixup(p.n, p.nblk, p.ntile, p.nctas, C, p.partial, p.g_pos, p.g_mass, st);
+        if (err == cudaSuccess) *launched = 2;
+    }
+    return err;
+}
+
+}  // namespace nbk
