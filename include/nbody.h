@@ -46,6 +46,12 @@
 
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define NBODY_API __attribute__((visibility("default")))
+#else
+#define NBODY_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -77,7 +83,7 @@ typedef struct nbody_opts {
 } nbody_opts;
 
 /* Fill *opts with the defaults (NULL stream, mixed, compensated, tuned). */
-void nbody_opts_default(nbody_opts* opts);
+NBODY_API void nbody_opts_default(nbody_opts* opts);
 
 /*
  * Acceleration (Eq. 1) and potential for all n bodies, FP64 positions.
@@ -86,12 +92,12 @@ void nbody_opts_default(nbody_opts* opts);
  *  pot  [n] float or NULL (NULL skips the potential term, a cheaper kernel)
  * opts->precision selects mixed (default) or plain FP32 coordinates.
  */
-int nbody_accel(int64_t n, const double* pos, const float* mass, double eps, float* acc, float* pot,
+NBODY_API int nbody_accel(int64_t n, const double* pos, const float* mass, double eps, float* acc, float* pot,
                 const nbody_opts* opts);
 
 /* The same with FP32 positions and softening (plain precision, Listing 4's
  * data types). */
-int nbody_accel_f32(int64_t n, const float* pos, const float* mass, float eps, float* acc, float* pot,
+NBODY_API int nbody_accel_f32(int64_t n, const float* pos, const float* mass, float eps, float* acc, float* pot,
                     const nbody_opts* opts);
 
 /*
@@ -102,11 +108,11 @@ int nbody_accel_f32(int64_t n, const float* pos, const float* mass, float eps, f
  * makes steps + 1 force evaluations.  pos, vel [n][3] double (FP64 drift and
  * kicks), mass [n] float.  steps == 0 leaves the state unchanged.
  */
-int nbody_leapfrog(int64_t n, double* pos, double* vel, const float* mass, double eps, double dt,
+NBODY_API int nbody_leapfrog(int64_t n, double* pos, double* vel, const float* mass, double eps, double dt,
                    int64_t steps, const nbody_opts* opts);
 
 /* The same with FP32 state (plain precision). */
-int nbody_leapfrog_f32(int64_t n, float* pos, float* vel, const float* mass, float eps, float dt,
+NBODY_API int nbody_leapfrog_f32(int64_t n, float* pos, float* vel, const float* mass, float eps, float dt,
                        int64_t steps, const nbody_opts* opts);
 
 /*
@@ -115,9 +121,9 @@ int nbody_leapfrog_f32(int64_t n, float* pos, float* vel, const float* mass, flo
  *  out[3..5] momentum sum m v, out[6..8] net force sum m a (zero by Newton's
  *  third law up to rounding).  One force-and-potential evaluation.
  */
-int nbody_energy(int64_t n, const double* pos, const double* vel, const float* mass, double eps,
+NBODY_API int nbody_energy(int64_t n, const double* pos, const double* vel, const float* mass, double eps,
                  double* out, const nbody_opts* opts);
-int nbody_energy_f32(int64_t n, const float* pos, const float* vel, const float* mass, float eps,
+NBODY_API int nbody_energy_f32(int64_t n, const float* pos, const float* vel, const float* mass, float eps,
                      double* out, const nbody_opts* opts);
 
 /*
@@ -134,13 +140,13 @@ int nbody_energy_f32(int64_t n, const float* pos, const float* vel, const float*
  * precision and accumulate are ignored.
  */
 #define NBODY_BATCH_MAX_N 12288
-int nbody_accel_batched(int64_t nsys, const int64_t* offsets, const float* pos, const float* mass, const float* eps,
+NBODY_API int nbody_accel_batched(int64_t nsys, const int64_t* offsets, const float* pos, const float* mass, const float* eps,
                         float* acc, float* pot, const nbody_opts* opts);
 
 /* Kick-drift-kick leapfrog of every system of a ragged batch, all steps inside
  * one persistent kernel (steps + 1 force evaluations per system); pos, vel
  * [N][3] float updated in place. */
-int nbody_leapfrog_batched(int64_t nsys, const int64_t* offsets, float* pos, float* vel, const float* mass,
+NBODY_API int nbody_leapfrog_batched(int64_t nsys, const int64_t* offsets, float* pos, float* vel, const float* mass,
                            const float* eps, float dt, int64_t steps, const nbody_opts* opts);
 
 /*
@@ -157,7 +163,7 @@ int nbody_leapfrog_batched(int64_t nsys, const int64_t* offsets, float* pos, flo
  *  NULL; g_pos [n][3] float and g_mass [n] float are overwritten.
  * opts->config selects the VJP kernel shape (0 .. 3), -1 = default.
  */
-int nbody_accel_vjp(int64_t n, const double* pos, const float* mass, double eps, const float* g_acc,
+NBODY_API int nbody_accel_vjp(int64_t n, const double* pos, const float* mass, double eps, const float* g_acc,
                     const float* g_pot, float* g_pos, float* g_mass, const nbody_opts* opts);
 
 /*
@@ -175,35 +181,35 @@ int nbody_accel_vjp(int64_t n, const double* pos, const float* mass, double eps,
  * device memory; the cotangent and gradient arrays may be host or device.
  * nbody_tape_bytes returns -1 for invalid sizes.
  */
-int64_t nbody_tape_bytes(int64_t n, int64_t steps, int64_t ckpt_every);
-int nbody_leapfrog_record(int64_t n, double* pos, double* vel, const float* mass, double eps, double dt,
+NBODY_API int64_t nbody_tape_bytes(int64_t n, int64_t steps, int64_t ckpt_every);
+NBODY_API int nbody_leapfrog_record(int64_t n, double* pos, double* vel, const float* mass, double eps, double dt,
                           int64_t steps, int64_t ckpt_every, void* tape, const nbody_opts* opts);
-int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, double dt, int64_t steps, int64_t ckpt_every,
+NBODY_API int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, double dt, int64_t steps, int64_t ckpt_every,
                        const void* tape, const double* g_posT, const double* g_velT, double* g_pos0, double* g_vel0,
                        double* g_mass, const nbody_opts* opts);
 
 /* Number of force-kernel shapes compiled in (for opts->config) and the
  * bodies per i-block of shape k (0 if k is out of range). */
-int nbody_num_configs(void);
-int nbody_config_block(int k);
+NBODY_API int nbody_num_configs(void);
+NBODY_API int nbody_config_block(int k);
 
 /* Synchronise the current device and report whether any kernel since the
  * last call hit a bounded-wait timeout (NBODY_ETIMEOUT) -- the flag is then
  * cleared -- or a CUDA error (NBODY_ECUDA); NBODY_OK otherwise. */
-int nbody_last_device_error(void);
+NBODY_API int nbody_last_device_error(void);
 
 /* The last CUDA runtime error code seen by the library on this thread. */
-int nbody_last_cuda_error(void);
+NBODY_API int nbody_last_cuda_error(void);
 
 /* Static description of an NBODY_* code. */
-const char* nbody_strerror(int code);
+NBODY_API const char* nbody_strerror(int code);
 
 /* Self-test of the bounded device-side wait that every pipelined kernel
  * uses: one CTA waits on a barrier phase that nothing completes, gives up
  * after limit_seconds (1e-6 .. 1), records the timeout and returns.
  * Synchronous; returns NBODY_ETIMEOUT when the timeout path works (the
  * GPU stays usable), NBODY_EINVAL for a limit out of range. */
-int nbody_selftest_wait(double limit_seconds, const nbody_opts* opts);
+NBODY_API int nbody_selftest_wait(double limit_seconds, const nbody_opts* opts);
 
 /*
  * nbody_accel_noalloc -- nbody_accel (mixed precision, compensated sums, the
@@ -242,7 +248,7 @@ int nbody_selftest_wait(double limit_seconds, const nbody_opts* opts);
  * other: order them on one stream or synchronise between them.
  */
 #define NBODY_NOALLOC_MAX_N 65536
-int nbody_accel_noalloc(int64_t n, const double* pos, const float* mass, double eps, float* acc, float* pot,
+NBODY_API int nbody_accel_noalloc(int64_t n, const double* pos, const float* mass, double eps, float* acc, float* pot,
                         int* status, void* stream);
 
 /* Benchmark instrumentation.  While enabled, every force-kernel launch is
@@ -250,14 +256,14 @@ int nbody_accel_noalloc(int64_t n, const double* pos, const float* mass, double 
  * nbody_profile_read waits for those events and returns the summed device
  * time of the force kernels (ms) and their number since the previous read,
  * plus the number of kernels of every kind the library queued; then resets. */
-void nbody_profile_enable(int on);
-int nbody_profile_read(double* force_ms, int64_t* force_launches, int64_t* all_launches);
+NBODY_API void nbody_profile_enable(int on);
+NBODY_API int nbody_profile_read(double* force_ms, int64_t* force_launches, int64_t* all_launches);
 
 /* Free every cached workspace on every device (synchronises each device). */
-void nbody_finalize(void);
+NBODY_API void nbody_finalize(void);
 
 /* Library version, major*10000 + minor*100 + patch. */
-int nbody_version(void);
+NBODY_API int nbody_version(void);
 
 #ifdef __cplusplus
 }

@@ -72,7 +72,8 @@ def header_functions(path: str = HEADER):
     """Names of the functions include/nbody.h declares."""
     src = open(path).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(nbody_\w+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:NBODY_API\s+)?(?:const\s+)?\w+\s*\*?\s*(nbody_\w+)\s*\(", src,
+                                 flags=re.M)))
 
 
 def load():

@@ -30,7 +30,7 @@ def nvcc() -> str:
 
 
 def _flags(extra):
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-Xptxas", "-v",
                    "-I", os.path.join(ROOT, "include")] + list(extra)
 
 
