@@ -72,6 +72,8 @@ extern "C" {
 #define NBODY_ACC_COMPENSATED 0 /* FP32 per j-tile, tiles folded by Kahan
                                    summation (default) */
 #define NBODY_ACC_FP32 1        /* one running FP32 sum over all j */
+#define NBODY_ACC_KAHAN_PAIR 2  /* Kahan summation of every pair term: the most
+                                   accurate and about twice the FP32 work */
 
 typedef struct nbody_opts {
     void* stream;   /* cudaStream_t to run on; NULL = legacy default stream */
@@ -148,6 +150,23 @@ NBODY_API int nbody_accel_batched(int64_t nsys, const int64_t* offsets, const fl
  * [N][3] float updated in place. */
 NBODY_API int nbody_leapfrog_batched(int64_t nsys, const int64_t* offsets, float* pos, float* vel, const float* mass,
                            const float* eps, float dt, int64_t steps, const nbody_opts* opts);
+
+/*
+ * Separate sinks and sources: Listing 4's own form calc_acc(Ni, ipos, iacc,
+ * Nj, jpos, eps).  acc[i] = sum_j m_j (r_j - r_i) / (|r_j - r_i|^2 + eps^2)^{3/2}
+ * and pot[i] = -sum_j m_j / (|r_j - r_i|^2 + eps^2)^{1/2} over all ni sinks and
+ * all nj sources, every pair included (a sink that coincides with a source
+ * gets zero force from it when eps > 0, -m_j/eps of potential, and a
+ * non-finite result when eps == 0).  Useful for subsample evaluation and for
+ * splitting the sinks of one system over several devices.
+ *  ipos [ni][3], jpos [nj][3] (double, or float for the _f32 call),
+ *  jmass [nj] float, acc [ni][3] float, pot [ni] float or NULL.
+ * nj == 0 writes zeros; mixed precision as nbody_accel (the _f32 call is plain).
+ */
+NBODY_API int nbody_accel_ij(int64_t ni, const double* ipos, int64_t nj, const double* jpos, const float* jmass,
+                             double eps, float* acc, float* pot, const nbody_opts* opts);
+NBODY_API int nbody_accel_ij_f32(int64_t ni, const float* ipos, int64_t nj, const float* jpos, const float* jmass,
+                                 float eps, float* acc, float* pot, const nbody_opts* opts);
 
 /*
  * Reverse mode of Eq. 1 (not in the paper; the derivative of the force it

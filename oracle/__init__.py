@@ -43,6 +43,7 @@ def _load():
         lib.oracle_accel_subset.argtypes = [i64, vp, vp, dbl, i64, vp, vp, vp]
         lib.oracle_leapfrog.argtypes = [i64, vp, vp, vp, dbl, dbl, i64, vp]
         lib.oracle_energy.argtypes = [i64, vp, vp, vp, dbl, vp]
+        lib.oracle_accel_ij.argtypes = [i64, vp, i64, vp, vp, dbl, vp, vp]
         lib.oracle_accel_vjp.argtypes = [i64, vp, vp, dbl, vp, vp, vp, vp]
         lib.oracle_leapfrog_vjp.argtypes = [i64, vp, vp, vp, dbl, dbl, i64, vp, vp, vp, vp, vp]
         _lib = lib
@@ -92,6 +93,18 @@ def accel_subset(pos, mass, eps, idx, with_pot: bool = True):
     acc = np.zeros((ns, 3))
     pot = np.zeros(ns) if with_pot else None
     _load().oracle_accel_subset(n, _p(pos), _p(mass), float(eps), ns, _p(idx), _p(acc), _p(pot))
+    return acc, pot
+
+
+def accel_ij(ipos, jpos, jmass, eps, with_pot=True):
+    """Listing 4's form: every sink against every source, no pair excluded."""
+    ipos = _c(ipos)
+    jpos = _c(jpos)
+    ni, nj = ipos.shape[0], jpos.shape[0]
+    jmass = _c(jmass, shape=(nj,))
+    acc = np.zeros((ni, 3))
+    pot = np.zeros(ni) if with_pot else None
+    _load().oracle_accel_ij(ni, _p(ipos), nj, _p(jpos), _p(jmass), float(eps), _p(acc), _p(pot))
     return acc, pot
 
 

@@ -97,6 +97,33 @@ void oracle_accel_subset(int64_t n, const double* pos, const double* mass, doubl
     for (int64_t k = 0; k < ns; ++k) body_sum(idx[k], n, pos, mass, eps2, acc + 3 * k, pot ? pot + k : NULL);
 }
 
+/* Separate sinks and sources (Listing 4's calc_acc form): every pair of the
+ * ni sinks with the nj sources is included. */
+void oracle_accel_ij(int64_t ni, const double* ipos, int64_t nj, const double* jpos, const double* jmass,
+                     double eps, double* acc, double* pot) {
+    const double eps2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < ni; ++i) {
+        double ax = 0.0, ay = 0.0, az = 0.0, p = 0.0;
+        for (int64_t j = 0; j < nj; ++j) {
+            const double dx = jpos[3 * j + 0] - ipos[3 * i + 0];
+            const double dy = jpos[3 * j + 1] - ipos[3 * i + 1];
+            const double dz = jpos[3 * j + 2] - ipos[3 * i + 2];
+            const double s = dx * dx + dy * dy + dz * dz + eps2;
+            const double rinv = 1.0 / sqrt(s);
+            const double w = jmass[j] * rinv * rinv * rinv;
+            ax += w * dx;
+            ay += w * dy;
+            az += w * dz;
+            p -= jmass[j] * rinv;
+        }
+        acc[3 * i + 0] = ax;
+        acc[3 * i + 1] = ay;
+        acc[3 * i + 2] = az;
+        if (pot) pot[i] = p;
+    }
+}
+
 /* Kick-drift-kick leapfrog, in place, steps >= 0.  The force at the end of a
  * step is reused for the first kick of the next, so steps + 1 evaluations.
  * acc_out (n,3), optional: the force at the final positions. */

@@ -23,6 +23,7 @@ NBODY_PREC_MIXED = 0
 NBODY_PREC_PLAIN = 1
 NBODY_ACC_COMPENSATED = 0
 NBODY_ACC_FP32 = 1
+NBODY_ACC_KAHAN_PAIR = 2
 
 
 class NbodyOpts(ctypes.Structure):
@@ -50,6 +51,8 @@ SIGNATURES = {
     "nbody_energy_f32": (_int, [_i64, _vp, _vp, _vp, _flt, _vp, _OPTS]),
     "nbody_accel_batched": (_int, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _OPTS]),
     "nbody_leapfrog_batched": (_int, [_i64, _vp, _vp, _vp, _vp, _vp, _flt, _i64, _OPTS]),
+    "nbody_accel_ij": (_int, [_i64, _vp, _i64, _vp, _vp, _dbl, _vp, _vp, _OPTS]),
+    "nbody_accel_ij_f32": (_int, [_i64, _vp, _i64, _vp, _vp, _flt, _vp, _vp, _OPTS]),
     "nbody_accel_vjp": (_int, [_i64, _vp, _vp, _dbl, _vp, _vp, _vp, _vp, _OPTS]),
     "nbody_tape_bytes": (_i64, [_i64, _i64, _i64]),
     "nbody_leapfrog_record": (_int, [_i64, _vp, _vp, _vp, _dbl, _dbl, _i64, _i64, _vp, _OPTS]),

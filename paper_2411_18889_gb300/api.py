@@ -145,6 +145,24 @@ def nbody_leapfrog_batched(offsets, pos, vel, mass, eps, dt, steps, **kw):
           "nbody_leapfrog_batched")
 
 
+def _accel_ij(fn, name, dt, ipos, jpos, jmass, eps, acc, pot, **kw):
+    ni, nj = _n(ipos), _n(jpos)
+    o = make_opts((ipos, jpos, acc, pot), **kw)
+    check(fn(ni, _ptr(ipos, dt, (ni, 3), "ipos"), nj, _ptr(jpos, dt, (nj, 3), "jpos"),
+             _ptr(jmass, "f32", (nj,), "jmass"), float(eps), _ptr(acc, "f32", (ni, 3), "acc"),
+             _ptr(pot, "f32", (ni,), "pot"), ctypes.byref(o)), name)
+
+
+def nbody_accel_ij(ipos, jpos, jmass, eps, acc, pot=None, **kw):
+    """nbody_accel_ij: sinks ipos (ni,3) f64, sources jpos (nj,3) f64 with jmass (nj,) f32."""
+    _accel_ij(load().nbody_accel_ij, "nbody_accel_ij", "f64", ipos, jpos, jmass, eps, acc, pot, **kw)
+
+
+def nbody_accel_ij_f32(ipos, jpos, jmass, eps, acc, pot=None, **kw):
+    """nbody_accel_ij_f32: as nbody_accel_ij with FP32 positions."""
+    _accel_ij(load().nbody_accel_ij_f32, "nbody_accel_ij_f32", "f32", ipos, jpos, jmass, eps, acc, pot, **kw)
+
+
 def nbody_accel_vjp(pos, mass, eps, g_acc, g_pot, g_pos, g_mass, **kw):
     """nbody_accel_vjp: pos (n,3) f64, mass (n,) f32, g_acc (n,3) f32, g_pot (n,) f32 or None;
     g_pos (n,3) f32 and g_mass (n,) f32 are overwritten."""

@@ -131,6 +131,8 @@ enum BufId {
     B_VGM,
     B_SEGX,
     B_SEGV,
+    B_IPACK,
+    B_ICENTRES,
     B_STAGE0,
     NBUF = B_STAGE0 + 8
 };
@@ -268,7 +270,9 @@ struct Opts {
 int read_opts(const nbody_opts* o, Opts* r) {
     if (o == nullptr) return NBODY_OK;
     if (o->precision != NBODY_PREC_MIXED && o->precision != NBODY_PREC_PLAIN) return NBODY_EINVAL;
-    if (o->accumulate != NBODY_ACC_COMPENSATED && o->accumulate != NBODY_ACC_FP32) return NBODY_EINVAL;
+    if (o->accumulate != NBODY_ACC_COMPENSATED && o->accumulate != NBODY_ACC_FP32 &&
+        o->accumulate != NBODY_ACC_KAHAN_PAIR)
+        return NBODY_EINVAL;
     if (o->config < -1 || o->config >= nbk::force_num_shapes()) return NBODY_EINVAL;
     if (o->reserved != 0) return NBODY_EINVAL;
     r->stream = (cudaStream_t)o->stream;
@@ -279,6 +283,16 @@ int read_opts(const nbody_opts* o, Opts* r) {
 }
 
 bool finite_nonneg(double x) { return isfinite(x) && x >= 0.0; }
+
+// Kernel summation mode for an NBODY_ACC_* option: 0 one FP32 running sum,
+// 1 per-tile FP32 folded by Kahan summation, 2 Kahan summation per pair.
+int summation_mode(int accumulate) {
+    switch (accumulate) {
+        case NBODY_ACC_FP32: return 0;
+        case NBODY_ACC_KAHAN_PAIR: return 2;
+        default: return 1;
+    }
+}
 
 // Everything one force evaluation needs, sized for n on this workspace.
 struct ForcePlan {
@@ -310,7 +324,7 @@ int plan_force(Workspace* ws, int64_t n, int shape, int num_sms, ForcePlan* fp) 
     return NBODY_OK;
 }
 
-int run_force(const ForcePlan& fp, int64_t n, float eps2, bool mixed, bool compensated, float* acc, float* pot,
+int run_force(const ForcePlan& fp, int64_t n, float eps2, bool mixed, int summation, float* acc, float* pot,
               cudaStream_t st) {
     if (fault("launch")) return NBODY_ECUDA;
     nbk::ForceArgs a;
@@ -323,7 +337,7 @@ int run_force(const ForcePlan& fp, int64_t n, float eps2, bool mixed, bool compe
     a.pot = pot;
     a.partial = fp.partial;
     a.err = fp.err;
-    a.compensated = compensated;
+    a.summation = summation;
     ProfPair pp;
     const bool timed = prof_pair(&pp);
     int launched = 0;
@@ -362,7 +376,7 @@ int accel_f64_dev(Ctx& c, int64_t n, const double* pos, const float* mass, doubl
     count(1);
     NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, const_cast<double*>(pos), nullptr, nullptr, mass, 0.0, 0.0, plain,
                           fp.jdup, fp.centres, c.o.stream));
-    return run_force(fp, n, (float)(eps * eps), !plain, c.o.accumulate == NBODY_ACC_COMPENSATED, acc, pot,
+    return run_force(fp, n, (float)(eps * eps), !plain, summation_mode(c.o.accumulate), acc, pot,
                      c.o.stream);
 }
 
@@ -372,7 +386,7 @@ int accel_f32_dev(Ctx& c, int64_t n, const float* pos, const float* mass, float 
     count(1);
     NB_CUDA(nbk::pack_f32(n, fp.npad, const_cast<float*>(pos), nullptr, nullptr, mass, 0.0f, 0.0f, fp.jdup,
                           c.o.stream));
-    return run_force(fp, n, eps * eps, false, c.o.accumulate == NBODY_ACC_COMPENSATED, acc, pot, c.o.stream);
+    return run_force(fp, n, eps * eps, false, summation_mode(c.o.accumulate), acc, pot, c.o.stream);
 }
 
 }  // namespace
@@ -474,7 +488,7 @@ int nbody_leapfrog(int64_t n, double* pos, double* vel, const float* mass, doubl
     NB_CHECK(ensure(c.ws, B_ACC, (size_t)n * 3 * sizeof(float), &p));
     float* a = (float*)p;
     const bool plain = c.o.precision == NBODY_PREC_PLAIN;
-    const bool comp = c.o.accumulate == NBODY_ACC_COMPENSATED;
+    const int comp = summation_mode(c.o.accumulate);
     const float eps2 = (float)(eps * eps);
     cudaStream_t st = c.o.stream;
     count(1);
@@ -512,7 +526,7 @@ int nbody_leapfrog_f32(int64_t n, float* pos, float* vel, const float* mass, flo
     void* p;
     NB_CHECK(ensure(c.ws, B_ACC, (size_t)n * 3 * sizeof(float), &p));
     float* a = (float*)p;
-    const bool comp = c.o.accumulate == NBODY_ACC_COMPENSATED;
+    const int comp = summation_mode(c.o.accumulate);
     cudaStream_t st = c.o.stream;
     count(1);
     NB_CUDA(nbk::pack_f32(n, fp.npad, x, nullptr, nullptr, m, 0.0f, 0.0f, fp.jdup, st));
@@ -526,6 +540,90 @@ int nbody_leapfrog_f32(int64_t n, float* pos, float* vel, const float* mass, flo
     count(1);
     NB_CUDA(nbk::kick_f32(n, v, a, 0.5f * dt, st));
     return sg.finish();
+}
+
+// ---------------------------------------------------------------------------
+// Separate sinks and sources
+// ---------------------------------------------------------------------------
+static int accel_ij_common(int64_t ni, const void* ipos, int64_t nj, const void* jpos, const float* jmass, double eps,
+                           float* acc, float* pot, const nbody_opts* opts, bool f64) {
+    if (ni < 0 || nj < 0 || !finite_nonneg(eps)) return NBODY_EINVAL;
+    if (ni > 0 && (ipos == nullptr || acc == nullptr)) return NBODY_EINVAL;
+    if (nj > 0 && (jpos == nullptr || jmass == nullptr)) return NBODY_EINVAL;
+    NB_CHECK(check_opts_only(opts));
+    if (ni == 0) return NBODY_OK;
+    Ctx c;
+    NB_CHECK(begin(opts, &c));
+    cudaStream_t st = c.o.stream;
+    if (nj == 0) {  // no sources: zero force and potential
+        Staging sg(c.ws);
+        sg.add(acc, (size_t)ni * 3 * sizeof(float), false, true);
+        sg.add(pot, (size_t)ni * sizeof(float), false, true);
+        NB_CHECK(sg.prepare());
+        NB_CUDA(cudaMemsetAsync(sg.dev(0), 0, (size_t)ni * 3 * sizeof(float), st));
+        if (pot) NB_CUDA(cudaMemsetAsync(sg.dev(1), 0, (size_t)ni * sizeof(float), st));
+        return sg.finish();
+    }
+    const size_t vb = f64 ? sizeof(double) : sizeof(float);
+    Staging sg(c.ws);
+    sg.add(ipos, (size_t)ni * 3 * vb, true, false);
+    sg.add(jpos, (size_t)nj * 3 * vb, true, false);
+    sg.add(jmass, (size_t)nj * sizeof(float), true, false);
+    sg.add(acc, (size_t)ni * 3 * sizeof(float), false, true);
+    sg.add(pot, (size_t)ni * sizeof(float), false, true);
+    NB_CHECK(sg.prepare());
+    // shape from the larger side; both sides padded to whole cells of it
+    ForcePlan fp;
+    NB_CHECK(plan_force(c.ws, nj, shape_for(c, ni > nj ? ni : nj, pot != nullptr), c.sms, &fp));
+    const int64_t niblk = (ni + fp.block - 1) / fp.block;
+    const int64_t nipad = niblk * fp.block;
+    void *pi, *pc;
+    NB_CHECK(ensure(c.ws, B_IPACK, (size_t)nipad * nbk::kJdupFloats * sizeof(float), &pi));
+    NB_CHECK(ensure(c.ws, B_ICENTRES, (size_t)niblk * 3 * sizeof(double), &pc));
+    const bool plain = !f64 || c.o.precision == NBODY_PREC_PLAIN;
+    // sinks need no mass: pack them with the sources' first mass pointer unused
+    if (f64) {
+        count(2);
+        NB_CUDA(nbk::pack_f64(ni, nipad, fp.block, (double*)sg.dev(0), nullptr, nullptr, nullptr, 0.0, 0.0, plain,
+                              (float*)pi, (double*)pc, st));
+        NB_CUDA(nbk::pack_f64(nj, fp.npad, fp.block, (double*)sg.dev(1), nullptr, nullptr, (const float*)sg.dev(2),
+                              0.0, 0.0, plain, fp.jdup, fp.centres, st));
+    } else {
+        count(2);
+        NB_CUDA(nbk::pack_f32(ni, nipad, (float*)sg.dev(0), nullptr, nullptr, nullptr, 0.0f, 0.0f, (float*)pi, st));
+        NB_CUDA(nbk::pack_f32(nj, fp.npad, (float*)sg.dev(1), nullptr, nullptr, (const float*)sg.dev(2), 0.0f, 0.0f,
+                              fp.jdup, st));
+    }
+    if (fault("launch")) return NBODY_ECUDA;
+    nbk::ForceArgs a;
+    a.jdup = fp.jdup;
+    a.centres = plain ? nullptr : fp.centres;
+    a.eps2 = f64 ? (float)(eps * eps) : (float)eps * (float)eps;
+    a.n = ni;
+    a.npad = fp.npad;
+    a.ipack = (const float*)pi;
+    a.icentres = plain ? nullptr : (const double*)pc;
+    a.nipad = nipad;
+    a.acc = (float*)sg.dev(3);
+    a.pot = pot ? (float*)sg.dev(4) : nullptr;
+    a.partial = fp.partial;
+    a.err = fp.err;
+    a.summation = summation_mode(c.o.accumulate);
+    int launched = 0;
+    cudaError_t e = nbk::force_launch(fp.shape, a, fp.num_sms, st, &launched);
+    count(launched);
+    NB_CUDA(e);
+    return sg.finish();
+}
+
+int nbody_accel_ij(int64_t ni, const double* ipos, int64_t nj, const double* jpos, const float* jmass, double eps,
+                   float* acc, float* pot, const nbody_opts* opts) {
+    return accel_ij_common(ni, ipos, nj, jpos, jmass, eps, acc, pot, opts, true);
+}
+
+int nbody_accel_ij_f32(int64_t ni, const float* ipos, int64_t nj, const float* jpos, const float* jmass, float eps,
+                       float* acc, float* pot, const nbody_opts* opts) {
+    return accel_ij_common(ni, ipos, nj, jpos, jmass, (double)eps, acc, pot, opts, false);
 }
 
 // ---------------------------------------------------------------------------
@@ -649,7 +747,7 @@ int nbody_leapfrog_record(int64_t n, double* pos, double* vel, const float* mass
     NB_CHECK(ensure(c.ws, B_ACC, (size_t)n * 3 * sizeof(float), &p));
     float* a = (float*)p;
     const bool plain = c.o.precision == NBODY_PREC_PLAIN;
-    const bool comp = c.o.accumulate == NBODY_ACC_COMPENSATED;
+    const int comp = summation_mode(c.o.accumulate);
     const float eps2 = (float)(eps * eps);
     count(1);
     NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, pos, nullptr, nullptr, mass, 0.0, 0.0, plain, fp.jdup, fp.centres,
@@ -701,7 +799,7 @@ int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, double dt, int6
     if (steps == 0) return sg.finish();
 
     const bool plain = c.o.precision == NBODY_PREC_PLAIN;
-    const bool comp = c.o.accumulate == NBODY_ACC_COMPENSATED;
+    const int comp = summation_mode(c.o.accumulate);
     const float eps2 = (float)(eps * eps);
     const double h = 0.5 * dt;
     const double* tp = (const double*)tape;

@@ -39,10 +39,13 @@ namespace nbk {
 namespace {
 
 struct KParams {
-    const float* jdup;
-    const double* centres;
+    const float* jdup;      // sources (packed j-array)
+    const double* centres;  // source cell centres (mixed) or nullptr
+    const float* ipack;     // sinks: == jdup when the sinks are the sources
+    const double* icentres; // sink cell centres (mixed)
+    int self;               // sinks are the sources: mask j == i in diagonal tiles
     float eps2;
-    int64_t n;
+    int64_t n;              // sinks
     int64_t nblk;
     int64_t ntile;  // j-tiles over the padded array
     int64_t units;  // nblk * ntile
@@ -54,10 +57,21 @@ struct KParams {
 };
 
 // One j-tile against the thread's IP i-pairs.
-template <int T, int IP, int J, int UNROLL, bool POT, bool DIAG>
+// Kahan step of one packed term into (sum, comp).
+__device__ __forceinline__ void kahan_add(f2& sum, f2& comp, f2 term) {
+    const f2 y = sub2(term, comp);
+    const f2 t = add2(sum, y);
+    comp = sub2(sub2(t, sum), y);
+    sum = t;
+}
+
+// Summation modes: 0 one FP32 running sum, 1 FP32 per tile folded by Kahan
+// summation, 2 Kahan summation of every pair term.
+template <int T, int IP, int J, int UNROLL, bool POT, bool DIAG, int MODE>
 __device__ __forceinline__ void tile_pass(const unsigned char* tile, const f2 (&xi)[IP], const f2 (&yi)[IP],
                                           const f2 (&zi)[IP], f2 eps2, f2 (&ax)[IP], f2 (&ay)[IP], f2 (&az)[IP],
-                                          f2 (&ap)[IP], int jl0, int tid) {
+                                          f2 (&ap)[IP], f2 (&kx)[IP], f2 (&ky)[IP], f2 (&kz)[IP], f2 (&kp)[IP],
+                                          int jl0, int tid) {
     const ulonglong2* tj = reinterpret_cast<const ulonglong2*>(tile);
 #pragma unroll UNROLL
     for (int j = 0; j < J; ++j) {
@@ -84,10 +98,17 @@ __device__ __forceinline__ void tile_pass(const unsigned char* tile, const f2 (&
             const f2 ri = pk(q0, q1);
             f2 w = mul2(ri, mul2(ri, ri));  // rsqrt cubed
             w = mul2(w, mj);                // times m_j
-            ax[q] = fma2(dx, w, ax[q]);
-            ay[q] = fma2(dy, w, ay[q]);
-            az[q] = fma2(dz, w, az[q]);
-            if (POT) ap[q] = fma2(r2, w, ap[q]);  // r2 * m_j / r^3 = m_j / r
+            if (MODE == 2) {
+                kahan_add(ax[q], kx[q], mul2(dx, w));
+                kahan_add(ay[q], ky[q], mul2(dy, w));
+                kahan_add(az[q], kz[q], mul2(dz, w));
+                if (POT) kahan_add(ap[q], kp[q], mul2(r2, w));
+            } else {
+                ax[q] = fma2(dx, w, ax[q]);
+                ay[q] = fma2(dy, w, ay[q]);
+                az[q] = fma2(dz, w, az[q]);
+                if (POT) ap[q] = fma2(r2, w, ap[q]);  // r2 * m_j / r^3 = m_j / r
+            }
         }
     }
 }
@@ -100,7 +121,7 @@ __device__ __forceinline__ void kahan2(f2& sum, f2& comp, f2& part) {
     part = 0ull;
 }
 
-template <int T, int IP, int J, int UNROLL, int MINB, bool POT, bool MIXED, bool KAHAN>
+template <int T, int IP, int J, int UNROLL, int MINB, bool POT, bool MIXED, int KAHAN>
 __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
     constexpr int C = 2 * IP * T;
     constexpr uint32_t TILE_BYTES = J * 32u;
@@ -147,8 +168,8 @@ __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
         f2 xi[IP], yi[IP], zi[IP];
 #pragma unroll
         for (int q = 0; q < IP; ++q) {
-            const float* a0 = p.jdup + (base + (2 * q) * T + tid) * kJdupFloats;
-            const float* a1 = p.jdup + (base + (2 * q + 1) * T + tid) * kJdupFloats;
+            const float* a0 = p.ipack + (base + (2 * q) * T + tid) * kJdupFloats;
+            const float* a1 = p.ipack + (base + (2 * q + 1) * T + tid) * kJdupFloats;
             xi[q] = pk(a0[0], a1[0]);
             yi[q] = pk(a0[2], a1[2]);
             zi[q] = pk(a0[4], a1[4]);
@@ -166,7 +187,7 @@ __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
             sx[q] = sy[q] = sz[q] = sp[q] = 0ull;
             cx[q] = cy[q] = cz[q] = cp[q] = 0ull;
         }
-        int64_t cur_cell = b;
+        int64_t cur_cell = p.self ? b : -1;  // i-offsets start relative to cell b's own centre
 
         for (int64_t tt = t0; tt < t1; ++tt, ++u) {
             const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u, kWaitLimitNs);
@@ -181,7 +202,7 @@ __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
                 // (x_i - c_I) - (c_J - c_I), the centre difference in FP64.
                 cur_cell = cell;
                 const double* cj = p.centres + 3 * cell;
-                const double* ci = p.centres + 3 * b;
+                const double* ci = p.icentres + 3 * b;
                 const float dx = (float)(cj[0] - ci[0]);
                 const float dy = (float)(cj[1] - ci[1]);
                 const float dz = (float)(cj[2] - ci[2]);
@@ -194,13 +215,14 @@ __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
                 }
             }
             const unsigned char* tile = tiles + s * TILE_BYTES;
-            if (cell == b) {
-                tile_pass<T, IP, J, UNROLL, POT, true>(tile, xi, yi, zi, eps2, ax, ay, az, ap,
-                                               (int)(tt * J - base), tid);
+            if (p.self && cell == b) {
+                tile_pass<T, IP, J, UNROLL, POT, true, KAHAN>(tile, xi, yi, zi, eps2, ax, ay, az, ap, cx, cy, cz,
+                                                              cp, (int)(tt * J - base), tid);
             } else {
-                tile_pass<T, IP, J, UNROLL, POT, false>(tile, xi, yi, zi, eps2, ax, ay, az, ap, 0, tid);
+                tile_pass<T, IP, J, UNROLL, POT, false, KAHAN>(tile, xi, yi, zi, eps2, ax, ay, az, ap, cx, cy, cz,
+                                                               cp, 0, tid);
             }
-            if (KAHAN) {
+            if (KAHAN == 1) {
 #pragma unroll
                 for (int q = 0; q < IP; ++q) {
                     kahan2(sx[q], cx[q], ax[q]);
@@ -222,16 +244,19 @@ __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
         for (int q = 0; q < IP; ++q) {
             float v[2][4];
             double d[2][4];
-            if (KAHAN) {
-                float s0, s1, c0, c1;
-                upk(sx[q], s0, s1); upk(cx[q], c0, c1);
-                d[0][0] = (double)s0 - (double)c0; d[1][0] = (double)s1 - (double)c1;
-                upk(sy[q], s0, s1); upk(cy[q], c0, c1);
-                d[0][1] = (double)s0 - (double)c0; d[1][1] = (double)s1 - (double)c1;
-                upk(sz[q], s0, s1); upk(cz[q], c0, c1);
-                d[0][2] = (double)s0 - (double)c0; d[1][2] = (double)s1 - (double)c1;
-                upk(sp[q], s0, s1); upk(cp[q], c0, c1);
-                d[0][3] = (double)s0 - (double)c0; d[1][3] = (double)s1 - (double)c1;
+            if (KAHAN != 0) {
+                // mode 1 keeps (sum, comp) in s*, c*; mode 2 in a*, c*
+                const f2 S[4] = {KAHAN == 1 ? sx[q] : ax[q], KAHAN == 1 ? sy[q] : ay[q], KAHAN == 1 ? sz[q] : az[q],
+                                 KAHAN == 1 ? sp[q] : ap[q]};
+                const f2 Cm[4] = {cx[q], cy[q], cz[q], cp[q]};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float s0, s1, c0, c1;
+                    upk(S[k], s0, s1);
+                    upk(Cm[k], c0, c1);
+                    d[0][k] = (double)s0 - (double)c0;
+                    d[1][k] = (double)s1 - (double)c1;
+                }
             } else {
                 float a0, a1;
                 upk(ax[q], a0, a1); d[0][0] = a0; d[1][0] = a1;
@@ -305,7 +330,7 @@ typedef void (*KernelFn)(const KParams);
 
 struct ShapeEntry {
     ForceShape shape;
-    KernelFn fn[2][2][2];  // [pot][mixed][kahan]
+    KernelFn fn[2][2][3];  // [pot][mixed][summation mode]
     size_t smem(bool mixed) const {
         return 2u * shape.jtile * 32u + (mixed ? (size_t)shape.ipairs * 3 * shape.threads * 8 : 0);
     }
@@ -315,14 +340,18 @@ template <int T, int IP, int J, int UNROLL, int MINB>
 ShapeEntry make_entry() {
     ShapeEntry e;
     e.shape = ForceShape{T, IP, J, 2 * IP * T};
-    e.fn[0][0][0] = force_kernel<T, IP, J, UNROLL, MINB, false, false, false>;
-    e.fn[0][0][1] = force_kernel<T, IP, J, UNROLL, MINB, false, false, true>;
-    e.fn[0][1][0] = force_kernel<T, IP, J, UNROLL, MINB, false, true, false>;
-    e.fn[0][1][1] = force_kernel<T, IP, J, UNROLL, MINB, false, true, true>;
-    e.fn[1][0][0] = force_kernel<T, IP, J, UNROLL, MINB, true, false, false>;
-    e.fn[1][0][1] = force_kernel<T, IP, J, UNROLL, MINB, true, false, true>;
-    e.fn[1][1][0] = force_kernel<T, IP, J, UNROLL, MINB, true, true, false>;
-    e.fn[1][1][1] = force_kernel<T, IP, J, UNROLL, MINB, true, true, true>;
+    e.fn[0][0][0] = force_kernel<T, IP, J, UNROLL, MINB, false, false, 0>;
+    e.fn[0][0][1] = force_kernel<T, IP, J, UNROLL, MINB, false, false, 1>;
+    e.fn[0][0][2] = force_kernel<T, IP, J, UNROLL, MINB, false, false, 2>;
+    e.fn[0][1][0] = force_kernel<T, IP, J, UNROLL, MINB, false, true, 0>;
+    e.fn[0][1][1] = force_kernel<T, IP, J, UNROLL, MINB, false, true, 1>;
+    e.fn[0][1][2] = force_kernel<T, IP, J, UNROLL, MINB, false, true, 2>;
+    e.fn[1][0][0] = force_kernel<T, IP, J, UNROLL, MINB, true, false, 0>;
+    e.fn[1][0][1] = force_kernel<T, IP, J, UNROLL, MINB, true, false, 1>;
+    e.fn[1][0][2] = force_kernel<T, IP, J, UNROLL, MINB, true, false, 2>;
+    e.fn[1][1][0] = force_kernel<T, IP, J, UNROLL, MINB, true, true, 0>;
+    e.fn[1][1][1] = force_kernel<T, IP, J, UNROLL, MINB, true, true, 1>;
+    e.fn[1][1][2] = force_kernel<T, IP, J, UNROLL, MINB, true, true, 2>;
     return e;
 }
 
@@ -365,7 +394,7 @@ constexpr int kNumShapes = 5;
 
 // Resident CTAs per SM for each kernel variant, queried once.
 std::mutex g_occ_mu;
-int g_occ[kNumShapes][2][2][2];
+int g_occ[kNumShapes][2][2][3];
 bool g_occ_init = false;
 
 int occupancy(int k, int pot, int mixed, int kahan) {
@@ -374,7 +403,7 @@ int occupancy(int k, int pot, int mixed, int kahan) {
         for (int a = 0; a < kNumShapes; ++a)
             for (int b = 0; b < 2; ++b)
                 for (int c = 0; c < 2; ++c)
-                    for (int d = 0; d < 2; ++d) g_occ[a][b][c][d] = -1;
+                    for (int d = 0; d < 3; ++d) g_occ[a][b][c][d] = -1;
         g_occ_init = true;
     }
     int& o = g_occ[k][pot][mixed][kahan];
@@ -409,6 +438,9 @@ cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t ntile, int64_t nctas, i
     KParams p;
     p.jdup = nullptr;
     p.centres = nullptr;
+    p.ipack = nullptr;
+    p.icentres = nullptr;
+    p.self = 1;
     p.eps2 = 0.0f;
     p.n = n;
     p.nblk = nblk;
@@ -425,7 +457,7 @@ cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t ntile, int64_t nctas, i
 
 size_t force_partial_doubles_for(int k, bool pot, bool mixed, bool compensated, int64_t npad, int num_sms) {
     const ShapeEntry& e = shapes()[k];
-    const int occ = std::min(occupancy(k, pot ? 1 : 0, mixed ? 1 : 0, compensated ? 1 : 0), 8);
+    const int occ = std::min(occupancy(k, pot ? 1 : 0, mixed ? 1 : 0, compensated ? 1 : 0), 8);  // mode 0 or 1
     const int64_t units = (npad / e.shape.block) * (npad / e.shape.jtile);
     const int64_t nctas = std::min<int64_t>((int64_t)num_sms * occ, units);
     return (size_t)nctas * 2u * (size_t)e.shape.block * 4u;
@@ -435,13 +467,16 @@ cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st
                          cudaEvent_t ev1) {
     const ShapeEntry& e = shapes()[k];
     const int C = e.shape.block;
-    const int pot = a.pot != nullptr, mixed = a.centres != nullptr, kahan = a.compensated ? 1 : 0;
+    const int pot = a.pot != nullptr, mixed = a.centres != nullptr, kahan = a.summation;
     KParams p;
     p.jdup = a.jdup;
     p.centres = a.centres;
+    p.ipack = a.ipack != nullptr ? a.ipack : a.jdup;
+    p.icentres = a.ipack != nullptr ? a.icentres : a.centres;
+    p.self = a.ipack == nullptr ? 1 : 0;
     p.eps2 = a.eps2;
     p.n = a.n;
-    p.nblk = a.npad / C;
+    p.nblk = (a.ipack != nullptr ? a.nipad : a.npad) / C;
     p.ntile = a.npad / e.shape.jtile;
     p.units = p.nblk * p.ntile;
     int occ = occupancy(k, pot, mixed, kahan);

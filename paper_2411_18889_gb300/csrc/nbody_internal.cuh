@@ -163,16 +163,20 @@ int force_num_shapes();
 ForceShape force_shape(int k);
 
 struct ForceArgs {
-    const float* jdup;      // [npad][8]
+    const float* jdup;      // sources [npad][8]
     const double* centres;  // [nblk][3] cell centres (mixed) or nullptr (plain)
     float eps2;
-    int64_t n;
-    int64_t npad;           // nblk * block
+    int64_t n;              // sinks
+    int64_t npad;           // sources, padded to whole cells
+    // Separate sinks (nullptr: the sinks are the sources, self pair masked).
+    const float* ipack = nullptr;     // [nipad][8]
+    const double* icentres = nullptr; // sink cell centres (mixed)
+    int64_t nipad = 0;
     float* acc;             // [n][3]
     float* pot;             // [n] or nullptr
     double* partial;        // scratch, force_partial_doubles(...) doubles
     int* err;               // device error word
-    bool compensated;
+    int summation;          // 0 FP32 running sum, 1 per-tile Kahan fold, 2 Kahan per pair
 };
 
 // Scratch doubles needed for the split i-block partial sums of shape k.

@@ -143,7 +143,7 @@ extern "C" int nbody_accel_noalloc(int64_t n, const double* pos, const float* ma
     a.pot = pot;
     a.partial = partial;
     a.err = word;
-    a.compensated = true;
+    a.summation = 1;
     int launched = 0;
     if (nbk::force_launch(kShape, a, d->num_sms, st, &launched) != cudaSuccess) {
         (void)cudaGetLastError();

@@ -26,7 +26,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // One CTA per cell.  Kick (vel += kick*acc), drift (pos += drift*vel), cell
-// centre, packed offsets.  kick/drift == 0 or vel/acc == nullptr skip them.
+// centre, packed offsets.  kick/drift == 0 or vel/acc == nullptr skip them;
+// mass == nullptr packs zero masses (sinks that exert nothing).
 __global__ void __launch_bounds__(256) pack_f64_kernel(int64_t n, int block, double* __restrict__ pos,
                                                        double* __restrict__ vel, const float* __restrict__ acc,
                                                        const float* __restrict__ mass, double kick, double drift,
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(256) pack_f64_kernel(int64_t n, int block, dou
         const int64_t g = base + lb;
         if (g < n) {
             store_jdup(jdup, g, (float)(pos[3 * g + 0] - cx), (float)(pos[3 * g + 1] - cy),
-                       (float)(pos[3 * g + 2] - cz), mass[g]);
+                       (float)(pos[3 * g + 2] - cz), mass != nullptr ? mass[g] : 0.0f);
         } else {
             store_jdup(jdup, g, kPadPos, kPadPos, kPadPos, 0.0f);
         }
@@ -126,7 +127,7 @@ __global__ void pack_f32_kernel(int64_t n, int64_t npad, float* __restrict__ pos
                     pos[3 * g + 2] = z;
                 }
             }
-            store_jdup(jdup, g, x, y, z, mass[g]);
+            store_jdup(jdup, g, x, y, z, mass != nullptr ? mass[g] : 0.0f);
         } else {
             store_jdup(jdup, g, kPadPos, kPadPos, kPadPos, 0.0f);
         }

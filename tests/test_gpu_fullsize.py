@@ -47,6 +47,12 @@ def test_precision_workload_force(nb, oracle_mod, c3):
     print(f"mixed N=2^20: median {np.median(e):.3g} max {e.max():.3g} pot max {ep.max():.3g}")
     assert np.median(e) <= 2e-6 and e.max() <= 1e-4
     assert ep.max() <= 1e-5
+    # one FP32 running sum over 2^20 terms instead of per-tile compensation
+    nb.nbody_accel(P, M, w.eps, acc, None, accumulate=nb.NBODY_ACC_FP32)
+    torch.cuda.synchronize()
+    e_fp32 = rel(acc.cpu().numpy()[idx], ra)
+    print(f"fp32 running sum N=2^20: median {np.median(e_fp32):.3g} max {e_fp32.max():.3g}")
+    assert np.median(e_fp32) > 2 * np.median(e)
     # plain FP32 absolute coordinates, same launch otherwise: fails by design
     nb.nbody_accel(P, M, w.eps, acc, None, precision=nb.NBODY_PREC_PLAIN)
     torch.cuda.synchronize()

@@ -200,3 +200,49 @@ def test_streams_are_independent(nb, oracle_mod):
     for acc, eps in outs:
         ra, _ = oracle_mod.accel(p, m32.astype(np.float64), eps, with_pot=False)
         check(acc.cpu().numpy(), None, ra, None)
+
+
+@pytest.mark.parametrize("api", ["f32", "mixed", "plain"])
+@pytest.mark.parametrize("ni_,nj_", [(1, 1), (37, 500), (1000, 4097), (3000, 257), (5, 0)])
+def test_sink_source_split_matches_oracle(nb, oracle_mod, api, ni_, nj_):
+    import torch
+    p, _, m = ni.plummer(max(nj_, 1), 900 + nj_, masses="loguniform", offset=(0.0, 0.0, 0.0))
+    p, m = p[:nj_], m[:nj_]
+    sinks, _, _ = ni.plummer(ni_, 901 + ni_)
+    sinks = sinks + np.array([0.11, -0.07, 0.05])  # a lone sink and a lone source both sit at the origin
+    m32 = m.astype(np.float32)
+    eps = 2.0 ** -7
+    acc = torch.empty((ni_, 3), dtype=torch.float32, device="cuda")
+    pot = torch.empty((ni_,), dtype=torch.float32, device="cuda")
+    if api == "f32":
+        nb.nbody_accel_ij_f32(t(sinks, np.float32), t(p, np.float32), t(m32, np.float32), np.float32(eps), acc, pot)
+        si, pj = sinks.astype(np.float32).astype(np.float64), p.astype(np.float32).astype(np.float64)
+    else:
+        prec = nb.NBODY_PREC_MIXED if api == "mixed" else nb.NBODY_PREC_PLAIN
+        nb.nbody_accel_ij(t(sinks, np.float64), t(p, np.float64), t(m32, np.float32), eps, acc, pot, precision=prec)
+        si, pj = sinks, p
+    torch.cuda.synchronize()
+    a, f = acc.cpu().numpy(), pot.cpu().numpy()
+    if nj_ == 0:
+        assert np.all(a == 0) and np.all(f == 0)
+        return
+    ra, rp = oracle_mod.accel_ij(si, pj, m32.astype(np.float64), eps)
+    check(a, f, ra, rp)
+
+
+def test_kahan_per_pair_mode(nb, oracle_mod):
+    """accumulate=KAHAN_PAIR compensates every pair term: within tolerance, and
+    no less accurate than the default per-tile compensation."""
+    p, _, m = ni.plummer(8192, 95, masses="loguniform", offset=(1e4, -3e3, 7e2))
+    m32 = m.astype(np.float32)
+    ra, rp = oracle_mod.accel(p, m32.astype(np.float64), 2.0 ** -8)
+    errs = {}
+    for mode in (nb.NBODY_ACC_KAHAN_PAIR, nb.NBODY_ACC_COMPENSATED, nb.NBODY_ACC_FP32):
+        acc, pot = gpu_accel(nb, "mixed", p, m32, 2.0 ** -8, accumulate=mode)
+        errs[mode] = np.median(rel_err(acc, ra))
+        if mode != nb.NBODY_ACC_FP32:
+            check(acc, pot, ra, rp)
+    assert errs[nb.NBODY_ACC_KAHAN_PAIR] <= 1.2 * errs[nb.NBODY_ACC_COMPENSATED]
+    # at this size the sums' rounding is below the pair arithmetic's, so the
+    # three modes differ by noise; the FP32 running sum's gap shows at large n
+    assert errs[nb.NBODY_ACC_COMPENSATED] <= 1.2 * errs[nb.NBODY_ACC_FP32]

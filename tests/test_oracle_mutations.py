@@ -15,11 +15,12 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 MUTANTS = {
-    "force_exponent_1": ("mass[j] * rinv * rinv * rinv", "mass[j] * rinv * rinv"),
+    "force_exponent_1": ("w = mass[j] * rinv * rinv * rinv", "w = mass[j] * rinv * rinv"),
     "self_term_kept_with_softening": ("if (j == i) continue;", "if (j == i && eps2 == 0.0) continue;"),
     "potential_sign": ("p -= mass[j] * rinv;", "p += mass[j] * rinv;"),
     "transposed_coordinate": ("pos[3 * j + 1] - yi", "pos[3 * j + 0] - yi"),
-    "softening_dropped": ("+ dz * dz + eps2", "+ dz * dz"),
+    "softening_dropped": ("const double s = dx * dx + dy * dy + dz * dz + eps2;\n        const double rinv = 1.0 / sqrt(s);\n        const double w = mass[j]",
+                          "const double s = dx * dx + dy * dy + dz * dz;\n        const double rinv = 1.0 / sqrt(s);\n        const double w = mass[j]"),
     "full_kick_instead_of_half": ("oracle_accel(n, pos, mass, eps, a, NULL);\n    const double h = 0.5 * dt;",
                                   "oracle_accel(n, pos, mass, eps, a, NULL);\n    const double h = dt;"),
     "sink_mass_instead_of_source": ("const double w = mass[j] *", "const double w = mass[i] *"),
@@ -30,6 +31,8 @@ MUTANTS = {
     "vjp_mass_gradient_sign": ("gm += (li[0] * d[0]", "gm -= (li[0] * d[0]"),
     "vjp_potential_masses_swapped": ("(mu[i] * mass[k] + mu[k] * mass[i])", "(mu[k] * mass[k] + mu[i] * mass[i])"),
     "adjoint_drift_uses_half_step": ("lv[k] += dt * gx0[k];", "lv[k] += h * gx0[k];"),
+    "sink_source_pot_sign": ("p -= jmass[j] * rinv;", "p += jmass[j] * rinv;"),
+    "sink_source_coordinate": ("jpos[3 * j + 2] - ipos[3 * i + 2]", "jpos[3 * j + 2] - ipos[3 * i + 1]"),
 }
 
 

@@ -218,3 +218,28 @@ def test_plummer_potential_energy_and_mean_field(oracle_mod):
         sel = (r > lo) & (r < hi)
         ratio = np.mean(ar[sel] / (Mfrac(r[sel]) / r[sel] ** 2))
         assert abs(ratio - 1) < 0.03
+
+
+# ---------------------------------------------------------------- sinks and sources
+def test_sink_source_split(oracle_mod):
+    """Listing 4's form (separate sinks and sources, no pair excluded): linear in
+    the sources; one source gives the two-body closed form; sinks taken from the
+    sources agree with the self-excluding sum except for the self pair's -m_i/eps
+    in the potential."""
+    p, _, m = ni.plummer(400, 90, masses="loguniform")
+    sinks = p[ni.subsample(400, 50, 91)] + 0.01
+    a12, f12 = oracle_mod.accel_ij(sinks, p, m, 0.03)
+    a1, f1 = oracle_mod.accel_ij(sinks, p[:150], m[:150], 0.03)
+    a2, f2 = oracle_mod.accel_ij(sinks, p[150:], m[150:], 0.03)
+    np.testing.assert_allclose(a12, a1 + a2, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(f12, f1 + f2, rtol=1e-12)
+    d = np.array([0.3, -0.4, 1.2])
+    a, f = oracle_mod.accel_ij(np.zeros((1, 3)), d[None, :], np.array([2.5]), 0.1)
+    s = d @ d + 0.01
+    np.testing.assert_allclose(a[0], 2.5 * d / s ** 1.5, rtol=1e-14)
+    np.testing.assert_allclose(f[0], -2.5 / s ** 0.5, rtol=1e-14)
+    idx = ni.subsample(400, 30, 92)
+    aij, fij = oracle_mod.accel_ij(p[idx], p, m, 0.03)
+    asub, fsub = oracle_mod.accel_subset(p, m, 0.03, idx)
+    np.testing.assert_allclose(aij, asub, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(fij, fsub - m[idx] / 0.03, rtol=1e-12)
