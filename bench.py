@@ -191,21 +191,37 @@ def workload_config(w):
             "(256 MiB write); the force kernel's 32 MiB j-array is L2-resident by design"}
 
 
-def profile_case(n: int) -> int:
-    """Two force evaluations (mixed precision, no potential) for ncu captures."""
+def profile_case(n: int, kind: str = "force") -> int:
+    """Two launches of one kernel for ncu captures."""
     import torch
     import nbody_inputs as ni
     import paper_2411_18889_gb300 as nb
     nb.load()
-    p, _, m = ni.plummer(n, 3, masses="loguniform", offset=ni.plummer_offset())
-    P = torch.from_numpy(p).cuda()
-    M = torch.from_numpy(m.astype(np.float32)).cuda()
-    acc = torch.empty((n, 3), dtype=torch.float32, device="cuda")
-    for _ in range(2):
-        nb.nbody_accel(P, M, 2.0 ** -9, acc, None)
+    if kind == "batched":
+        off, pos, _, mass, eps = ni.ragged_batch(nsys=n)
+        O = torch.from_numpy(off).cuda()
+        P = torch.from_numpy(pos.astype(np.float32)).cuda()
+        M = torch.from_numpy(mass.astype(np.float32)).cuda()
+        E = torch.from_numpy(eps.astype(np.float32)).cuda()
+        acc = torch.empty((pos.shape[0], 3), dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            nb.nbody_accel_batched(O, P, M, E, acc)
+    else:
+        p, _, m = ni.plummer(n, 3, masses="loguniform", offset=ni.plummer_offset())
+        P = torch.from_numpy(p).cuda()
+        M = torch.from_numpy(m.astype(np.float32)).cuda()
+        acc = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        if kind == "vjp":
+            lam = torch.from_numpy(ni.gaussian((n, 3), 5).astype(np.float32)).cuda()
+            gm = torch.empty((n,), dtype=torch.float32, device="cuda")
+            for _ in range(2):
+                nb.nbody_accel_vjp(P, M, 2.0 ** -9, lam, None, acc, gm)
+        else:
+            for _ in range(2):
+                nb.nbody_accel(P, M, 2.0 ** -9, acc, None)
     torch.cuda.synchronize()
     assert nb.nbody_last_device_error() == 0
-    print(f"profile case n={n}: sum|a| = {float(acc.abs().sum()):.6e}")
+    print(f"profile case {kind} n={n}: sum|out| = {float(acc.abs().sum()):.6e}")
     return 0
 
 
@@ -314,14 +330,16 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--profile-case", type=int, default=0, metavar="N",
-                    help="only run nbody_accel twice on the precision workload's recipe at N bodies "
-                         "(mixed, no potential: the leapfrog's force variant), for profilers")
+                    help="only run one kernel twice at size N, for profilers: the force (nbody_accel, mixed, "
+                         "no potential, the precision workload's recipe), the VJP (nbody_accel_vjp) or the "
+                         "batched force (the ragged recipe with N systems)")
+    ap.add_argument("--profile-kind", default="force", choices=["force", "vjp", "batched"])
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
     if args.profile_case:
-        return profile_case(args.profile_case)
+        return profile_case(args.profile_case, args.profile_kind)
 
     import torch
     import nbody_inputs as ni

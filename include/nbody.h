@@ -212,6 +212,21 @@ NBODY_API int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, doubl
 NBODY_API int nbody_num_configs(void);
 NBODY_API int nbody_config_block(int k);
 
+/*
+ * Kernel-shape table (the paper chose its thread count by a parameter survey
+ * on each machine, Sec. III.A; paper_2411_18889_gb300.tune runs that survey
+ * and writes the table).  nbody_tune_load(path) replaces the rules with those
+ * of a file (path NULL: NBODY_TUNE_FILE, else nbody_tune.txt beside the
+ * library, else the built-in GB300 table) and returns the number of rules or
+ * NBODY_EINVAL (malformed line or shape index out of range; the table is then
+ * unchanged).  Lines: "force <pot 0|1> <n_min> <shape>", "vjp <n_min>
+ * <shape>", "batched <shape>", '#' comments.  nbody_tuned_shape(kind, n, pot)
+ * returns the shape used for kind 0 (force), 1 (VJP) or 2 (batched; n = the
+ * largest system) when opts->config is -1.
+ */
+NBODY_API int nbody_tune_load(const char* path);
+NBODY_API int nbody_tuned_shape(int kind, int64_t n, int pot);
+
 /* Synchronise the current device and report whether any kernel since the
  * last call hit a bounded-wait timeout (NBODY_ETIMEOUT) -- the flag is then
  * cleared -- or a CUDA error (NBODY_ECUDA); NBODY_OK otherwise. */

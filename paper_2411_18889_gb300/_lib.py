@@ -57,6 +57,8 @@ SIGNATURES = {
     "nbody_tape_bytes": (_i64, [_i64, _i64, _i64]),
     "nbody_leapfrog_record": (_int, [_i64, _vp, _vp, _vp, _dbl, _dbl, _i64, _i64, _vp, _OPTS]),
     "nbody_leapfrog_vjp": (_int, [_i64, _vp, _dbl, _dbl, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _OPTS]),
+    "nbody_tune_load": (_int, [ctypes.c_char_p]),
+    "nbody_tuned_shape": (_int, [_int, _i64, _int]),
     "nbody_num_configs": (_int, []),
     "nbody_config_block": (_int, [_int]),
     "nbody_last_device_error": (_int, []),

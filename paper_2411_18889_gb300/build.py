@@ -72,7 +72,7 @@ def build(force: bool = False, extra=(), lib_path: str = LIB, verbose: bool = Fa
                 sys.stderr.write(rep)
     if force or reports or _stale(lib_path, objs):
         tmp = lib_path + f".tmp{os.getpid()}"
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"]
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -7,8 +7,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <dlfcn.h>
+
 #include <algorithm>
 #include <atomic>
+#include <string>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -246,18 +249,130 @@ struct Staging {
 // ---------------------------------------------------------------------------
 // Kernel-shape choice.
 // ---------------------------------------------------------------------------
-// Shape measured fastest on GB300 for each size class (plain/mixed alike, with
-// or without the potential).
+// ---------------------------------------------------------------------------
+// Kernel-shape table: rules "force <pot> <n_min> <shape>", "vjp <n_min>
+// <shape>", "batched <shape>" read from the tuner's file (NBODY_TUNE_FILE, or
+// nbody_tune.txt beside the library); the rule with the largest n_min <= n
+// wins.  Built-in defaults (measured on GB300) apply when no file is found.
+// ---------------------------------------------------------------------------
+struct TuneRule {
+    int kind;  // 0 force, 1 vjp, 2 batched
+    int pot;
+    int64_t n_min;
+    int shape;
+};
+std::mutex g_tune_mu;
+std::vector<TuneRule> g_tune;
+bool g_tune_loaded = false;
+
+void tune_defaults(std::vector<TuneRule>& r) {
+    r.clear();
+    for (int pot = 0; pot < 2; ++pot) {
+        r.push_back({0, pot, 0, 4});
+        r.push_back({0, pot, 40960, pot ? 0 : 2});
+    }
+    r.push_back({1, 0, 0, 3});
+    r.push_back({1, 0, 40960, 0});
+    r.push_back({2, 0, 0, 2});
+}
+
+int kind_shapes(int kind) {
+    return kind == 0 ? nbk::force_num_shapes() : kind == 1 ? nbk::vjp_num_shapes() : nbk::batched_num_shapes();
+}
+
+// Parse a table file into `out`; returns the number of rules or NBODY_EINVAL.
+int tune_parse(const char* path, std::vector<TuneRule>& out) {
+    FILE* f = fopen(path, "r");
+    if (f == nullptr) return NBODY_EINVAL;
+    char line[256];
+    int bad = 0;
+    out.clear();
+    while (fgets(line, sizeof line, f) != nullptr) {
+        char* s = line;
+        while (*s == ' ' || *s == '\t') ++s;
+        if (*s == '#' || *s == '\n' || *s == '\0') continue;
+        char kind[16] = {0};
+        long long a = 0, b = 0, d = 0;
+        TuneRule r{};
+        if (sscanf(s, "%15s", kind) != 1) {
+            bad = 1;
+            break;
+        }
+        if (strcmp(kind, "force") == 0 && sscanf(s, "%*s %lld %lld %lld", &a, &b, &d) == 3) {
+            r = {0, (int)a, (int64_t)b, (int)d};
+        } else if (strcmp(kind, "vjp") == 0 && sscanf(s, "%*s %lld %lld", &b, &d) == 2) {
+            r = {1, 0, (int64_t)b, (int)d};
+        } else if (strcmp(kind, "batched") == 0 && sscanf(s, "%*s %lld", &d) == 1) {
+            r = {2, 0, 0, (int)d};
+        } else {
+            bad = 1;
+            break;
+        }
+        if (r.pot < 0 || r.pot > 1 || r.n_min < 0 || r.shape < 0 || r.shape >= kind_shapes(r.kind)) {
+            bad = 1;
+            break;
+        }
+        out.push_back(r);
+    }
+    fclose(f);
+    if (bad) {
+        out.clear();
+        return NBODY_EINVAL;
+    }
+    return (int)out.size();
+}
+
+std::string default_tune_path() {
+    const char* env = getenv("NBODY_TUNE_FILE");
+    if (env != nullptr) return std::string(env);
+    Dl_info info;
+    if (dladdr((void*)&tune_defaults, &info) != 0 && info.dli_fname != nullptr) {
+        std::string p(info.dli_fname);
+        const size_t k = p.find_last_of('/');
+        return (k == std::string::npos ? std::string(".") : p.substr(0, k)) + "/nbody_tune.txt";
+    }
+    return std::string();
+}
+
+void tune_ensure_loaded() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (g_tune_loaded) return;
+    std::vector<TuneRule> r;
+    const std::string p = default_tune_path();
+    if (p.empty() || tune_parse(p.c_str(), r) <= 0) tune_defaults(r);
+    g_tune = r;
+    g_tune_loaded = true;
+}
+
+int tuned_shape(int kind, int64_t n, int pot) {
+    tune_ensure_loaded();
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    int best = -1;
+    int64_t best_n = -1;
+    for (const TuneRule& r : g_tune)
+        if (r.kind == kind && (kind != 0 || r.pot == pot) && r.n_min <= n && r.n_min > best_n) {
+            best = r.shape;
+            best_n = r.n_min;
+        }
+    if (best < 0) {  // the file has no rule for this case: built-in default
+        std::vector<TuneRule> d;
+        tune_defaults(d);
+        for (const TuneRule& r : d)
+            if (r.kind == kind && (kind != 0 || r.pot == pot) && r.n_min <= n && r.n_min > best_n) {
+                best = r.shape;
+                best_n = r.n_min;
+            }
+    }
+    return best < 0 ? 0 : best;
+}
+
 int choose_shape(int64_t n, bool pot) {
     const char* env = getenv("NBODY_SHAPE");
     if (env != nullptr) {
         int k = atoi(env);
         if (k >= 0 && k < nbk::force_num_shapes()) return k;
     }
-    (void)pot;
-    if (n >= (1 << 14)) return 1;
-    if (n >= (1 << 11)) return 3;
-    return 4;
+    return tuned_shape(0, n, pot ? 1 : 0);
 }
 
 struct Opts {
@@ -629,11 +744,7 @@ int nbody_accel_ij_f32(int64_t ni, const float* ipos, int64_t nj, const float* j
 // ---------------------------------------------------------------------------
 // Reverse mode
 // ---------------------------------------------------------------------------
-static int choose_vjp_shape(int64_t n) {
-    if (n >= (1 << 14)) return 0;
-    if (n >= (1 << 11)) return 1;
-    return 3;
-}
+static int choose_vjp_shape(int64_t n) { return tuned_shape(1, n, 0); }
 
 struct VjpPlan {
     int shape, block;
@@ -930,7 +1041,7 @@ static int batched_common(int64_t nsys, const int64_t* offsets, float* pos, floa
     a.dt = dt;
     a.steps = leapfrog ? steps : 0;
     a.max_ns = (int)max_ns;
-    const int shape = c.o.config >= 0 ? c.o.config : 0;
+    const int shape = c.o.config >= 0 ? c.o.config : tuned_shape(2, max_ns, 0);
     count(1);
     NB_CUDA(nbk::batched_launch(shape, a, c.sms, st));
     // (a pageable-to-device copy has read `order` before cudaMemcpyAsync returns)
@@ -1033,6 +1144,29 @@ int nbody_selftest_wait(double limit_seconds, const nbody_opts* opts) {
         return NBODY_ETIMEOUT;
     }
     return NBODY_OK;
+}
+
+int nbody_tune_load(const char* path) {
+    std::vector<TuneRule> r;
+    const std::string p = path != nullptr ? std::string(path) : default_tune_path();
+    int k = p.empty() ? NBODY_EINVAL : tune_parse(p.c_str(), r);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (k <= 0) {
+        if (path == nullptr) {  // no file beside the library: the built-in table
+            tune_defaults(g_tune);
+            g_tune_loaded = true;
+            return 0;
+        }
+        return NBODY_EINVAL;
+    }
+    g_tune = r;
+    g_tune_loaded = true;
+    return k;
+}
+
+int nbody_tuned_shape(int kind, int64_t n, int pot) {
+    if (kind < 0 || kind > 2 || n < 0 || pot < 0 || pot > 1) return NBODY_EINVAL;
+    return tuned_shape(kind, n, pot);
 }
 
 void nbody_profile_enable(int on) { g_prof_on.store(on != 0); }

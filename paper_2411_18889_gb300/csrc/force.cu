@@ -1,6 +1,12 @@
 // force.cu -- the all-pairs softened force and potential (Eq. 1 of Miki &
 // Hanawa, Sec. III.A, with the per-pair arithmetic of their Listing 4).
 //
+// Occupancy.  The persistent grid holds 16 warps per SM (two 256-thread CTAs
+// or one of 512) even when registers would allow more: with the FP32 FMA pipe
+// as the bound, more resident warps only trade registers (ILP) for latency
+// hiding the kernel does not need; on GB300 a 256-thread shape ran at 60.5 %
+// of FP32 peak with three CTAs per SM and 66 % with two.
+//
 // Decomposition.  Bodies are grouped in i-blocks ("cells") of
 // block = 2 * IP * T bodies; the j-range is cut into tiles of J bodies.  The
 // work is the grid of units (i-block, j-tile), flattened i-block-major, and a
@@ -330,6 +336,7 @@ typedef void (*KernelFn)(const KParams);
 
 struct ShapeEntry {
     ForceShape shape;
+    int cap;  // most CTAs per SM the persistent grid uses (16 warps per SM)
     KernelFn fn[2][2][3];  // [pot][mixed][summation mode]
     size_t smem(bool mixed) const {
         return 2u * shape.jtile * 32u + (mixed ? (size_t)shape.ipairs * 3 * shape.threads * 8 : 0);
@@ -340,6 +347,7 @@ template <int T, int IP, int J, int UNROLL, int MINB>
 ShapeEntry make_entry() {
     ShapeEntry e;
     e.shape = ForceShape{T, IP, J, 2 * IP * T};
+    e.cap = T >= 512 ? 1 : 512 / T;
     e.fn[0][0][0] = force_kernel<T, IP, J, UNROLL, MINB, false, false, 0>;
     e.fn[0][0][1] = force_kernel<T, IP, J, UNROLL, MINB, false, false, 1>;
     e.fn[0][0][2] = force_kernel<T, IP, J, UNROLL, MINB, false, false, 2>;
@@ -357,9 +365,9 @@ ShapeEntry make_entry() {
 
 const ShapeEntry* shapes() {
     static const ShapeEntry table[] = {
-        make_entry<256, 4, 256, 2, 0>(),  // 0: 2048-body blocks
-        make_entry<256, 2, 256, 4, 0>(),  // 1: 1024 (fastest at large n, with or without potential)
-        make_entry<512, 2, 256, 2, 0>(),  // 2: 2048
+        make_entry<256, 4, 256, 4, 0>(),  // 0: 2048-body blocks (fastest with the potential)
+        make_entry<256, 2, 256, 4, 0>(),  // 1: 1024
+        make_entry<512, 2, 256, 4, 0>(),  // 2: 2048 (fastest without the potential)
         make_entry<128, 2, 128, 2, 0>(),  // 3: 512
         make_entry<128, 1, 64, 2, 0>(),   // 4: 256 (small n)
 #ifdef NBODY_EXTRA_SHAPES
@@ -457,7 +465,7 @@ cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t ntile, int64_t nctas, i
 
 size_t force_partial_doubles_for(int k, bool pot, bool mixed, bool compensated, int64_t npad, int num_sms) {
     const ShapeEntry& e = shapes()[k];
-    const int occ = std::min(occupancy(k, pot ? 1 : 0, mixed ? 1 : 0, compensated ? 1 : 0), 8);  // mode 0 or 1
+    const int occ = std::min(occupancy(k, pot ? 1 : 0, mixed ? 1 : 0, compensated ? 1 : 0), e.cap);  // mode 0 or 1
     const int64_t units = (npad / e.shape.block) * (npad / e.shape.jtile);
     const int64_t nctas = std::min<int64_t>((int64_t)num_sms * occ, units);
     return (size_t)nctas * 2u * (size_t)e.shape.block * 4u;
@@ -480,7 +488,7 @@ cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st
     p.ntile = a.npad / e.shape.jtile;
     p.units = p.nblk * p.ntile;
     int occ = occupancy(k, pot, mixed, kahan);
-    occ = std::min(occ, 8);
+    occ = std::min(occ, e.cap);
     p.nctas = std::min<int64_t>((int64_t)num_sms * occ, p.units);
     p.acc = a.acc;
     p.pot = a.pot;

@@ -88,3 +88,29 @@ def test_python_binding_checks_arrays():
         nb.nbody_accel_f32(p, m[:3], 0.1, a)
     with pytest.raises(ValueError):
         nb.nbody_accel_f32(np.zeros((3, 4), dtype=np.float32).T, m[:3], 0.1, a)
+
+
+def test_tune_table_parse_and_query(lib, tmp_path):
+    """The shape table: built-in rules, a file's rules (largest n_min <= n wins),
+    rejection of malformed lines and out-of-range shapes (table unchanged)."""
+    EINVAL = -1
+    good = tmp_path / "t.txt"
+    good.write_text("# comment\nforce 0 0 3\nforce 0 5000 2\nforce 1 0 0\nvjp 0 1\nvjp 100000 2\nbatched 3\n")
+    assert lib.nbody_tune_load(str(good).encode()) == 6
+    assert lib.nbody_tuned_shape(0, 10, 0) == 3
+    assert lib.nbody_tuned_shape(0, 5000, 0) == 2
+    assert lib.nbody_tuned_shape(0, 10 ** 7, 1) == 0
+    assert lib.nbody_tuned_shape(1, 99999, 0) == 1
+    assert lib.nbody_tuned_shape(1, 100000, 0) == 2
+    assert lib.nbody_tuned_shape(2, 4096, 0) == 3
+    for bad in ("force 0 0 99\n", "force 2 0 1\n", "vjp -5 1\n", "nonsense 1 2\n", "force 0\n"):
+        f = tmp_path / "bad.txt"
+        f.write_text(bad)
+        assert lib.nbody_tune_load(str(f).encode()) == EINVAL
+        assert lib.nbody_tuned_shape(0, 5000, 0) == 2  # unchanged
+    assert lib.nbody_tune_load(str(tmp_path / "missing.txt").encode()) == EINVAL
+    assert lib.nbody_tuned_shape(3, 10, 0) == EINVAL
+    assert lib.nbody_tune_load(None) >= 0  # back to the default location / built-in table
+    for n in (1, 1000, 1 << 20):
+        for pot in (0, 1):
+            assert 0 <= lib.nbody_tuned_shape(0, n, pot) < lib.nbody_num_configs()
