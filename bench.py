@@ -316,7 +316,8 @@ def adjoint_leg(nb, dev, args):
     return {"workload": "plummer_n16384_eps2^-7_kdk64_dt2^-8_ckpt8_loss_sum_m_x_minus_y_sq",
             "forward_ms": f * 1e3, "gradient_ms": g * 1e3, "adjoint_to_forward": g / f,
             "forward_gints": inter / f / 1e9,
-            "note": "gradient = replay of 48 force evaluations from 8 checkpoints + 65 force VJPs"}
+            "note": "gradient = replay of 48 force evaluations from 8 checkpoints (on a second stream, two "
+                    "segments ahead) + 65 force VJPs"}
 
 
 # ---------------------------------------------------------------------------

@@ -144,7 +144,16 @@ struct Workspace {
     int device = 0;
     cudaStream_t stream = nullptr;
     Buf buf[NBUF];
+    cudaStream_t aux = nullptr;  // second stream (adjoint replay), created on first use
+    cudaEvent_t ev[5] = {};      // ordering events between the two streams
 };
+
+int ensure_aux(Workspace* w) {
+    if (w->aux != nullptr) return NBODY_OK;
+    NB_CUDA(cudaStreamCreateWithFlags(&w->aux, cudaStreamNonBlocking));
+    for (auto& e : w->ev) NB_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return NBODY_OK;
+}
 
 std::mutex g_ws_mu;
 std::map<std::pair<int, cudaStream_t>, Workspace*> g_ws;
@@ -924,13 +933,45 @@ int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, double dt, int6
     NB_CHECK(ensure(c.ws, B_VG, (size_t)n * 3 * sizeof(float), &pg));
     NB_CHECK(ensure(c.ws, B_VGM, (size_t)n * sizeof(float), &pgm));
     NB_CHECK(ensure(c.ws, B_ACC, (size_t)n * 3 * sizeof(float), &pa));
-    NB_CHECK(ensure(c.ws, B_SEGX, (size_t)ckpt_every * n3b, &px));
+    NB_CHECK(ensure(c.ws, B_SEGX, 2 * (size_t)ckpt_every * n3b, &px));
     NB_CHECK(ensure(c.ws, B_SEGV, n3b, &pv));
     float* g = (float*)pg;
     float* gm = (float*)pgm;
     float* a = (float*)pa;
-    double* X = (double*)px;
+    double* X = (double*)px;  // two segment buffers, [2][ckpt_every][n][3]
     double* v = (double*)pv;
+    NB_CHECK(ensure_aux(c.ws));
+    cudaStream_t aux = c.ws->aux;
+    cudaEvent_t ev_start = c.ws->ev[0], ev_rep[2] = {c.ws->ev[1], c.ws->ev[2]}, ev_sw[2] = {c.ws->ev[3], c.ws->ev[4]};
+    const size_t segd = (size_t)ckpt_every * n * 3;
+
+    // Segment replays run on the auxiliary stream, two segments ahead of the
+    // reverse sweep on the caller's stream: the replay (force kernels) of
+    // segment s-2 overlaps the VJPs of segment s.  Buffer s % 2 holds segment
+    // s; ev_rep[p] says it is filled, ev_sw[p] that the sweep has read it.
+    auto replay = [&](int64_t seg) -> int {
+        const int64_t c0 = seg * ckpt_every;
+        const int64_t c1 = (c0 + ckpt_every < steps) ? c0 + ckpt_every : steps;
+        const double* slot = tp + (size_t)seg * 2 * n * 3;
+        double* Xs = X + (size_t)(seg & 1) * segd;
+        NB_CUDA(cudaMemcpyAsync(Xs, slot, n3b, cudaMemcpyDeviceToDevice, aux));
+        if (c1 - c0 > 1) NB_CUDA(cudaMemcpyAsync(v, slot + (size_t)n * 3, n3b, cudaMemcpyDeviceToDevice, aux));
+        for (int64_t k = c0 + 1; k < c1; ++k) {
+            double* xk = Xs + (size_t)(k - c0) * n * 3;
+            NB_CUDA(cudaMemcpyAsync(xk, xk - (size_t)n * 3, n3b, cudaMemcpyDeviceToDevice, aux));
+            // x_k = x_{k-1} + dt v_{k-1/2}; v_{k-1/2} = v_{k-3/2} + dt a(x_{k-1}) for k > c0 + 1
+            count(1);
+            NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, xk, v, k > c0 + 1 ? a : nullptr, mass,
+                                  k > c0 + 1 ? dt : 0.0, dt, plain, fp.jdup, fp.centres, aux));
+            if (k + 1 < c1) NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, aux));
+        }
+        NB_CUDA(cudaEventRecord(ev_rep[seg & 1], aux));
+        return NBODY_OK;
+    };
+    NB_CUDA(cudaEventRecord(ev_start, st));  // the tape and inputs are ready on the caller's stream
+    NB_CUDA(cudaStreamWaitEvent(aux, ev_start, 0));
+    NB_CHECK(replay(nck - 1));
+    if (nck >= 2) NB_CHECK(replay(nck - 2));
 
     // v_K = v_{K-1/2} + h a(x_K)
     count(1);
@@ -940,26 +981,20 @@ int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, double dt, int6
     for (int64_t seg = nck - 1; seg >= 0; --seg) {
         const int64_t c0 = seg * ckpt_every;
         const int64_t c1 = (c0 + ckpt_every < steps) ? c0 + ckpt_every : steps;
-        const double* slot = tp + (size_t)seg * 2 * n * 3;
-        // replay x_{c0} .. x_{c1-1} from the checkpoint (x_{c0}, v_{c0+1/2})
-        NB_CUDA(cudaMemcpyAsync(X, slot, n3b, cudaMemcpyDeviceToDevice, st));
-        if (c1 - c0 > 1) NB_CUDA(cudaMemcpyAsync(v, slot + (size_t)n * 3, n3b, cudaMemcpyDeviceToDevice, st));
-        for (int64_t k = c0 + 1; k < c1; ++k) {
-            double* xk = X + (size_t)(k - c0) * n * 3;
-            NB_CUDA(cudaMemcpyAsync(xk, xk - (size_t)n * 3, n3b, cudaMemcpyDeviceToDevice, st));
-            // x_k = x_{k-1} + dt v_{k-1/2}; v_{k-1/2} = v_{k-3/2} + dt a(x_{k-1}) for k > c0 + 1
-            count(1);
-            NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, xk, v, k > c0 + 1 ? a : nullptr, mass,
-                                  k > c0 + 1 ? dt : 0.0, dt, plain, fp.jdup, fp.centres, st));
-            if (k + 1 < c1) NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, st));
-        }
+        const double* Xs = X + (size_t)(seg & 1) * segd;
+        NB_CUDA(cudaStreamWaitEvent(st, ev_rep[seg & 1], 0));
         // reverse over the segment
         for (int64_t s = c1 - 1; s >= c0; --s) {
             const double kappa = (s == 0) ? h : dt;
             count(1);
-            NB_CUDA(nbk::pack_vjp(n, vp.npad, vp.block, X + (size_t)(s - c0) * n * 3, mass, nullptr, lamv, lamx, g,
-                                  gm, gm_acc, dt, kappa, nullptr, plain, vp.jv, vp.centres, st));
+            NB_CUDA(nbk::pack_vjp(n, vp.npad, vp.block, Xs + (size_t)(s - c0) * n * 3, mass, nullptr, lamv, lamx,
+                                  g, gm, gm_acc, dt, kappa, nullptr, plain, vp.jv, vp.centres, st));
             NB_CHECK(run_vjp(vp, n, eps2, !plain, false, g, gm, c.sms, st));
+        }
+        NB_CUDA(cudaEventRecord(ev_sw[seg & 1], st));
+        if (seg >= 2) {
+            NB_CUDA(cudaStreamWaitEvent(aux, ev_sw[seg & 1], 0));
+            NB_CHECK(replay(seg - 2));
         }
     }
     count(1);
@@ -1203,6 +1238,10 @@ void nbody_finalize(void) {
             (void)cudaDeviceSynchronize();
             for (int k = 0; k < NBUF; ++k)
                 if (w->buf[k].p) (void)cudaFree(w->buf[k].p);
+            if (w->aux != nullptr) {
+                for (auto& e : w->ev) (void)cudaEventDestroy(e);
+                (void)cudaStreamDestroy(w->aux);
+            }
         }
         delete w;
     }
