@@ -164,6 +164,22 @@ __device__ __forceinline__ void eval_pass(const float* __restrict__ sj, int npai
     (void)ev;
 }
 
+// eval_pass with I' = min(I, left) i-bodies per thread.
+template <int T, int I, bool POT, bool MASK>
+__device__ __forceinline__ void pass_dispatch(int left, const float* __restrict__ sj, int npair, int ns, int base,
+                                              f2 eps2, const BParams& p, int64_t off, int64_t ev, float kick,
+                                              bool drift, float eps2s) {
+    if (I >= 4 && left >= 4) {
+        eval_pass<T, (I >= 4 ? 4 : 1), POT, MASK>(sj, npair, ns, base, eps2, p, off, ev, kick, drift, eps2s);
+    } else if (I >= 3 && left == 3) {
+        eval_pass<T, (I >= 3 ? 3 : 1), POT, MASK>(sj, npair, ns, base, eps2, p, off, ev, kick, drift, eps2s);
+    } else if (I >= 2 && left >= 2) {
+        eval_pass<T, (I >= 2 ? 2 : 1), POT, MASK>(sj, npair, ns, base, eps2, p, off, ev, kick, drift, eps2s);
+    } else {
+        eval_pass<T, 1, POT, MASK>(sj, npair, ns, base, eps2, p, off, ev, kick, drift, eps2s);
+    }
+}
+
 // Shared-memory image of system s: j-pairs, an odd count padded with a
 // massless body far away.
 __device__ __forceinline__ void load_system(float* sj, const BParams& p, int64_t off, int ns) {
@@ -209,10 +225,15 @@ __global__ void __launch_bounds__(T) batched_kernel(const BParams p) {
             const float kick = (p.steps == 0) ? 0.0f : ((ev == 0 || ev == p.steps) ? 0.5f * p.dt : p.dt);
             const bool drift = ev < p.steps;
             for (int base = 0; base < ns; base += T * I) {
-                if (eps2s == 0.0f)
-                    eval_pass<T, I, POT, true>(sj, npair, ns, base, eps2, p, off, ev, kick, drift, eps2s);
-                else
-                    eval_pass<T, I, POT, false>(sj, npair, ns, base, eps2, p, off, ev, kick, drift, eps2s);
+                // The last pass of a system takes only as many i-bodies per
+                // thread as it has left (rounded up to whole warps' worth), so
+                // padding costs at most T - 1 bodies per system, not T*I - 1.
+                const int left = (ns - base + T - 1) / T;
+                if (eps2s == 0.0f) {
+                    pass_dispatch<T, I, POT, true>(left, sj, npair, ns, base, eps2, p, off, ev, kick, drift, eps2s);
+                } else {
+                    pass_dispatch<T, I, POT, false>(left, sj, npair, ns, base, eps2, p, off, ev, kick, drift, eps2s);
+                }
             }
             __syncthreads();
             if (drift) {

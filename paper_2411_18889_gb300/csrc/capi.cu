@@ -77,8 +77,17 @@ bool prof_pair(ProfPair* out) {
     return true;
 }
 
-// Queue `launches` kernels' worth of accounting after a successful launch.
-inline void count(int launches) { g_launches += launches; }
+// Queue `launches` kernels' worth of accounting after a successful launch
+// (while a graph is being captured the kernels are only recorded: they are
+// counted when the graph runs).
+thread_local bool t_capturing = false;
+thread_local int t_captured = 0;
+inline void count(int launches) {
+    if (t_capturing)
+        t_captured += launches;
+    else
+        g_launches += launches;
+}
 
 struct DeviceInfo {
     bool checked = false;
@@ -146,7 +155,25 @@ struct Workspace {
     Buf buf[NBUF];
     cudaStream_t aux = nullptr;  // second stream (adjoint replay), created on first use
     cudaEvent_t ev[5] = {};      // ordering events between the two streams
+    uint64_t gen = 0;            // bumped whenever a buffer moves (invalidates cached graphs)
+    cudaStream_t cap = nullptr;  // private stream that leapfrog graphs are captured on
+    std::map<std::vector<uint64_t>, struct GraphEntry*> graphs;
+    uint64_t tick = 0;
 };
+
+struct GraphEntry {
+    int seen = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;
+    uint64_t last = 0;
+};
+
+void drop_graph(GraphEntry* e) {
+    if (e->exec) (void)cudaGraphExecDestroy(e->exec);
+    if (e->graph) (void)cudaGraphDestroy(e->graph);
+    delete e;
+}
 
 int ensure_aux(Workspace* w) {
     if (w->aux != nullptr) return NBODY_OK;
@@ -195,6 +222,7 @@ int ensure(Workspace* w, int id, size_t bytes, void** out) {
         if (id == B_ERR) NB_CUDA(cudaMemset(p, 0, sz));
         b.p = p;
         b.cap = sz;
+        ++w->gen;
     }
     *out = b.p;
     return NBODY_OK;
@@ -590,6 +618,107 @@ int nbody_accel_f32(int64_t n, const float* pos, const float* mass, float eps, f
     return sg.finish();
 }
 
+}  // extern "C"
+
+// The launch sequence of a leapfrog call (state type V: double or float).
+template <typename V>
+static int leapfrog_issue(int64_t n, V* x, V* v, const float* m, double eps, double dt, int64_t steps,
+                          const ForcePlan& fp, float* a, bool plain, int comp, cudaStream_t st) {
+    const bool f64 = sizeof(V) == sizeof(double);
+    const float eps2 = f64 ? (float)(eps * eps) : (float)eps * (float)eps;
+    count(1);
+    if (f64)
+        NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, (double*)x, nullptr, nullptr, m, 0.0, 0.0, plain, fp.jdup,
+                              fp.centres, st));
+    else
+        NB_CUDA(nbk::pack_f32(n, fp.npad, (float*)x, nullptr, nullptr, m, 0.0f, 0.0f, fp.jdup, st));
+    NB_CHECK(run_force(fp, n, eps2, f64 && !plain, comp, a, nullptr, st));
+    for (int64_t s = 0; s < steps; ++s) {
+        const double kick = (s == 0) ? 0.5 * dt : dt;  // merged closing + opening half kicks
+        count(1);
+        if (f64)
+            NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, (double*)x, (double*)v, a, m, kick, dt, plain, fp.jdup,
+                                  fp.centres, st));
+        else
+            NB_CUDA(nbk::pack_f32(n, fp.npad, (float*)x, (float*)v, a, m, (float)kick, (float)dt, fp.jdup, st));
+        NB_CHECK(run_force(fp, n, eps2, f64 && !plain, comp, a, nullptr, st));
+    }
+    count(1);
+    if (f64)
+        NB_CUDA(nbk::kick_f64(n, (double*)v, a, 0.5 * dt, st));
+    else
+        NB_CUDA(nbk::kick_f32(n, (float*)v, a, 0.5f * (float)dt, st));
+    return NBODY_OK;
+}
+
+// A call repeated with the same arguments and workspace (the loop of a
+// simulation) is captured, on its second occurrence, into a CUDA graph that
+// later occurrences launch as one unit; the first occurrence runs directly.
+template <typename V>
+static int leapfrog_run(Ctx& c, int64_t n, V* x, V* v, const float* m, double eps, double dt, int64_t steps,
+                        bool graphable) {
+    ForcePlan fp;
+    NB_CHECK(plan_force(c.ws, n, shape_for(c, n, false), c.sms, &fp));
+    void* p;
+    NB_CHECK(ensure(c.ws, B_ACC, (size_t)n * 3 * sizeof(float), &p));
+    float* a = (float*)p;
+    const bool plain = sizeof(V) == sizeof(float) || c.o.precision == NBODY_PREC_PLAIN;
+    const int comp = summation_mode(c.o.accumulate);
+    cudaStream_t st = c.o.stream;
+    if (!graphable || g_prof_on.load() || getenv("NBODY_NO_GRAPH") != nullptr)
+        return leapfrog_issue<V>(n, x, v, m, eps, dt, steps, fp, a, plain, comp, st);
+    double e = eps, d = dt;
+    uint64_t be, bd;
+    memcpy(&be, &e, 8);
+    memcpy(&bd, &d, 8);
+    const std::vector<uint64_t> key = {(uint64_t)sizeof(V), (uint64_t)n, (uint64_t)steps, (uint64_t)(uintptr_t)x,
+                                       (uint64_t)(uintptr_t)v, (uint64_t)(uintptr_t)m, be, bd,
+                                       (uint64_t)fp.shape, (uint64_t)plain, (uint64_t)comp, c.ws->gen};
+    GraphEntry*& ge = c.ws->graphs[key];
+    if (ge == nullptr) ge = new GraphEntry();
+    ge->last = ++c.ws->tick;
+    if (ge->exec != nullptr) {
+        NB_CUDA(cudaGraphLaunch(ge->exec, st));
+        count(ge->kernels);
+        return NBODY_OK;
+    }
+    if (ge->seen++ == 0) return leapfrog_issue<V>(n, x, v, m, eps, dt, steps, fp, a, plain, comp, st);
+    if (c.ws->cap == nullptr) NB_CUDA(cudaStreamCreateWithFlags(&c.ws->cap, cudaStreamNonBlocking));
+    NB_CUDA(cudaStreamBeginCapture(c.ws->cap, cudaStreamCaptureModeThreadLocal));
+    t_capturing = true;
+    t_captured = 0;
+    const int rc = leapfrog_issue<V>(n, x, v, m, eps, dt, steps, fp, a, plain, comp, c.ws->cap);
+    t_capturing = false;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c.ws->cap, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (rc != NBODY_OK || ec != cudaSuccess || graph == nullptr ||
+        cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (graph) (void)cudaGraphDestroy(graph);
+        ge->seen = 1;  // try again next time; run this call directly
+        return leapfrog_issue<V>(n, x, v, m, eps, dt, steps, fp, a, plain, comp, st);
+    }
+    ge->graph = graph;
+    ge->exec = exec;
+    ge->kernels = t_captured;
+    // keep at most 16 graphs per workspace: drop the least recently used
+    if (c.ws->graphs.size() > 16) {
+        auto victim = c.ws->graphs.begin();
+        for (auto it = c.ws->graphs.begin(); it != c.ws->graphs.end(); ++it)
+            if (it->second->last < victim->second->last) victim = it;
+        if (victim->second != ge) {
+            drop_graph(victim->second);
+            c.ws->graphs.erase(victim);
+        }
+    }
+    NB_CUDA(cudaGraphLaunch(exec, st));
+    count(ge->kernels);
+    return NBODY_OK;
+}
+
+extern "C" {
+
 int nbody_leapfrog(int64_t n, double* pos, double* vel, const float* mass, double eps, double dt, int64_t steps,
                    const nbody_opts* opts) {
     if (n < 0 || steps < 0 || !finite_nonneg(eps) || !isfinite(dt)) return NBODY_EINVAL;
@@ -603,29 +732,8 @@ int nbody_leapfrog(int64_t n, double* pos, double* vel, const float* mass, doubl
     sg.add(vel, (size_t)n * 3 * sizeof(double), true, true);
     sg.add(mass, (size_t)n * sizeof(float), true, false);
     NB_CHECK(sg.prepare());
-    double* x = (double*)sg.dev(0);
-    double* v = (double*)sg.dev(1);
-    const float* m = (const float*)sg.dev(2);
-    ForcePlan fp;
-    NB_CHECK(plan_force(c.ws, n, shape_for(c, n, false), c.sms, &fp));
-    void* p;
-    NB_CHECK(ensure(c.ws, B_ACC, (size_t)n * 3 * sizeof(float), &p));
-    float* a = (float*)p;
-    const bool plain = c.o.precision == NBODY_PREC_PLAIN;
-    const int comp = summation_mode(c.o.accumulate);
-    const float eps2 = (float)(eps * eps);
-    cudaStream_t st = c.o.stream;
-    count(1);
-    NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, x, nullptr, nullptr, m, 0.0, 0.0, plain, fp.jdup, fp.centres, st));
-    NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, st));
-    for (int64_t s = 0; s < steps; ++s) {
-        const double kick = (s == 0) ? 0.5 * dt : dt;  // merged closing + opening half kicks
-        count(1);
-    NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, x, v, a, m, kick, dt, plain, fp.jdup, fp.centres, st));
-        NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, st));
-    }
-    count(1);
-    NB_CUDA(nbk::kick_f64(n, v, a, 0.5 * dt, st));
+    NB_CHECK(leapfrog_run<double>(c, n, (double*)sg.dev(0), (double*)sg.dev(1), (const float*)sg.dev(2), eps, dt,
+                                  steps, !sg.any_host));
     return sg.finish();
 }
 
@@ -642,27 +750,8 @@ int nbody_leapfrog_f32(int64_t n, float* pos, float* vel, const float* mass, flo
     sg.add(vel, (size_t)n * 3 * sizeof(float), true, true);
     sg.add(mass, (size_t)n * sizeof(float), true, false);
     NB_CHECK(sg.prepare());
-    float* x = (float*)sg.dev(0);
-    float* v = (float*)sg.dev(1);
-    const float* m = (const float*)sg.dev(2);
-    ForcePlan fp;
-    NB_CHECK(plan_force(c.ws, n, shape_for(c, n, false), c.sms, &fp));
-    void* p;
-    NB_CHECK(ensure(c.ws, B_ACC, (size_t)n * 3 * sizeof(float), &p));
-    float* a = (float*)p;
-    const int comp = summation_mode(c.o.accumulate);
-    cudaStream_t st = c.o.stream;
-    count(1);
-    NB_CUDA(nbk::pack_f32(n, fp.npad, x, nullptr, nullptr, m, 0.0f, 0.0f, fp.jdup, st));
-    NB_CHECK(run_force(fp, n, eps * eps, false, comp, a, nullptr, st));
-    for (int64_t s = 0; s < steps; ++s) {
-        const float kick = (s == 0) ? 0.5f * dt : dt;
-        count(1);
-    NB_CUDA(nbk::pack_f32(n, fp.npad, x, v, a, m, kick, dt, fp.jdup, st));
-        NB_CHECK(run_force(fp, n, eps * eps, false, comp, a, nullptr, st));
-    }
-    count(1);
-    NB_CUDA(nbk::kick_f32(n, v, a, 0.5f * dt, st));
+    NB_CHECK(leapfrog_run<float>(c, n, (float*)sg.dev(0), (float*)sg.dev(1), (const float*)sg.dev(2), (double)eps,
+                                 (double)dt, steps, !sg.any_host));
     return sg.finish();
 }
 
@@ -1242,6 +1331,8 @@ void nbody_finalize(void) {
                 for (auto& e : w->ev) (void)cudaEventDestroy(e);
                 (void)cudaStreamDestroy(w->aux);
             }
+            for (auto& kv2 : w->graphs) drop_graph(kv2.second);
+            if (w->cap != nullptr) (void)cudaStreamDestroy(w->cap);
         }
         delete w;
     }
