@@ -65,8 +65,11 @@ extern "C" {
 
 /* Pair arithmetic precision. */
 #define NBODY_PREC_MIXED 0 /* FP64 positions; FP32 pair math on coordinates
-                              relative to FP64 cell centres (default) */
+                              relative to the FP64 centres of cells of
+                              bodies sorted along a Morton curve (default) */
 #define NBODY_PREC_PLAIN 1 /* FP32 absolute coordinates (FP64 input rounded) */
+#define NBODY_PREC_MIXED_UNSORTED 2 /* mixed, with cells taken in the caller's
+                                       order instead of a Morton order */
 
 /* Per-body summation over j. */
 #define NBODY_ACC_COMPENSATED 0 /* FP32 per j-tile, tiles folded by Kahan
@@ -246,8 +249,9 @@ NBODY_API const char* nbody_strerror(int code);
 NBODY_API int nbody_selftest_wait(double limit_seconds, const nbody_opts* opts);
 
 /*
- * nbody_accel_noalloc -- nbody_accel (mixed precision, compensated sums, the
- * potential when pot != NULL) for callers that cannot allocate GPU memory.
+ * nbody_accel_noalloc -- nbody_accel (mixed precision with cells in the
+ * caller's order as NBODY_PREC_MIXED_UNSORTED, compensated sums, the potential
+ * when pot != NULL) for callers that cannot allocate GPU memory.
  * The paper has no counterpart; this is a deployment variant of the same
  * force evaluation.
  *

@@ -21,6 +21,7 @@ NBODY_ETIMEOUT = -4
 NBODY_ENOTSUP = -5
 NBODY_PREC_MIXED = 0
 NBODY_PREC_PLAIN = 1
+NBODY_PREC_MIXED_UNSORTED = 2
 NBODY_ACC_COMPENSATED = 0
 NBODY_ACC_FP32 = 1
 NBODY_ACC_KAHAN_PAIR = 2

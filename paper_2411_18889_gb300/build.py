@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libnbody.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["force.cu", "vjp.cu", "batched.cu", "pack.cu", "reduce.cu", "selftest.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["force.cu", "vjp.cu", "batched.cu", "order.cu", "pack.cu", "reduce.cu", "selftest.cu", "capi.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

@@ -145,6 +145,8 @@ enum BufId {
     B_SEGV,
     B_IPACK,
     B_ICENTRES,
+    B_PERM,
+    B_ORDS,
     B_STAGE0,
     NBUF = B_STAGE0 + 8
 };
@@ -421,7 +423,9 @@ struct Opts {
 
 int read_opts(const nbody_opts* o, Opts* r) {
     if (o == nullptr) return NBODY_OK;
-    if (o->precision != NBODY_PREC_MIXED && o->precision != NBODY_PREC_PLAIN) return NBODY_EINVAL;
+    if (o->precision != NBODY_PREC_MIXED && o->precision != NBODY_PREC_PLAIN &&
+        o->precision != NBODY_PREC_MIXED_UNSORTED)
+        return NBODY_EINVAL;
     if (o->accumulate != NBODY_ACC_COMPENSATED && o->accumulate != NBODY_ACC_FP32 &&
         o->accumulate != NBODY_ACC_KAHAN_PAIR)
         return NBODY_EINVAL;
@@ -456,7 +460,28 @@ struct ForcePlan {
     double* partial;
     int* err;
     int num_sms;
+    int* perm = nullptr;            // spatial order of the bodies (mixed precision), or none
+    void* order_scratch = nullptr;
 };
+
+// Buffers of the spatial order (mixed precision sorts the bodies along a
+// Morton curve so that each cell is a compact region).
+int plan_order(Workspace* ws, int64_t n, ForcePlan* fp) {
+    void *p, *q;
+    NB_CHECK(ensure(ws, B_PERM, (size_t)n * sizeof(int), &p));
+    NB_CHECK(ensure(ws, B_ORDS, nbk::order_scratch_bytes(n), &q));
+    fp->perm = (int*)p;
+    fp->order_scratch = q;
+    return NBODY_OK;
+}
+
+int issue_order(const ForcePlan& fp, int64_t n, const double* pos, cudaStream_t st) {
+    count(14);
+    NB_CUDA(nbk::spatial_order(n, pos, fp.perm, fp.order_scratch, st));
+    return NBODY_OK;
+}
+
+bool sorted_mixed(int precision) { return precision == NBODY_PREC_MIXED; }
 
 int plan_force(Workspace* ws, int64_t n, int shape, int num_sms, ForcePlan* fp) {
     fp->shape = shape;
@@ -490,6 +515,7 @@ int run_force(const ForcePlan& fp, int64_t n, float eps2, bool mixed, int summat
     a.partial = fp.partial;
     a.err = fp.err;
     a.summation = summation;
+    a.perm = fp.perm;
     ProfPair pp;
     const bool timed = prof_pair(&pp);
     int launched = 0;
@@ -525,9 +551,13 @@ int accel_f64_dev(Ctx& c, int64_t n, const double* pos, const float* mass, doubl
     ForcePlan fp;
     NB_CHECK(plan_force(c.ws, n, shape_for(c, n, pot != nullptr), c.sms, &fp));
     const bool plain = c.o.precision == NBODY_PREC_PLAIN;
+    if (sorted_mixed(c.o.precision)) {
+        NB_CHECK(plan_order(c.ws, n, &fp));
+        NB_CHECK(issue_order(fp, n, pos, c.o.stream));
+    }
     count(1);
     NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, const_cast<double*>(pos), nullptr, nullptr, mass, 0.0, 0.0, plain,
-                          fp.jdup, fp.centres, c.o.stream));
+                          fp.jdup, fp.centres, c.o.stream, fp.perm));
     return run_force(fp, n, (float)(eps * eps), !plain, summation_mode(c.o.accumulate), acc, pot,
                      c.o.stream);
 }
@@ -626,10 +656,11 @@ static int leapfrog_issue(int64_t n, V* x, V* v, const float* m, double eps, dou
                           const ForcePlan& fp, float* a, bool plain, int comp, cudaStream_t st) {
     const bool f64 = sizeof(V) == sizeof(double);
     const float eps2 = f64 ? (float)(eps * eps) : (float)eps * (float)eps;
+    if (f64 && fp.perm != nullptr) NB_CHECK(issue_order(fp, n, (const double*)x, st));  // order of the call
     count(1);
     if (f64)
         NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, (double*)x, nullptr, nullptr, m, 0.0, 0.0, plain, fp.jdup,
-                              fp.centres, st));
+                              fp.centres, st, fp.perm));
     else
         NB_CUDA(nbk::pack_f32(n, fp.npad, (float*)x, nullptr, nullptr, m, 0.0f, 0.0f, fp.jdup, st));
     NB_CHECK(run_force(fp, n, eps2, f64 && !plain, comp, a, nullptr, st));
@@ -638,7 +669,7 @@ static int leapfrog_issue(int64_t n, V* x, V* v, const float* m, double eps, dou
         count(1);
         if (f64)
             NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, (double*)x, (double*)v, a, m, kick, dt, plain, fp.jdup,
-                                  fp.centres, st));
+                                  fp.centres, st, fp.perm));
         else
             NB_CUDA(nbk::pack_f32(n, fp.npad, (float*)x, (float*)v, a, m, (float)kick, (float)dt, fp.jdup, st));
         NB_CHECK(run_force(fp, n, eps2, f64 && !plain, comp, a, nullptr, st));
@@ -665,6 +696,7 @@ static int leapfrog_run(Ctx& c, int64_t n, V* x, V* v, const float* m, double ep
     const bool plain = sizeof(V) == sizeof(float) || c.o.precision == NBODY_PREC_PLAIN;
     const int comp = summation_mode(c.o.accumulate);
     cudaStream_t st = c.o.stream;
+    if (sizeof(V) == sizeof(double) && sorted_mixed(c.o.precision)) NB_CHECK(plan_order(c.ws, n, &fp));
     if (!graphable || g_prof_on.load() || getenv("NBODY_NO_GRAPH") != nullptr)
         return leapfrog_issue<V>(n, x, v, m, eps, dt, steps, fp, a, plain, comp, st);
     double e = eps, d = dt;
@@ -958,9 +990,13 @@ int nbody_leapfrog_record(int64_t n, double* pos, double* vel, const float* mass
     const bool plain = c.o.precision == NBODY_PREC_PLAIN;
     const int comp = summation_mode(c.o.accumulate);
     const float eps2 = (float)(eps * eps);
+    if (sorted_mixed(c.o.precision)) {  // the same order nbody_leapfrog takes (from x_0)
+        NB_CHECK(plan_order(c.ws, n, &fp));
+        NB_CHECK(issue_order(fp, n, pos, st));
+    }
     count(1);
     NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, pos, nullptr, nullptr, mass, 0.0, 0.0, plain, fp.jdup, fp.centres,
-                          st));
+                          st, fp.perm));
     NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, st));
     for (int64_t s = 0; s < steps; ++s) {
         const bool ck = (s % ckpt_every) == 0;
@@ -968,7 +1004,8 @@ int nbody_leapfrog_record(int64_t n, double* pos, double* vel, const float* mass
         if (ck) NB_CUDA(cudaMemcpyAsync(slot, pos, n3b, cudaMemcpyDeviceToDevice, st));
         const double kick = (s == 0) ? 0.5 * dt : dt;
         count(1);
-        NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, pos, vel, a, mass, kick, dt, plain, fp.jdup, fp.centres, st));
+        NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, pos, vel, a, mass, kick, dt, plain, fp.jdup, fp.centres, st,
+                              fp.perm));
         if (ck) NB_CUDA(cudaMemcpyAsync(slot + (size_t)n * 3, vel, n3b, cudaMemcpyDeviceToDevice, st));
         NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, st));
     }
@@ -1018,6 +1055,7 @@ int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, double dt, int6
     NB_CHECK(plan_vjp(c.ws, n, choose_vjp_shape(n), c.sms, &vp));
     ForcePlan fp;
     NB_CHECK(plan_force(c.ws, n, shape_for(c, n, false), c.sms, &fp));
+    if (sorted_mixed(c.o.precision)) NB_CHECK(plan_order(c.ws, n, &fp));
     void *pg, *pgm, *pa, *px, *pv;
     NB_CHECK(ensure(c.ws, B_VG, (size_t)n * 3 * sizeof(float), &pg));
     NB_CHECK(ensure(c.ws, B_VGM, (size_t)n * sizeof(float), &pgm));
@@ -1051,7 +1089,7 @@ int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, double dt, int6
             // x_k = x_{k-1} + dt v_{k-1/2}; v_{k-1/2} = v_{k-3/2} + dt a(x_{k-1}) for k > c0 + 1
             count(1);
             NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, xk, v, k > c0 + 1 ? a : nullptr, mass,
-                                  k > c0 + 1 ? dt : 0.0, dt, plain, fp.jdup, fp.centres, aux));
+                                  k > c0 + 1 ? dt : 0.0, dt, plain, fp.jdup, fp.centres, aux, fp.perm));
             if (k + 1 < c1) NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, aux));
         }
         NB_CUDA(cudaEventRecord(ev_rep[seg & 1], aux));
@@ -1059,6 +1097,7 @@ int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, double dt, int6
     };
     NB_CUDA(cudaEventRecord(ev_start, st));  // the tape and inputs are ready on the caller's stream
     NB_CUDA(cudaStreamWaitEvent(aux, ev_start, 0));
+    if (sorted_mixed(c.o.precision)) NB_CHECK(issue_order(fp, n, tp, aux));  // x_0's order, as recorded
     NB_CHECK(replay(nck - 1));
     if (nck >= 2) NB_CHECK(replay(nck - 2));
 

@@ -50,6 +50,7 @@ struct KParams {
     const float* ipack;     // sinks: == jdup when the sinks are the sources
     const double* icentres; // sink cell centres (mixed)
     int self;               // sinks are the sources: mask j == i in diagonal tiles
+    const int* perm;        // sink slot g holds body perm[g] (nullptr: slot g is body g)
     float eps2;
     int64_t n;              // sinks
     int64_t nblk;
@@ -277,10 +278,11 @@ __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
                 if (full) {
                     if (g < p.n) {
                         for (int k = 0; k < 4; ++k) v[h][k] = (float)d[h][k];
-                        p.acc[3 * g + 0] = v[h][0];
-                        p.acc[3 * g + 1] = v[h][1];
-                        p.acc[3 * g + 2] = v[h][2];
-                        if (POT) p.pot[g] = -v[h][3];
+                        const int64_t o = p.perm != nullptr ? (int64_t)p.perm[g] : g;
+                        p.acc[3 * o + 0] = v[h][0];
+                        p.acc[3 * o + 1] = v[h][1];
+                        p.acc[3 * o + 2] = v[h][2];
+                        if (POT) p.pot[o] = -v[h][3];
                     }
                 } else {
                     double4* dst = reinterpret_cast<double4*>(p.partial) + ((cta * 2 + slot) * C + lb);
@@ -325,10 +327,11 @@ __global__ void fixup_kernel(const KParams p, int C, int pot_on) {
             sz += v.z;
             sp += v.w;
         }
-        p.acc[3 * g + 0] = (float)sx;
-        p.acc[3 * g + 1] = (float)sy;
-        p.acc[3 * g + 2] = (float)sz;
-        if (pot_on) p.pot[g] = -(float)sp;
+        const int64_t o = p.perm != nullptr ? (int64_t)p.perm[g] : g;
+        p.acc[3 * o + 0] = (float)sx;
+        p.acc[3 * o + 1] = (float)sy;
+        p.acc[3 * o + 2] = (float)sz;
+        if (pot_on) p.pot[o] = -(float)sp;
     }
 }
 
@@ -442,13 +445,14 @@ size_t force_partial_doubles(int k, int num_sms) {
 }
 
 cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t ntile, int64_t nctas, int block, const double* partial,
-                        float* out3, float* out1, cudaStream_t st) {
+                        float* out3, float* out1, cudaStream_t st, const int* perm) {
     KParams p;
     p.jdup = nullptr;
     p.centres = nullptr;
     p.ipack = nullptr;
     p.icentres = nullptr;
     p.self = 1;
+    p.perm = perm;
     p.eps2 = 0.0f;
     p.n = n;
     p.nblk = nblk;
@@ -482,6 +486,7 @@ cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st
     p.ipack = a.ipack != nullptr ? a.ipack : a.jdup;
     p.icentres = a.ipack != nullptr ? a.icentres : a.centres;
     p.self = a.ipack == nullptr ? 1 : 0;
+    p.perm = a.perm;
     p.eps2 = a.eps2;
     p.n = a.n;
     p.nblk = (a.ipack != nullptr ? a.nipad : a.npad) / C;

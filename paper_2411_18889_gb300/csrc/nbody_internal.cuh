@@ -172,6 +172,7 @@ struct ForceArgs {
     const float* ipack = nullptr;     // [nipad][8]
     const double* icentres = nullptr; // sink cell centres (mixed)
     int64_t nipad = 0;
+    const int* perm = nullptr;        // sink slot k is body perm[k] (results go to perm[k])
     float* acc;             // [n][3]
     float* pot;             // [n] or nullptr
     double* partial;        // scratch, force_partial_doubles(...) doubles
@@ -185,7 +186,7 @@ size_t force_partial_doubles(int k, int num_sms);
 // one scalar) of every i-block a stream-K slice boundary cut, in CTA order, and
 // writes out3[3g..3g+2] and out1[g] = -(scalar) for those blocks.
 cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t ntile, int64_t nctas, int block, const double* partial,
-                        float* out3, float* out1, cudaStream_t st);
+                        float* out3, float* out1, cudaStream_t st, const int* perm = nullptr);
 
 // Exact scratch doubles force_launch needs for this variant and padded size
 // (its grid: resident CTAs on num_sms SMs, capped by the work units).
@@ -200,9 +201,10 @@ cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st
 // Pack kernels: build jdup (and cell centres) from the state, optionally
 // applying a kick (vel += kick * acc) and a drift (pos += drift * vel) first.
 // All FP64 state arithmetic for the mixed path happens here.
+// perm (optional): slot k of the packed array holds body perm[k].
 cudaError_t pack_f64(int64_t n, int64_t npad, int block, double* pos, double* vel, const float* acc,
                      const float* mass, double kick, double drift, bool plain, float* jdup,
-                     double* centres, cudaStream_t st);
+                     double* centres, cudaStream_t st, const int* perm = nullptr);
 cudaError_t pack_f32(int64_t n, int64_t npad, float* pos, float* vel, const float* acc,
                      const float* mass, float kick, float drift, float* jdup, cudaStream_t st);
 // vel += kick * acc (the closing half kick of a leapfrog call).
@@ -275,6 +277,12 @@ cudaError_t pack_vjp(int64_t n, int64_t npad, int block, const double* pos, cons
 cudaError_t adjoint_accumulate(int64_t n, double* lamx, const float* g, double* gm_acc, const float* gm,
                                cudaStream_t st);
 cudaError_t vjp_launch(int k, const VjpArgs& a, int num_sms, cudaStream_t st, int* launched);
+
+// ---- spatial order (order.cu) ----
+// perm[k] = index of the body at position k of the Morton order (stable, by
+// index within equal keys).  `scratch` holds order_scratch_bytes(n) bytes.
+size_t order_scratch_bytes(int64_t n);
+cudaError_t spatial_order(int64_t n, const double* pos, int* perm, void* scratch, cudaStream_t st);
 
 // One CTA waits on an mbarrier nothing completes, for limit_ns, then sets *err.
 cudaError_t selftest_wait(uint64_t limit_ns, int* err, cudaStream_t st);

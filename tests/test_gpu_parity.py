@@ -37,7 +37,8 @@ def gpu_accel(nb, api, pos, mass32, eps, with_pot=True, **kw):
     if api == "f32":
         nb.nbody_accel_f32(t(pos, np.float32), t(mass32, np.float32), np.float32(eps), acc, pot, **kw)
     else:
-        prec = nb.NBODY_PREC_MIXED if api == "mixed" else nb.NBODY_PREC_PLAIN
+        prec = {"mixed": nb.NBODY_PREC_MIXED, "plain": nb.NBODY_PREC_PLAIN,
+                "unsorted": nb.NBODY_PREC_MIXED_UNSORTED}[api]
         nb.nbody_accel(t(pos, np.float64), t(mass32, np.float32), eps, acc, pot, precision=prec, **kw)
     torch.cuda.synchronize()
     assert nb.nbody_last_device_error() == 0
@@ -58,7 +59,7 @@ def check(acc, pot, ra, rp, med=ACC_MED, mx=ACC_MAX, pmx=POT_MAX):
         assert ep.max() <= pmx, f"max rel pot err {ep.max():.3g}"
 
 
-@pytest.mark.parametrize("api", ["f32", "mixed", "plain"])
+@pytest.mark.parametrize("api", ["f32", "mixed", "plain", "unsorted"])
 @pytest.mark.parametrize("n", [2, 3, 31, 257, 1000, 2500, 4097])
 def test_accel_matches_oracle(nb, oracle_mod, api, n):
     p, _, m = ni.plummer(n, 1000 + n, masses="loguniform")
@@ -246,3 +247,21 @@ def test_kahan_per_pair_mode(nb, oracle_mod):
     # at this size the sums' rounding is below the pair arithmetic's, so the
     # three modes differ by noise; the FP32 running sum's gap shows at large n
     assert errs[nb.NBODY_ACC_COMPENSATED] <= 1.2 * errs[nb.NBODY_ACC_FP32]
+
+
+def test_morton_order_shrinks_close_pair_errors(nb, oracle_mod):
+    """All 65536 bodies of an offset sphere: in the caller's order a cell spans
+    the system and close pairs carry FP32 offset rounding of the system's size
+    (worst body ~1.8e-4 relative); in the default Morton order cells are compact
+    and the worst body stays within the 1e-4 bound."""
+    n = 65536
+    p, _, m = ni.plummer(n, 4242 + n, masses="loguniform", offset=(1e4, -3e3, 7e2))
+    m32 = m.astype(np.float32)
+    ra, rp = oracle_mod.accel(p, m32.astype(np.float64), 2.0 ** -9)
+    acc_s, pot_s = gpu_accel(nb, "mixed", p, m32, 2.0 ** -9)
+    acc_u, _ = gpu_accel(nb, "unsorted", p, m32, 2.0 ** -9, with_pot=False)
+    es, eu = rel_err(acc_s, ra), rel_err(acc_u, ra)
+    print(f"all bodies: sorted median {np.median(es):.3g} max {es.max():.3g}; "
+          f"caller's order median {np.median(eu):.3g} max {eu.max():.3g}")
+    check(acc_s, pot_s, ra, rp)
+    assert es.max() < 0.5 * eu.max()

@@ -5,7 +5,7 @@ processes), with all scratch in the library's fixed device array.
 Called through the C ABI (ctypes) on device arrays and compared with
 nbody_accel's output on two calls in a row, within the parity tolerances of
 the other GPU tests.  nbody_accel runs with the same kernel shape (1024-body
-i-blocks) as the static-scratch variant: bodies with a neighbour far inside
+i-blocks) and cell order (the caller's) as the static-scratch variant: bodies with a neighbour far inside
 the softening length carry FP32 coordinate-rounding errors of up to ~2e-4
 relative in every shape, and two shapes that round differently would compare
 those errors with each other rather than the two entry points.  The file
@@ -49,7 +49,7 @@ def test_noalloc_matches_accel_twice(nb, n, with_pot):
     # reference: the allocating entry point
     acc_ref = torch.empty((n, 3), dtype=torch.float32, device="cuda")
     pot_ref = torch.empty((n,), dtype=torch.float32, device="cuda") if with_pot else None
-    nb.nbody_accel(P, M, eps, acc_ref, pot_ref, config=NOALLOC_SHAPE)
+    nb.nbody_accel(P, M, eps, acc_ref, pot_ref, config=NOALLOC_SHAPE, precision=nb.NBODY_PREC_MIXED_UNSORTED)
     torch.cuda.synchronize()
     acc_ref = acc_ref.cpu().numpy()
     pot_ref = pot_ref.cpu().numpy() if with_pot else None
