@@ -62,6 +62,7 @@ extern "C" {
 #define NBODY_ECUDA (-3)    /* a CUDA runtime call failed; see nbody_last_cuda_error() */
 #define NBODY_ETIMEOUT (-4) /* a bounded device-side wait expired (kernel returned early) */
 #define NBODY_ENOTSUP (-5)  /* no usable sm_103 device or unsupported option */
+#define NBODY_EBOUNDS (-6)  /* a kernel of a checked build (-DNBODY_CHECKS) met an index out of range */
 
 /* Pair arithmetic precision. */
 #define NBODY_PREC_MIXED 0 /* FP64 positions; FP32 pair math on coordinates
@@ -231,8 +232,10 @@ NBODY_API int nbody_tune_load(const char* path);
 NBODY_API int nbody_tuned_shape(int kind, int64_t n, int pot);
 
 /* Synchronise the current device and report whether any kernel since the
- * last call hit a bounded-wait timeout (NBODY_ETIMEOUT) -- the flag is then
- * cleared -- or a CUDA error (NBODY_ECUDA); NBODY_OK otherwise. */
+ * last call hit a bounded-wait timeout (NBODY_ETIMEOUT) or, in a checked
+ * build, an index out of range (NBODY_EBOUNDS; the access was skipped) --
+ * the flag is then cleared -- or a CUDA error (NBODY_ECUDA); NBODY_OK
+ * otherwise. */
 NBODY_API int nbody_last_device_error(void);
 
 /* The last CUDA runtime error code seen by the library on this thread. */
@@ -273,7 +276,8 @@ NBODY_API int nbody_selftest_wait(double limit_seconds, const nbody_opts* opts);
  *  float or NULL: device (or managed) memory only -- host arrays would need
  *  staging buffers, so they return NBODY_EINVAL.
  *  status: NULL, or a device int the call sets to 0 and its kernels set to 1
- *  if a bounded device-side wait expired (results then incomplete).
+ *  if a bounded device-side wait expired (results then incomplete), or to 2
+ *  in a checked build (-DNBODY_CHECKS) if an index was out of range.
  *  stream: cudaStream_t to run on (NULL = legacy default stream); the call
  *  is asynchronous.
  *

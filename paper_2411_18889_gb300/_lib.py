@@ -19,6 +19,7 @@ NBODY_ENOMEM = -2
 NBODY_ECUDA = -3
 NBODY_ETIMEOUT = -4
 NBODY_ENOTSUP = -5
+NBODY_EBOUNDS = -6
 NBODY_PREC_MIXED = 0
 NBODY_PREC_PLAIN = 1
 NBODY_PREC_MIXED_UNSORTED = 2
@@ -82,20 +83,24 @@ def header_functions(path: str = HEADER):
                                  flags=re.M)))
 
 
-def load():
-    """Load libnbody.so (build it first: paper_2411_18889_gb300.build)."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    if not os.path.exists(LIB_PATH):
-        raise ImportError(f"libnbody.so is not built ({LIB_PATH}); run paper_2411_18889_gb300.build.build()")
-    lib = ctypes.CDLL(LIB_PATH)
+def open_library(path: str):
+    """ctypes handle of a build of the library at `path`, signatures set."""
+    if not os.path.exists(path):
+        raise ImportError(f"libnbody.so is not built ({path}); run paper_2411_18889_gb300.build.build()")
+    lib = ctypes.CDLL(path)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    _lib = lib
     return lib
+
+
+def load():
+    """Load libnbody.so (build it first: paper_2411_18889_gb300.build)."""
+    global _lib
+    if _lib is None:
+        _lib = open_library(LIB_PATH)
+    return _lib
 
 
 def strerror(code: int) -> str:

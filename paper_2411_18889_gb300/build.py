@@ -8,6 +8,7 @@ paper_2411_18889_gb300.build`` runs it from the command line.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import hashlib
 import os
 import shutil
 import subprocess
@@ -54,7 +55,7 @@ def build(force: bool = False, extra=(), lib_path: str = LIB, verbose: bool = Fa
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "nbody.h"))
-    tag = "" if not extra else "_" + str(abs(hash(tuple(extra))) % 10 ** 8)
+    tag = "" if not extra else "_" + hashlib.sha1(" ".join(extra).encode()).hexdigest()[:8]
     objs, jobs = [], []
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         for src in SOURCES:

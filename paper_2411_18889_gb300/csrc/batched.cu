@@ -50,6 +50,8 @@ struct BParams {
     float* pot;              // [N] or nullptr (force only)
     float dt;
     int64_t steps;           // 0: force only
+    int64_t ntot;            // bodies over all systems
+    int* err;                // error word (checked builds record index faults)
 };
 
 template <int T, int I, bool POT, bool MASK>
@@ -126,6 +128,7 @@ __device__ __forceinline__ void eval_pass(const float* __restrict__ sj, int npai
         upk(tz[k], a0, a1);
         const float az_ = a0 + a1;
         const int64_t g = off + ib[k];
+        if (!in_range(g, p.ntot, p.err)) continue;
         if (p.steps == 0) {
             p.acc[3 * g + 0] = ax_;
             p.acc[3 * g + 1] = ay_;
@@ -186,7 +189,7 @@ __device__ __forceinline__ void load_system(float* sj, const BParams& p, int64_t
     const int nb = (ns + 1) & ~1;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         float x = kPadPos, y = kPadPos, z = kPadPos, m = 0.0f;
-        if (b < ns) {
+        if (b < ns && in_range(off + b, p.ntot, p.err)) {
             const int64_t g = off + b;
             x = p.pos[3 * g + 0];
             y = p.pos[3 * g + 1];
@@ -212,6 +215,7 @@ __global__ void __launch_bounds__(T) batched_kernel(const BParams p) {
         __syncthreads();
         if (k >= p.nsys) break;
         const int s = p.order[k];
+        if (!in_range(s, p.nsys, p.err)) continue;
         const int64_t off = p.offsets[s];
         const int ns = (int)(p.offsets[s + 1] - off);
         if (ns <= 0) continue;
@@ -300,6 +304,8 @@ cudaError_t batched_launch(int k, const BatchArgs& a, int num_sms, cudaStream_t 
     p.pot = a.pot;
     p.dt = a.dt;
     p.steps = a.steps;
+    p.ntot = a.ntot;
+    p.err = a.err;
     const int64_t grid = std::min<int64_t>((int64_t)num_sms * occ, std::max<int64_t>(a.nsys, 1));
     err = cudaMemsetAsync(a.queue, 0, sizeof(int), st);
     if (err != cudaSuccess) return err;

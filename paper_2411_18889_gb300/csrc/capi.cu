@@ -557,7 +557,7 @@ int accel_f64_dev(Ctx& c, int64_t n, const double* pos, const float* mass, doubl
     }
     count(1);
     NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, const_cast<double*>(pos), nullptr, nullptr, mass, 0.0, 0.0, plain,
-                          fp.jdup, fp.centres, c.o.stream, fp.perm));
+                          fp.jdup, fp.centres, c.o.stream, fp.perm, fp.err));
     return run_force(fp, n, (float)(eps * eps), !plain, summation_mode(c.o.accumulate), acc, pot,
                      c.o.stream);
 }
@@ -603,6 +603,7 @@ const char* nbody_strerror(int code) {
         case NBODY_ENOMEM: return "out of memory";
         case NBODY_ECUDA: return "CUDA runtime error";
         case NBODY_ETIMEOUT: return "bounded device wait expired";
+        case NBODY_EBOUNDS: return "device index out of range (checked build)";
         case NBODY_ENOTSUP: return "unsupported device or option";
         default: return "unknown error code";
     }
@@ -660,7 +661,7 @@ static int leapfrog_issue(int64_t n, V* x, V* v, const float* m, double eps, dou
     count(1);
     if (f64)
         NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, (double*)x, nullptr, nullptr, m, 0.0, 0.0, plain, fp.jdup,
-                              fp.centres, st, fp.perm));
+                              fp.centres, st, fp.perm, fp.err));
     else
         NB_CUDA(nbk::pack_f32(n, fp.npad, (float*)x, nullptr, nullptr, m, 0.0f, 0.0f, fp.jdup, st));
     NB_CHECK(run_force(fp, n, eps2, f64 && !plain, comp, a, nullptr, st));
@@ -669,7 +670,7 @@ static int leapfrog_issue(int64_t n, V* x, V* v, const float* m, double eps, dou
         count(1);
         if (f64)
             NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, (double*)x, (double*)v, a, m, kick, dt, plain, fp.jdup,
-                                  fp.centres, st, fp.perm));
+                                  fp.centres, st, fp.perm, fp.err));
         else
             NB_CUDA(nbk::pack_f32(n, fp.npad, (float*)x, (float*)v, a, m, (float)kick, (float)dt, fp.jdup, st));
         NB_CHECK(run_force(fp, n, eps2, f64 && !plain, comp, a, nullptr, st));
@@ -996,7 +997,7 @@ int nbody_leapfrog_record(int64_t n, double* pos, double* vel, const float* mass
     }
     count(1);
     NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, pos, nullptr, nullptr, mass, 0.0, 0.0, plain, fp.jdup, fp.centres,
-                          st, fp.perm));
+                          st, fp.perm, fp.err));
     NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, st));
     for (int64_t s = 0; s < steps; ++s) {
         const bool ck = (s % ckpt_every) == 0;
@@ -1005,7 +1006,7 @@ int nbody_leapfrog_record(int64_t n, double* pos, double* vel, const float* mass
         const double kick = (s == 0) ? 0.5 * dt : dt;
         count(1);
         NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, pos, vel, a, mass, kick, dt, plain, fp.jdup, fp.centres, st,
-                              fp.perm));
+                              fp.perm, fp.err));
         if (ck) NB_CUDA(cudaMemcpyAsync(slot + (size_t)n * 3, vel, n3b, cudaMemcpyDeviceToDevice, st));
         NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, st));
     }
@@ -1089,7 +1090,7 @@ int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, double dt, int6
             // x_k = x_{k-1} + dt v_{k-1/2}; v_{k-1/2} = v_{k-3/2} + dt a(x_{k-1}) for k > c0 + 1
             count(1);
             NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, xk, v, k > c0 + 1 ? a : nullptr, mass,
-                                  k > c0 + 1 ? dt : 0.0, dt, plain, fp.jdup, fp.centres, aux, fp.perm));
+                                  k > c0 + 1 ? dt : 0.0, dt, plain, fp.jdup, fp.centres, aux, fp.perm, fp.err));
             if (k + 1 < c1) NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, aux));
         }
         NB_CUDA(cudaEventRecord(ev_rep[seg & 1], aux));
@@ -1185,7 +1186,7 @@ static int batched_common(int64_t nsys, const int64_t* offsets, float* pos, floa
     sg.add(acc, leapfrog ? 0 : (size_t)ntot * 3 * sizeof(float), false, !leapfrog);
     sg.add(pot, (leapfrog || pot == nullptr) ? 0 : (size_t)ntot * sizeof(float), false, !leapfrog);
     NB_CHECK(sg.prepare());
-    void *po, *pq;
+    void *po, *pq, *pe;
     NB_CHECK(ensure(c.ws, B_ORDER, order.size() * sizeof(int), &po));
     NB_CHECK(ensure(c.ws, B_QUEUE, sizeof(int), &pq));
     NB_CUDA(cudaMemcpyAsync(po, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -1204,6 +1205,9 @@ static int batched_common(int64_t nsys, const int64_t* offsets, float* pos, floa
     a.dt = dt;
     a.steps = leapfrog ? steps : 0;
     a.max_ns = (int)max_ns;
+    a.ntot = ntot;
+    NB_CHECK(ensure(c.ws, B_ERR, sizeof(int), &pe));
+    a.err = (int*)pe;
     const int shape = c.o.config >= 0 ? c.o.config : tuned_shape(2, max_ns, 0);
     count(1);
     NB_CUDA(nbk::batched_launch(shape, a, c.sms, st));
@@ -1283,7 +1287,7 @@ int nbody_last_device_error(void) {
         int flag = 0;
         NB_CUDA(cudaMemcpy(&flag, w->buf[B_ERR].p, sizeof(int), cudaMemcpyDeviceToHost));
         if (flag != 0) {
-            result = NBODY_ETIMEOUT;
+            result = flag == 2 ? NBODY_EBOUNDS : NBODY_ETIMEOUT;
             NB_CUDA(cudaMemset(w->buf[B_ERR].p, 0, sizeof(int)));
         }
     }

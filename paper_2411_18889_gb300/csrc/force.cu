@@ -151,7 +151,8 @@ __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
     __syncthreads();
 
     auto issue = [&](int s, int64_t unit) {
-        const int64_t tile = unit % p.ntile;
+        int64_t tile = unit % p.ntile;
+        if (!in_range(tile, p.ntile, p.err)) tile = 0;
         mbar_expect_tx(&bar[s], TILE_BYTES);
         bulk_g2s(tiles + s * TILE_BYTES, p.jdup + tile * (int64_t)J * kJdupFloats, TILE_BYTES, &bar[s]);
     };
@@ -175,8 +176,11 @@ __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
         f2 xi[IP], yi[IP], zi[IP];
 #pragma unroll
         for (int q = 0; q < IP; ++q) {
-            const float* a0 = p.ipack + (base + (2 * q) * T + tid) * kJdupFloats;
-            const float* a1 = p.ipack + (base + (2 * q + 1) * T + tid) * kJdupFloats;
+            int64_t s0 = base + (2 * q) * T + tid, s1 = s0 + T;
+            if (!in_range(s0, p.nblk * C, p.err)) s0 = 0;
+            if (!in_range(s1, p.nblk * C, p.err)) s1 = 0;
+            const float* a0 = p.ipack + s0 * kJdupFloats;
+            const float* a1 = p.ipack + s1 * kJdupFloats;
             xi[q] = pk(a0[0], a1[0]);
             yi[q] = pk(a0[2], a1[2]);
             zi[q] = pk(a0[4], a1[4]);
@@ -279,13 +283,16 @@ __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
                     if (g < p.n) {
                         for (int k = 0; k < 4; ++k) v[h][k] = (float)d[h][k];
                         const int64_t o = p.perm != nullptr ? (int64_t)p.perm[g] : g;
+                        if (!in_range(o, p.n, p.err)) continue;
                         p.acc[3 * o + 0] = v[h][0];
                         p.acc[3 * o + 1] = v[h][1];
                         p.acc[3 * o + 2] = v[h][2];
                         if (POT) p.pot[o] = -v[h][3];
                     }
                 } else {
-                    double4* dst = reinterpret_cast<double4*>(p.partial) + ((cta * 2 + slot) * C + lb);
+                    const int64_t pi = (cta * 2 + slot) * C + lb;
+                    if (!in_range(pi, p.nctas * 2 * C, p.err)) continue;
+                    double4* dst = reinterpret_cast<double4*>(p.partial) + pi;
                     *dst = make_double4(d[h][0], d[h][1], d[h][2], d[h][3]);
                 }
             }
@@ -321,13 +328,16 @@ __global__ void fixup_kernel(const KParams p, int C, int pot_on) {
         for (int64_t c = c_lo; c <= c_hi; ++c) {
             const int64_t ub = c * p.units / p.nctas;
             const int slot = (ub / p.ntile == b) ? 0 : 1;
-            const double4 v = reinterpret_cast<const double4*>(p.partial)[(c * 2 + slot) * C + lb];
+            const int64_t pi = (c * 2 + slot) * C + lb;
+            if (!in_range(pi, p.nctas * 2 * C, p.err)) continue;
+            const double4 v = reinterpret_cast<const double4*>(p.partial)[pi];
             sx += v.x;
             sy += v.y;
             sz += v.z;
             sp += v.w;
         }
         const int64_t o = p.perm != nullptr ? (int64_t)p.perm[g] : g;
+        if (!in_range(o, p.n, p.err)) continue;
         p.acc[3 * o + 0] = (float)sx;
         p.acc[3 * o + 1] = (float)sy;
         p.acc[3 * o + 2] = (float)sz;
@@ -445,7 +455,7 @@ size_t force_partial_doubles(int k, int num_sms) {
 }
 
 cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t ntile, int64_t nctas, int block, const double* partial,
-                        float* out3, float* out1, cudaStream_t st, const int* perm) {
+                        float* out3, float* out1, cudaStream_t st, const int* perm, int* err) {
     KParams p;
     p.jdup = nullptr;
     p.centres = nullptr;
@@ -462,7 +472,7 @@ cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t ntile, int64_t nctas, i
     p.acc = out3;
     p.pot = out1;
     p.partial = const_cast<double*>(partial);
-    p.err = nullptr;
+    p.err = err;
     fixup_kernel<<<(unsigned)nblk, 256, 0, st>>>(p, block, out1 != nullptr ? 1 : 0);
     return cudaGetLastError();
 }

@@ -138,6 +138,23 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 // lets the kernel return (no trap, no endless spin).
 constexpr uint64_t kWaitLimitNs = 4000000000ull;
 constexpr int kErrTimeout = 1;
+constexpr int kErrBounds = 2;
+
+// Checked builds (-DNBODY_CHECKS, the stand-in for a memory sanitizer): every
+// computed global index is tested before use; an index out of range records
+// kErrBounds in the error word and the access is skipped.  In normal builds
+// the test folds away.
+#ifdef NBODY_CHECKS
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+__device__ __forceinline__ bool in_range(int64_t i, int64_t n, int* err) {
+    if (!kChecked) return true;
+    if (i >= 0 && i < n) return true;
+    if (err != nullptr) atomicCAS(err, 0, kErrBounds);
+    return false;
+}
 
 // Wait for phase `parity` of `bar`; false if the limit expired.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
@@ -186,7 +203,8 @@ size_t force_partial_doubles(int k, int num_sms);
 // one scalar) of every i-block a stream-K slice boundary cut, in CTA order, and
 // writes out3[3g..3g+2] and out1[g] = -(scalar) for those blocks.
 cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t ntile, int64_t nctas, int block, const double* partial,
-                        float* out3, float* out1, cudaStream_t st, const int* perm = nullptr);
+                        float* out3, float* out1, cudaStream_t st, const int* perm = nullptr,
+                        int* err = nullptr);
 
 // Exact scratch doubles force_launch needs for this variant and padded size
 // (its grid: resident CTAs on num_sms SMs, capped by the work units).
@@ -204,7 +222,7 @@ cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st
 // perm (optional): slot k of the packed array holds body perm[k].
 cudaError_t pack_f64(int64_t n, int64_t npad, int block, double* pos, double* vel, const float* acc,
                      const float* mass, double kick, double drift, bool plain, float* jdup,
-                     double* centres, cudaStream_t st, const int* perm = nullptr);
+                     double* centres, cudaStream_t st, const int* perm = nullptr, int* err = nullptr);
 cudaError_t pack_f32(int64_t n, int64_t npad, float* pos, float* vel, const float* acc,
                      const float* mass, float kick, float drift, float* jdup, cudaStream_t st);
 // vel += kick * acc (the closing half kick of a leapfrog call).
@@ -238,6 +256,8 @@ struct BatchArgs {
     float dt;
     int64_t steps;  // 0: force only (acc, pot); > 0: leapfrog in place
     int max_ns;     // largest system (sizes the shared-memory image)
+    int64_t ntot;   // bodies over all systems
+    int* err;       // error word
 };
 int batched_num_shapes();
 BatchShape batched_shape(int k);

@@ -32,7 +32,8 @@ __global__ void __launch_bounds__(256) pack_f64_kernel(int64_t n, int block, dou
                                                        double* __restrict__ vel, const float* __restrict__ acc,
                                                        const float* __restrict__ mass, double kick, double drift,
                                                        int plain, float* __restrict__ jdup,
-                                                       double* __restrict__ centres, const int* __restrict__ perm) {
+                                                       double* __restrict__ centres, const int* __restrict__ perm,
+                                                       int* __restrict__ err) {
     __shared__ double red[3][8];
     __shared__ double cen[3];
     const int64_t base = (int64_t)blockIdx.x * block;
@@ -41,7 +42,8 @@ __global__ void __launch_bounds__(256) pack_f64_kernel(int64_t n, int block, dou
     for (int lb = tid; lb < block; lb += blockDim.x) {
         const int64_t k = base + lb;
         if (k >= n) break;
-        const int64_t g = perm != nullptr ? perm[k] : k;  // body in slot k
+        int64_t g = perm != nullptr ? perm[k] : k;  // body in slot k
+        if (!in_range(g, n, err)) g = k;
         double x = pos[3 * g + 0], y = pos[3 * g + 1], z = pos[3 * g + 2];
         if (vel != nullptr && (kick != 0.0 || drift != 0.0)) {
             double vx = vel[3 * g + 0], vy = vel[3 * g + 1], vz = vel[3 * g + 2];
@@ -94,7 +96,8 @@ __global__ void __launch_bounds__(256) pack_f64_kernel(int64_t n, int block, dou
     for (int lb = tid; lb < block; lb += blockDim.x) {
         const int64_t k = base + lb;
         if (k < n) {
-            const int64_t g = perm != nullptr ? perm[k] : k;
+            int64_t g = perm != nullptr ? perm[k] : k;
+            if (!in_range(g, n, err)) g = k;
             store_jdup(jdup, k, (float)(pos[3 * g + 0] - cx), (float)(pos[3 * g + 1] - cy),
                        (float)(pos[3 * g + 2] - cz), mass != nullptr ? mass[g] : 0.0f);
         } else {
@@ -153,10 +156,10 @@ unsigned grid_for(int64_t work, int threads) {
 
 cudaError_t pack_f64(int64_t n, int64_t npad, int block, double* pos, double* vel, const float* acc,
                      const float* mass, double kick, double drift, bool plain, float* jdup, double* centres,
-                     cudaStream_t st, const int* perm) {
+                     cudaStream_t st, const int* perm, int* err) {
     const unsigned nblk = (unsigned)(npad / block);
     pack_f64_kernel<<<nblk, 256, 0, st>>>(n, block, pos, vel, acc, mass, kick, drift, plain ? 1 : 0, jdup,
-                                          centres, perm);
+                                          centres, perm, err);
     return cudaGetLastError();
 }
 

@@ -131,7 +131,8 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
     }
     __syncthreads();
     auto issue = [&](int s, int64_t unit) {
-        const int64_t tile = unit % p.ntile;
+        int64_t tile = unit % p.ntile;
+        if (!in_range(tile, p.ntile, p.err)) tile = 0;
         mbar_expect_tx(&bar[s], TILE_BYTES);
         bulk_g2s(tiles + s * TILE_BYTES, p.jv + tile * (int64_t)J * kVjpFloats, TILE_BYTES, &bar[s]);
     };
@@ -153,8 +154,11 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
         f2 xi[IP], yi[IP], zi[IP], nlx[IP], nly[IP], nlz[IP], mi[IP], nmi[IP], nmui[IP];
 #pragma unroll
         for (int q = 0; q < IP; ++q) {
-            const float* a0 = p.jv + (base + (2 * q) * T + tid) * kVjpFloats;
-            const float* a1 = p.jv + (base + (2 * q + 1) * T + tid) * kVjpFloats;
+            int64_t s0 = base + (2 * q) * T + tid, s1 = s0 + T;
+            if (!in_range(s0, p.nblk * C, p.err)) s0 = 0;
+            if (!in_range(s1, p.nblk * C, p.err)) s1 = 0;
+            const float* a0 = p.jv + s0 * kVjpFloats;
+            const float* a1 = p.jv + s1 * kVjpFloats;
             xi[q] = pk(a0[0], a1[0]);
             yi[q] = pk(a0[2], a1[2]);
             zi[q] = pk(a0[4], a1[4]);
@@ -234,13 +238,16 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
                 const int64_t g = base + lb;
                 if (full) {
                     if (g < p.n) {
+                        if (!in_range(g, p.n, p.err)) continue;
                         p.g_pos[3 * g + 0] = v[h][0];
                         p.g_pos[3 * g + 1] = v[h][1];
                         p.g_pos[3 * g + 2] = v[h][2];
                         p.g_mass[g] = -v[h][3];
                     }
                 } else {
-                    double4* dst = reinterpret_cast<double4*>(p.partial) + ((cta * 2 + slot) * C + lb);
+                    const int64_t pi = (cta * 2 + slot) * C + lb;
+                    if (!in_range(pi, p.nctas * 2 * C, p.err)) continue;
+                    double4* dst = reinterpret_cast<double4*>(p.partial) + pi;
                     *dst = make_double4(v[h][0], v[h][1], v[h][2], v[h][3]);
                 }
             }
@@ -467,7 +474,7 @@ cudaError_t vjp_launch(int k, const VjpArgs& a, int num_sms, cudaStream_t st, in
     if (err != cudaSuccess) return err;
     *launched = 1;
     if (p.nctas > 1) {
-        err = split_fixup(p.n, p.nblk, p.ntile, p.nctas, C, p.partial, p.g_pos, p.g_mass, st);
+        err = split_fixup(p.n, p.nblk, p.ntile, p.nctas, C, p.partial, p.g_pos, p.g_mass, st, nullptr, p.err);
         if (err == cudaSuccess) *launched = 2;
     }
     return err;
