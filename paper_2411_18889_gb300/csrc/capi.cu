@@ -158,7 +158,7 @@ struct Workspace {
     cudaStream_t aux = nullptr;  // second stream (adjoint replay), created on first use
     cudaEvent_t ev[5] = {};      // ordering events between the two streams
     uint64_t gen = 0;            // bumped whenever a buffer moves (invalidates cached graphs)
-    cudaStream_t cap = nullptr;  // private stream that leapfrog graphs are captured on
+    cudaStream_t cap = nullptr;  // private stream that repeated calls are captured on
     std::map<std::vector<uint64_t>, struct GraphEntry*> graphs;
     uint64_t tick = 0;
 };
@@ -686,6 +686,64 @@ static int leapfrog_issue(int64_t n, V* x, V* v, const float* m, double eps, dou
 // A call repeated with the same arguments and workspace (the loop of a
 // simulation) is captured, on its second occurrence, into a CUDA graph that
 // later occurrences launch as one unit; the first occurrence runs directly.
+// `key` names everything the launch sequence depends on besides the contents
+// of the buffers it reads; issue(stream) queues that sequence.
+template <typename F>
+static int run_graphed(Ctx& c, std::vector<uint64_t> key, bool graphable, F issue) {
+    cudaStream_t st = c.o.stream;
+    if (!graphable || g_prof_on.load() || getenv("NBODY_NO_GRAPH") != nullptr) return issue(st);
+    key.push_back(c.ws->gen);
+    auto found = c.ws->graphs.find(key);
+    if (found == c.ws->graphs.end()) {
+        // keep at most 16 entries (captured or only seen) per workspace:
+        // drop the least recently used before adding one
+        if (c.ws->graphs.size() >= 16) {
+            auto victim = c.ws->graphs.begin();
+            for (auto it = c.ws->graphs.begin(); it != c.ws->graphs.end(); ++it)
+                if (it->second->last < victim->second->last) victim = it;
+            drop_graph(victim->second);
+            c.ws->graphs.erase(victim);
+        }
+        found = c.ws->graphs.emplace(key, new GraphEntry()).first;
+    }
+    GraphEntry* ge = found->second;
+    ge->last = ++c.ws->tick;
+    if (ge->exec != nullptr) {
+        NB_CUDA(cudaGraphLaunch(ge->exec, st));
+        count(ge->kernels);
+        return NBODY_OK;
+    }
+    if (ge->seen++ == 0) return issue(st);
+    if (c.ws->cap == nullptr) NB_CUDA(cudaStreamCreateWithFlags(&c.ws->cap, cudaStreamNonBlocking));
+    NB_CUDA(cudaStreamBeginCapture(c.ws->cap, cudaStreamCaptureModeThreadLocal));
+    t_capturing = true;
+    t_captured = 0;
+    const int rc = issue(c.ws->cap);
+    t_capturing = false;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c.ws->cap, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (rc != NBODY_OK || ec != cudaSuccess || graph == nullptr ||
+        cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (graph) (void)cudaGraphDestroy(graph);
+        ge->seen = 1;  // try again next time; run this call directly
+        return issue(st);
+    }
+    ge->graph = graph;
+    ge->exec = exec;
+    ge->kernels = t_captured;
+    NB_CUDA(cudaGraphLaunch(exec, st));
+    count(ge->kernels);
+    return NBODY_OK;
+}
+
+static uint64_t bits_of(double x) {
+    uint64_t b;
+    memcpy(&b, &x, 8);
+    return b;
+}
+
 template <typename V>
 static int leapfrog_run(Ctx& c, int64_t n, V* x, V* v, const float* m, double eps, double dt, int64_t steps,
                         bool graphable) {
@@ -696,58 +754,14 @@ static int leapfrog_run(Ctx& c, int64_t n, V* x, V* v, const float* m, double ep
     float* a = (float*)p;
     const bool plain = sizeof(V) == sizeof(float) || c.o.precision == NBODY_PREC_PLAIN;
     const int comp = summation_mode(c.o.accumulate);
-    cudaStream_t st = c.o.stream;
     if (sizeof(V) == sizeof(double) && sorted_mixed(c.o.precision)) NB_CHECK(plan_order(c.ws, n, &fp));
-    if (!graphable || g_prof_on.load() || getenv("NBODY_NO_GRAPH") != nullptr)
-        return leapfrog_issue<V>(n, x, v, m, eps, dt, steps, fp, a, plain, comp, st);
-    double e = eps, d = dt;
-    uint64_t be, bd;
-    memcpy(&be, &e, 8);
-    memcpy(&bd, &d, 8);
-    const std::vector<uint64_t> key = {(uint64_t)sizeof(V), (uint64_t)n, (uint64_t)steps, (uint64_t)(uintptr_t)x,
-                                       (uint64_t)(uintptr_t)v, (uint64_t)(uintptr_t)m, be, bd,
-                                       (uint64_t)fp.shape, (uint64_t)plain, (uint64_t)comp, c.ws->gen};
-    GraphEntry*& ge = c.ws->graphs[key];
-    if (ge == nullptr) ge = new GraphEntry();
-    ge->last = ++c.ws->tick;
-    if (ge->exec != nullptr) {
-        NB_CUDA(cudaGraphLaunch(ge->exec, st));
-        count(ge->kernels);
-        return NBODY_OK;
-    }
-    if (ge->seen++ == 0) return leapfrog_issue<V>(n, x, v, m, eps, dt, steps, fp, a, plain, comp, st);
-    if (c.ws->cap == nullptr) NB_CUDA(cudaStreamCreateWithFlags(&c.ws->cap, cudaStreamNonBlocking));
-    NB_CUDA(cudaStreamBeginCapture(c.ws->cap, cudaStreamCaptureModeThreadLocal));
-    t_capturing = true;
-    t_captured = 0;
-    const int rc = leapfrog_issue<V>(n, x, v, m, eps, dt, steps, fp, a, plain, comp, c.ws->cap);
-    t_capturing = false;
-    cudaGraph_t graph = nullptr;
-    const cudaError_t ec = cudaStreamEndCapture(c.ws->cap, &graph);
-    cudaGraphExec_t exec = nullptr;
-    if (rc != NBODY_OK || ec != cudaSuccess || graph == nullptr ||
-        cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
-        (void)cudaGetLastError();
-        if (graph) (void)cudaGraphDestroy(graph);
-        ge->seen = 1;  // try again next time; run this call directly
-        return leapfrog_issue<V>(n, x, v, m, eps, dt, steps, fp, a, plain, comp, st);
-    }
-    ge->graph = graph;
-    ge->exec = exec;
-    ge->kernels = t_captured;
-    // keep at most 16 graphs per workspace: drop the least recently used
-    if (c.ws->graphs.size() > 16) {
-        auto victim = c.ws->graphs.begin();
-        for (auto it = c.ws->graphs.begin(); it != c.ws->graphs.end(); ++it)
-            if (it->second->last < victim->second->last) victim = it;
-        if (victim->second != ge) {
-            drop_graph(victim->second);
-            c.ws->graphs.erase(victim);
-        }
-    }
-    NB_CUDA(cudaGraphLaunch(exec, st));
-    count(ge->kernels);
-    return NBODY_OK;
+    const std::vector<uint64_t> key = {1, (uint64_t)sizeof(V), (uint64_t)n, (uint64_t)steps, (uint64_t)(uintptr_t)x,
+                                       (uint64_t)(uintptr_t)v, (uint64_t)(uintptr_t)m, bits_of(eps), bits_of(dt),
+                                       (uint64_t)fp.shape, (uint64_t)plain, (uint64_t)comp,
+                                       (uint64_t)(fp.perm != nullptr)};
+    return run_graphed(c, key, graphable, [&](cudaStream_t s) {
+        return leapfrog_issue<V>(n, x, v, m, eps, dt, steps, fp, a, plain, comp, s);
+    });
 }
 
 extern "C" {
@@ -1209,8 +1223,19 @@ static int batched_common(int64_t nsys, const int64_t* offsets, float* pos, floa
     NB_CHECK(ensure(c.ws, B_ERR, sizeof(int), &pe));
     a.err = (int*)pe;
     const int shape = c.o.config >= 0 ? c.o.config : tuned_shape(2, max_ns, 0);
-    count(1);
-    NB_CUDA(nbk::batched_launch(shape, a, c.sms, st));
+    // The order array is uploaded on every call (above); the graph holds the
+    // queue reset and the persistent launch.
+    const std::vector<uint64_t> key = {2, (uint64_t)nsys, (uint64_t)(uintptr_t)a.offsets,
+                                       (uint64_t)(uintptr_t)a.order, (uint64_t)(uintptr_t)a.queue,
+                                       (uint64_t)(uintptr_t)a.pos, (uint64_t)(uintptr_t)a.vel,
+                                       (uint64_t)(uintptr_t)a.mass, (uint64_t)(uintptr_t)a.eps,
+                                       (uint64_t)(uintptr_t)a.acc, (uint64_t)(uintptr_t)a.pot, bits_of(dt),
+                                       (uint64_t)a.steps, (uint64_t)max_ns, (uint64_t)ntot, (uint64_t)shape};
+    NB_CHECK(run_graphed(c, key, true, [&](cudaStream_t s) {
+        count(1);
+        NB_CUDA(nbk::batched_launch(shape, a, c.sms, s));
+        return NBODY_OK;
+    }));
     // (a pageable-to-device copy has read `order` before cudaMemcpyAsync returns)
     return sg.finish();
 }

@@ -152,3 +152,35 @@ def test_ragged_workload_sampled_systems(nb, oracle_mod):
         eg = oracle_mod.energy(pg[a:b], vg[a:b], mass[a:b], eps[s])["E"]
         assert abs(eg - er) <= 1e-5 * abs(e0), (s, b - a)
         assert np.abs(pg[a:b] - pr).max() <= 1e-4, (s, b - a)
+
+
+def test_repeated_batched_calls_replay_a_cuda_graph(nb):
+    """A batched leapfrog call repeated with the same arguments is captured into
+    a CUDA graph from its second occurrence on; the results stay bit-identical
+    to calls that never repeat their arguments, also after more distinct
+    argument sets than the graph cache keeps."""
+    import torch
+    sizes = [70, 0, 300, 1025, 5]
+    off, pos, vel, mass, eps = make_batch(sizes, 61)
+    O, M, E = t(off, np.int64), t(mass, np.float32), t(eps, np.float32)
+    X1, V1 = t(pos, np.float32), t(vel, np.float32)
+    for _ in range(4):
+        nb.nbody_leapfrog_batched(O, X1, V1, M, E, 2.0 ** -8, 3)
+    keep = []
+    X2, V2 = t(pos, np.float32), t(vel, np.float32)
+    for _ in range(4):
+        X2, V2 = X2.clone(), V2.clone()
+        keep.append((X2, V2))  # hold every array so no address is reused
+        nb.nbody_leapfrog_batched(O, X2, V2, M, E, 2.0 ** -8, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(X1, X2) and torch.equal(V1, V2)
+    for _ in range(20):  # more distinct argument sets than the cache holds
+        Y, W = t(pos, np.float32), t(vel, np.float32)
+        keep.append((Y, W))
+        nb.nbody_leapfrog_batched(O, Y, W, M, E, 2.0 ** -8, 3)
+    for _ in range(2):
+        nb.nbody_leapfrog_batched(O, X1, V1, M, E, 2.0 ** -8, 3)
+        nb.nbody_leapfrog_batched(O, X2, V2, M, E, 2.0 ** -8, 3)
+    torch.cuda.synchronize()
+    assert nb.nbody_last_device_error() == 0
+    assert torch.equal(X1, X2) and torch.equal(V1, V2)
