@@ -248,11 +248,14 @@ __global__ void __launch_bounds__(T) batched_kernel(const BParams p) {
             const float kick = (p.steps == 0) ? 0.0f : ((ev == 0 || ev == p.steps) ? 0.5f * p.dt : p.dt);
             const bool drift = ev < p.steps;
             for (int base = 0; base < ns; base += T * I) {
-                // The last pass of a system takes only as many i-bodies per
-                // thread as it has left (rounded up to whole warps' worth), so
-                // padding costs at most T - 1 bodies per system, not T*I - 1.
-                const int left = (ns - base + T - 1) / T;
-                if (eps2s == 0.0f) {
+                // Each warp takes only as many i-bodies per thread as it has
+                // left in this pass (slot k of lane l is body base + k*T + l),
+                // and a warp with none skips the pass: padding costs less than
+                // one warp's row of bodies per system, not up to T*I - 1.
+                const int lw = ns - base - 32 * (int)(threadIdx.x >> 5);
+                const int left = lw <= 0 ? 0 : (lw + T - 1) / T;
+                if (left == 0) {
+                } else if (eps2s == 0.0f) {
                     if (uni)
                         pass_dispatch<T, I, POT, true, true>(left, sj, npair, ns, base, eps2, p, off, ev, kick,
                                                              drift, eps2s, mu);
