@@ -113,6 +113,15 @@ NBODY_API int nbody_accel_f32(int64_t n, const float* pos, const float* mass, fl
  * The force at the end of a step serves the first kick of the next, so a call
  * makes steps + 1 force evaluations.  pos, vel [n][3] double (FP64 drift and
  * kicks), mass [n] float.  steps == 0 leaves the state unchanged.
+ *
+ * A call repeated with the same arguments (device arrays, same stream and
+ * options: a simulation loop) is captured into a CUDA graph on its second
+ * occurrence and replayed as one unit from then on, with results
+ * bit-identical to direct launches; nbody_leapfrog_batched does the same.
+ * Graphs are not used while profiling is on (nbody_profile_enable), when the
+ * environment sets NBODY_NO_GRAPH, or when a CUDA tool is injected into the
+ * process (CUDA_INJECTION64_PATH set, as under ncu), so tools see every
+ * kernel launched directly.
  */
 NBODY_API int nbody_leapfrog(int64_t n, double* pos, double* vel, const float* mass, double eps, double dt,
                    int64_t steps, const nbody_opts* opts);

@@ -691,7 +691,11 @@ static int leapfrog_issue(int64_t n, V* x, V* v, const float* m, double eps, dou
 template <typename F>
 static int run_graphed(Ctx& c, std::vector<uint64_t> key, bool graphable, F issue) {
     cudaStream_t st = c.o.stream;
-    if (!graphable || g_prof_on.load() || getenv("NBODY_NO_GRAPH") != nullptr) return issue(st);
+    // Direct launches while profiling, on request, or under an injected CUDA
+    // tool (a profiler measures kernels one launch at a time).
+    if (!graphable || g_prof_on.load() || getenv("NBODY_NO_GRAPH") != nullptr ||
+        getenv("CUDA_INJECTION64_PATH") != nullptr)
+        return issue(st);
     key.push_back(c.ws->gen);
     auto found = c.ws->graphs.find(key);
     if (found == c.ws->graphs.end()) {
