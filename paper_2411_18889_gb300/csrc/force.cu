@@ -74,7 +74,7 @@ __device__ __forceinline__ void kahan_add(f2& sum, f2& comp, f2 term) {
 
 // Summation modes: 0 one FP32 running sum, 1 FP32 per tile folded by Kahan
 // summation, 2 Kahan summation of every pair term.
-template <int T, int IP, int J, int UNROLL, bool POT, bool DIAG, int MODE>
+template <int T, int IP, int J, int UNROLL, bool POT, bool DIAG, int MODE, int WF>
 __device__ __forceinline__ void tile_pass(const unsigned char* tile, const f2 (&xi)[IP], const f2 (&yi)[IP],
                                           const f2 (&zi)[IP], f2 eps2, f2 (&ax)[IP], f2 (&ay)[IP], f2 (&az)[IP],
                                           f2 (&ap)[IP], f2 (&kx)[IP], f2 (&ky)[IP], f2 (&kz)[IP], f2 (&kp)[IP],
@@ -103,8 +103,15 @@ __device__ __forceinline__ void tile_pass(const unsigned char* tile, const f2 (&
                 if (jl == (2 * q + 1) * T + tid) q1 = 0.0f;
             }
             const f2 ri = pk(q0, q1);
-            f2 w = mul2(ri, mul2(ri, ri));  // rsqrt cubed
-            w = mul2(w, mj);                // times m_j
+            // m_j rsqrt(s)^3 in one of two association orders (the same
+            // three products; which schedules better depends on the shape)
+            f2 w;
+            if (WF == 1) {
+                w = mul2(mul2(ri, ri), mul2(ri, mj));
+            } else {
+                w = mul2(ri, mul2(ri, ri));
+                w = mul2(w, mj);
+            }
             if (MODE == 2) {
                 kahan_add(ax[q], kx[q], mul2(dx, w));
                 kahan_add(ay[q], ky[q], mul2(dy, w));
@@ -128,7 +135,7 @@ __device__ __forceinline__ void kahan2(f2& sum, f2& comp, f2& part) {
     part = 0ull;
 }
 
-template <int T, int IP, int J, int UNROLL, int MINB, bool POT, bool MIXED, int KAHAN>
+template <int T, int IP, int J, int UNROLL, int MINB, bool POT, bool MIXED, int KAHAN, int WF>
 __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
     constexpr int C = 2 * IP * T;
     constexpr uint32_t TILE_BYTES = J * 32u;
@@ -227,10 +234,10 @@ __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
             }
             const unsigned char* tile = tiles + s * TILE_BYTES;
             if (p.self && cell == b) {
-                tile_pass<T, IP, J, UNROLL, POT, true, KAHAN>(tile, xi, yi, zi, eps2, ax, ay, az, ap, cx, cy, cz,
+                tile_pass<T, IP, J, UNROLL, POT, true, KAHAN, WF>(tile, xi, yi, zi, eps2, ax, ay, az, ap, cx, cy, cz,
                                                               cp, (int)(tt * J - base), tid);
             } else {
-                tile_pass<T, IP, J, UNROLL, POT, false, KAHAN>(tile, xi, yi, zi, eps2, ax, ay, az, ap, cx, cy, cz,
+                tile_pass<T, IP, J, UNROLL, POT, false, KAHAN, WF>(tile, xi, yi, zi, eps2, ax, ay, az, ap, cx, cy, cz,
                                                                cp, 0, tid);
             }
             if (KAHAN == 1) {
@@ -356,23 +363,25 @@ struct ShapeEntry {
     }
 };
 
-template <int T, int IP, int J, int UNROLL, int MINB>
+// WF0: association order of m_j rsqrt(s)^3 in the kernels without the
+// potential (those with it use order 0).
+template <int T, int IP, int J, int UNROLL, int MINB, int WF0 = 0>
 ShapeEntry make_entry() {
     ShapeEntry e;
     e.shape = ForceShape{T, IP, J, 2 * IP * T};
     e.cap = T >= 512 ? 1 : 512 / T;
-    e.fn[0][0][0] = force_kernel<T, IP, J, UNROLL, MINB, false, false, 0>;
-    e.fn[0][0][1] = force_kernel<T, IP, J, UNROLL, MINB, false, false, 1>;
-    e.fn[0][0][2] = force_kernel<T, IP, J, UNROLL, MINB, false, false, 2>;
-    e.fn[0][1][0] = force_kernel<T, IP, J, UNROLL, MINB, false, true, 0>;
-    e.fn[0][1][1] = force_kernel<T, IP, J, UNROLL, MINB, false, true, 1>;
-    e.fn[0][1][2] = force_kernel<T, IP, J, UNROLL, MINB, false, true, 2>;
-    e.fn[1][0][0] = force_kernel<T, IP, J, UNROLL, MINB, true, false, 0>;
-    e.fn[1][0][1] = force_kernel<T, IP, J, UNROLL, MINB, true, false, 1>;
-    e.fn[1][0][2] = force_kernel<T, IP, J, UNROLL, MINB, true, false, 2>;
-    e.fn[1][1][0] = force_kernel<T, IP, J, UNROLL, MINB, true, true, 0>;
-    e.fn[1][1][1] = force_kernel<T, IP, J, UNROLL, MINB, true, true, 1>;
-    e.fn[1][1][2] = force_kernel<T, IP, J, UNROLL, MINB, true, true, 2>;
+    e.fn[0][0][0] = force_kernel<T, IP, J, UNROLL, MINB, false, false, 0, WF0>;
+    e.fn[0][0][1] = force_kernel<T, IP, J, UNROLL, MINB, false, false, 1, WF0>;
+    e.fn[0][0][2] = force_kernel<T, IP, J, UNROLL, MINB, false, false, 2, WF0>;
+    e.fn[0][1][0] = force_kernel<T, IP, J, UNROLL, MINB, false, true, 0, WF0>;
+    e.fn[0][1][1] = force_kernel<T, IP, J, UNROLL, MINB, false, true, 1, WF0>;
+    e.fn[0][1][2] = force_kernel<T, IP, J, UNROLL, MINB, false, true, 2, WF0>;
+    e.fn[1][0][0] = force_kernel<T, IP, J, UNROLL, MINB, true, false, 0, 0>;
+    e.fn[1][0][1] = force_kernel<T, IP, J, UNROLL, MINB, true, false, 1, 0>;
+    e.fn[1][0][2] = force_kernel<T, IP, J, UNROLL, MINB, true, false, 2, 0>;
+    e.fn[1][1][0] = force_kernel<T, IP, J, UNROLL, MINB, true, true, 0, 0>;
+    e.fn[1][1][1] = force_kernel<T, IP, J, UNROLL, MINB, true, true, 1, 0>;
+    e.fn[1][1][2] = force_kernel<T, IP, J, UNROLL, MINB, true, true, 2, 0>;
     return e;
 }
 
@@ -380,7 +389,7 @@ const ShapeEntry* shapes() {
     static const ShapeEntry table[] = {
         make_entry<256, 4, 256, 4, 0>(),  // 0: 2048-body blocks (fastest with the potential)
         make_entry<256, 2, 256, 4, 0>(),  // 1: 1024
-        make_entry<512, 2, 256, 4, 0>(),  // 2: 2048 (fastest without the potential)
+        make_entry<512, 2, 256, 4, 0, 1>(),  // 2: 2048 (fastest without the potential)
         make_entry<128, 2, 128, 2, 0>(),  // 3: 512
         make_entry<128, 1, 64, 2, 0>(),   // 4: 256 (small n)
 #ifdef NBODY_EXTRA_SHAPES
