@@ -40,6 +40,13 @@
  *    distinct positions.
  *  - Interactions are counted as n*n per force evaluation (the paper's
  *    "interaction pairs", Sec. III.A).
+ *  - Each call opens an NVTX range named after it (visible to timeline
+ *    tools; a no-op otherwise).
+ *  - Environment: NBODY_TUNE_FILE names the kernel-shape table (default:
+ *    nbody_tune.txt beside the library); NBODY_NO_GRAPH turns off the graph
+ *    replay of repeated calls; NBODY_FAULT=alloc|launch|tune injects a
+ *    host-side failure for tests (NBODY_ENOMEM, NBODY_ECUDA, an unreadable
+ *    shape table) without queuing GPU work.
  */
 #ifndef NBODY_H
 #define NBODY_H

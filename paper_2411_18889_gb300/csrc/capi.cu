@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <dlfcn.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -41,11 +42,22 @@ int cuda_fail(cudaError_t e) {
 
 // Host-side fault injection for tests: NBODY_FAULT=alloc makes workspace
 // allocation report NBODY_ENOMEM, NBODY_FAULT=launch makes the launch report
-// NBODY_ECUDA.  Nothing is sent to the GPU in either case.
+// NBODY_ECUDA, NBODY_FAULT=tune makes reading a kernel-shape table fail (the
+// built-in table then serves).  Nothing is sent to the GPU in any case.
 bool fault(const char* what) {
     const char* f = getenv("NBODY_FAULT");
     return f != nullptr && strcmp(f, what) == 0;
 }
+
+// An NVTX range around each public call, so that a timeline tool shows the
+// library's calls by name around their kernels (a no-op without a tool).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define NB_RANGE(name) NvtxRange nb_range_(name)
 
 // ---------------------------------------------------------------------------
 // Launch accounting and optional force-kernel timing (for benchmarks).
@@ -321,6 +333,7 @@ int kind_shapes(int kind) {
 
 // Parse a table file into `out`; returns the number of rules or NBODY_EINVAL.
 int tune_parse(const char* path, std::vector<TuneRule>& out) {
+    if (fault("tune")) return NBODY_EINVAL;
     FILE* f = fopen(path, "r");
     if (f == nullptr) return NBODY_EINVAL;
     char line[256];
@@ -613,6 +626,7 @@ int nbody_last_cuda_error(void) { return t_last_cuda; }
 
 int nbody_accel(int64_t n, const double* pos, const float* mass, double eps, float* acc, float* pot,
                 const nbody_opts* opts) {
+    NB_RANGE("nbody_accel");
     if (n < 0 || !finite_nonneg(eps)) return NBODY_EINVAL;
     if (n > 0 && (pos == nullptr || mass == nullptr || acc == nullptr)) return NBODY_EINVAL;
     NB_CHECK(check_opts_only(opts));
@@ -632,6 +646,7 @@ int nbody_accel(int64_t n, const double* pos, const float* mass, double eps, flo
 
 int nbody_accel_f32(int64_t n, const float* pos, const float* mass, float eps, float* acc, float* pot,
                     const nbody_opts* opts) {
+    NB_RANGE("nbody_accel_f32");
     if (n < 0 || !finite_nonneg((double)eps)) return NBODY_EINVAL;
     if (n > 0 && (pos == nullptr || mass == nullptr || acc == nullptr)) return NBODY_EINVAL;
     NB_CHECK(check_opts_only(opts));
@@ -772,6 +787,7 @@ extern "C" {
 
 int nbody_leapfrog(int64_t n, double* pos, double* vel, const float* mass, double eps, double dt, int64_t steps,
                    const nbody_opts* opts) {
+    NB_RANGE("nbody_leapfrog");
     if (n < 0 || steps < 0 || !finite_nonneg(eps) || !isfinite(dt)) return NBODY_EINVAL;
     if (n > 0 && (pos == nullptr || vel == nullptr || mass == nullptr)) return NBODY_EINVAL;
     NB_CHECK(check_opts_only(opts));
@@ -790,6 +806,7 @@ int nbody_leapfrog(int64_t n, double* pos, double* vel, const float* mass, doubl
 
 int nbody_leapfrog_f32(int64_t n, float* pos, float* vel, const float* mass, float eps, float dt, int64_t steps,
                        const nbody_opts* opts) {
+    NB_RANGE("nbody_leapfrog_f32");
     if (n < 0 || steps < 0 || !finite_nonneg((double)eps) || !isfinite(dt)) return NBODY_EINVAL;
     if (n > 0 && (pos == nullptr || vel == nullptr || mass == nullptr)) return NBODY_EINVAL;
     NB_CHECK(check_opts_only(opts));
@@ -882,11 +899,13 @@ static int accel_ij_common(int64_t ni, const void* ipos, int64_t nj, const void*
 
 int nbody_accel_ij(int64_t ni, const double* ipos, int64_t nj, const double* jpos, const float* jmass, double eps,
                    float* acc, float* pot, const nbody_opts* opts) {
+    NB_RANGE("nbody_accel_ij");
     return accel_ij_common(ni, ipos, nj, jpos, jmass, eps, acc, pot, opts, true);
 }
 
 int nbody_accel_ij_f32(int64_t ni, const float* ipos, int64_t nj, const float* jpos, const float* jmass, float eps,
                        float* acc, float* pot, const nbody_opts* opts) {
+    NB_RANGE("nbody_accel_ij_f32");
     return accel_ij_common(ni, ipos, nj, jpos, jmass, (double)eps, acc, pot, opts, false);
 }
 
@@ -944,6 +963,7 @@ static int run_vjp(const VjpPlan& vp, int64_t n, float eps2, bool mixed, bool ha
 
 int nbody_accel_vjp(int64_t n, const double* pos, const float* mass, double eps, const float* g_acc,
                     const float* g_pot, float* g_pos, float* g_mass, const nbody_opts* opts) {
+    NB_RANGE("nbody_accel_vjp");
     if (n < 0 || !finite_nonneg(eps)) return NBODY_EINVAL;
     if (n > 0 && (pos == nullptr || mass == nullptr || g_acc == nullptr || g_pos == nullptr || g_mass == nullptr))
         return NBODY_EINVAL;
@@ -985,6 +1005,7 @@ static bool device_only(const void* p) { return p != nullptr && !is_host_ptr(p);
 
 int nbody_leapfrog_record(int64_t n, double* pos, double* vel, const float* mass, double eps, double dt,
                           int64_t steps, int64_t ckpt_every, void* tape, const nbody_opts* opts) {
+    NB_RANGE("nbody_leapfrog_record");
     if (n < 0 || steps < 0 || ckpt_every < 1 || !finite_nonneg(eps) || !isfinite(dt)) return NBODY_EINVAL;
     if (n > 0 && (pos == nullptr || vel == nullptr || mass == nullptr || tape == nullptr)) return NBODY_EINVAL;
     NB_CHECK(check_opts_only(opts));
@@ -1037,6 +1058,7 @@ int nbody_leapfrog_record(int64_t n, double* pos, double* vel, const float* mass
 int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, double dt, int64_t steps, int64_t ckpt_every,
                        const void* tape, const double* g_posT, const double* g_velT, double* g_pos0, double* g_vel0,
                        double* g_mass, const nbody_opts* opts) {
+    NB_RANGE("nbody_leapfrog_vjp");
     if (n < 0 || steps < 0 || ckpt_every < 1 || !finite_nonneg(eps) || !isfinite(dt)) return NBODY_EINVAL;
     if (n > 0 && (mass == nullptr || tape == nullptr || g_posT == nullptr || g_velT == nullptr ||
                   g_pos0 == nullptr || g_vel0 == nullptr || g_mass == nullptr))
@@ -1246,12 +1268,14 @@ static int batched_common(int64_t nsys, const int64_t* offsets, float* pos, floa
 
 int nbody_accel_batched(int64_t nsys, const int64_t* offsets, const float* pos, const float* mass, const float* eps,
                         float* acc, float* pot, const nbody_opts* opts) {
+    NB_RANGE("nbody_accel_batched");
     return batched_common(nsys, offsets, const_cast<float*>(pos), nullptr, mass, eps, acc, pot, 0.0f, 0, opts,
                           false);
 }
 
 int nbody_leapfrog_batched(int64_t nsys, const int64_t* offsets, float* pos, float* vel, const float* mass,
                            const float* eps, float dt, int64_t steps, const nbody_opts* opts) {
+    NB_RANGE("nbody_leapfrog_batched");
     return batched_common(nsys, offsets, pos, vel, mass, eps, nullptr, nullptr, dt, steps, opts, true);
 }
 
@@ -1296,11 +1320,13 @@ static int energy_common(int64_t n, const void* pos, const void* vel, const floa
 
 int nbody_energy(int64_t n, const double* pos, const double* vel, const float* mass, double eps, double* out,
                  const nbody_opts* opts) {
+    NB_RANGE("nbody_energy");
     return energy_common(n, pos, vel, mass, eps, out, opts, true);
 }
 
 int nbody_energy_f32(int64_t n, const float* pos, const float* vel, const float* mass, float eps, double* out,
                      const nbody_opts* opts) {
+    NB_RANGE("nbody_energy_f32");
     return energy_common(n, pos, vel, mass, (double)eps, out, opts, false);
 }
 
@@ -1324,6 +1350,7 @@ int nbody_last_device_error(void) {
 }
 
 int nbody_selftest_wait(double limit_seconds, const nbody_opts* opts) {
+    NB_RANGE("nbody_selftest_wait");
     if (!(limit_seconds >= 1e-6 && limit_seconds <= 1.0)) return NBODY_EINVAL;
     NB_CHECK(check_opts_only(opts));
     Ctx c;

@@ -114,3 +114,19 @@ def test_tune_table_parse_and_query(lib, tmp_path):
     for n in (1, 1000, 1 << 20):
         for pot in (0, 1):
             assert 0 <= lib.nbody_tuned_shape(0, n, pot) < lib.nbody_num_configs()
+
+
+def test_tune_table_fault_injection(lib, tmp_path, monkeypatch):
+    """NBODY_FAULT=tune: reading a shape table fails as if the file were bad;
+    the built-in table keeps serving and nothing touches a GPU."""
+    good = tmp_path / "t.txt"
+    good.write_text("force 0 0 3\nvjp 0 1\nbatched 3\n")
+    monkeypatch.setenv("NBODY_FAULT", "tune")
+    assert lib.nbody_tune_load(str(good).encode()) == -1
+    assert lib.nbody_tune_load(None) == 0  # default location unreadable: built-in table
+    for n in (1, 1000, 1 << 20):
+        assert 0 <= lib.nbody_tuned_shape(0, n, 0) < lib.nbody_num_configs()
+    monkeypatch.delenv("NBODY_FAULT")
+    assert lib.nbody_tune_load(str(good).encode()) == 3
+    assert lib.nbody_tuned_shape(0, 10, 0) == 3
+    assert lib.nbody_tune_load(None) >= 0
