@@ -108,6 +108,8 @@ __device__ __forceinline__ void tile_pass(const unsigned char* tile, const f2 (&
             f2 w;
             if (WF == 1) {
                 w = mul2(mul2(ri, ri), mul2(ri, mj));
+            } else if (WF == 2) {
+                w = mul2(mul2(mul2(ri, mj), ri), ri);
             } else {
                 w = mul2(ri, mul2(ri, ri));
                 w = mul2(w, mj);
@@ -389,7 +391,7 @@ const ShapeEntry* shapes() {
     static const ShapeEntry table[] = {
         make_entry<256, 4, 256, 4, 0>(),  // 0: 2048-body blocks (fastest with the potential)
         make_entry<256, 2, 256, 4, 0>(),  // 1: 1024
-        make_entry<512, 2, 256, 4, 0, 1>(),  // 2: 2048 (fastest without the potential)
+        make_entry<512, 2, 512, 4, 0, 1>(),  // 2: 2048 (fastest without the potential)
         make_entry<128, 2, 128, 2, 0>(),  // 3: 512
         make_entry<128, 1, 64, 2, 0>(),   // 4: 256 (small n)
 #ifdef NBODY_EXTRA_SHAPES
@@ -412,12 +414,25 @@ const ShapeEntry* shapes() {
         make_entry<128, 2, 128, 4, 0>(),  // 21
         make_entry<128, 1, 64, 4, 0>(),   // 22
         make_entry<64, 2, 128, 4, 0>(),   // 23
+        make_entry<512, 2, 256, 2, 0, 1>(),   // 24
+        make_entry<512, 2, 256, 8, 0, 1>(),   // 25
+        make_entry<512, 2, 128, 4, 0, 1>(),   // 26
+        make_entry<512, 2, 256, 4, 0, 1>(),   // 27
+        make_entry<1024, 1, 256, 4, 0, 1>(),  // 28
+        make_entry<512, 1, 256, 4, 0, 1>(),   // 29
+        make_entry<512, 3, 256, 4, 0, 1>(),   // 30
+        make_entry<256, 2, 256, 4, 0, 2>(),   // 31
+        make_entry<512, 2, 256, 4, 0, 2>(),   // 32
+        make_entry<384, 2, 256, 4, 0, 1>(),   // 33
+        make_entry<128, 2, 256, 4, 0, 1>(),   // 34
+        make_entry<256, 2, 512, 4, 0, 1>(),   // 35
+        make_entry<512, 4, 256, 4, 0, 1>(),   // 36
 #endif
     };
     return table;
 }
 #ifdef NBODY_EXTRA_SHAPES
-constexpr int kNumShapes = 24;
+constexpr int kNumShapes = 37;
 #else
 constexpr int kNumShapes = 5;
 #endif
