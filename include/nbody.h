@@ -240,7 +240,9 @@ NBODY_API int nbody_config_block(int k);
  * library, else the built-in GB300 table) and returns the number of rules or
  * NBODY_EINVAL (malformed line or shape index out of range; the table is then
  * unchanged).  Lines: "force <pot 0|1> <n_min> <shape>", "vjp <n_min>
- * <shape>", "batched <shape>", '#' comments.  nbody_tuned_shape(kind, n, pot)
+ * <shape>", "batched [<n_min>] <shape>" (for a batched rule n_min is compared
+ * with the largest system of the batch; omitted, it is 0), '#' comments; the
+ * rule of a kind with the largest n_min <= n applies.  nbody_tuned_shape(kind, n, pot)
  * returns the shape used for kind 0 (force), 1 (VJP) or 2 (batched; n = the
  * largest system) when opts->config is -1.
  */

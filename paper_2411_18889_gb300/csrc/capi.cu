@@ -302,7 +302,8 @@ struct Staging {
 // ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
 // Kernel-shape table: rules "force <pot> <n_min> <shape>", "vjp <n_min>
-// <shape>", "batched <shape>" read from the tuner's file (NBODY_TUNE_FILE, or
+// <shape>", "batched [<n_min>] <shape>" (n_min of a batched rule is compared
+// with the batch's largest system) read from the tuner's file (NBODY_TUNE_FILE, or
 // nbody_tune.txt beside the library); the rule with the largest n_min <= n
 // wins.  Built-in defaults (measured on GB300) apply when no file is found.
 // ---------------------------------------------------------------------------
@@ -324,7 +325,9 @@ void tune_defaults(std::vector<TuneRule>& r) {
     }
     r.push_back({1, 0, 0, 3});
     r.push_back({1, 0, 40960, 0});
-    r.push_back({2, 0, 0, 2});
+    r.push_back({2, 0, 0, 3});
+    r.push_back({2, 0, 320, 2});
+    r.push_back({2, 0, 763, 0});
 }
 
 int kind_shapes(int kind) {
@@ -354,6 +357,8 @@ int tune_parse(const char* path, std::vector<TuneRule>& out) {
             r = {0, (int)a, (int64_t)b, (int)d};
         } else if (strcmp(kind, "vjp") == 0 && sscanf(s, "%*s %lld %lld", &b, &d) == 2) {
             r = {1, 0, (int64_t)b, (int)d};
+        } else if (strcmp(kind, "batched") == 0 && sscanf(s, "%*s %lld %lld", &b, &d) == 2) {
+            r = {2, 0, (int64_t)b, (int)d};  // n_min = largest system of the batch
         } else if (strcmp(kind, "batched") == 0 && sscanf(s, "%*s %lld", &d) == 1) {
             r = {2, 0, 0, (int)d};
         } else {

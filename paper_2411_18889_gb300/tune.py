@@ -60,7 +60,8 @@ def survey(sizes=(1024, 4096, 16384, 65536, 262144, 1048576), vjp_sizes=(1024, 4
     lib = load()
     lines = [f"# kernel-shape table written by paper_2411_18889_gb300.tune on "
              f"{torch.cuda.get_device_name(0)}, {datetime.date.today().isoformat()}",
-             "# kind pot n_min shape   (force), kind n_min shape (vjp), kind shape (batched)"]
+             "# kind pot n_min shape (force), kind n_min shape (vjp), kind n_min shape (batched; n_min compared "
+             "with the largest system)"]
     nf = lib.nbody_num_configs()
     for pot in (0, 1):
         winners = []
@@ -94,16 +95,31 @@ def survey(sizes=(1024, 4096, 16384, 65536, 262144, 1048576), vjp_sizes=(1024, 4
         log(f"vjp n={n}: " + " ".join(f"{i}:{n * n / x / 1e9:.0f}" for i, x in enumerate(t)) + f" Gint/s -> {k}")
     for n_min, k in _rules(vjp_sizes, winners):
         lines.append(f"vjp {n_min} {k}")
-    off, pos, vel, mass, eps = ni.ragged_batch(nsys=512, seed=4)
-    O = torch.from_numpy(off).cuda()
-    P = torch.from_numpy(pos.astype(np.float32)).cuda()
-    M = torch.from_numpy(mass.astype(np.float32)).cuda()
-    E = torch.from_numpy(eps.astype(np.float32)).cuda()
-    acc = torch.empty((pos.shape[0], 3), dtype=torch.float32, device="cuda")
-    t = [_time(lambda k=k: api.nbody_accel_batched(O, P, M, E, acc, config=k), 3) for k in range(4)]
-    k = int(np.argmin(t))
-    log(f"batched: " + " ".join(f"{i}:{x * 1e3:.2f}ms" for i, x in enumerate(t)) + f" -> {k}")
-    lines.append(f"batched {k}")
+    # Batched: ragged families keyed by their largest system, each advanced a
+    # few leapfrog steps in one persistent launch (the way ensembles run).
+    nb_shapes = 4
+    fam_max, bwin = [], []
+    for nmax, nsys in ((128, 4096), (512, 2048), (1024, 1024), (4096, 512)):
+        off, pos, vel, mass, eps = ni.ragged_batch(nsys=nsys, seed=4, nmin=max(16, nmax // 64), nmax=nmax)
+        O = torch.from_numpy(off).cuda()
+        P0 = torch.from_numpy(pos.astype(np.float32)).cuda()
+        V0 = torch.from_numpy(vel.astype(np.float32)).cuda()
+        M = torch.from_numpy(mass.astype(np.float32)).cuda()
+        E = torch.from_numpy(eps.astype(np.float32)).cuda()
+        P, V = P0.clone(), V0.clone()
+
+        def run(k):
+            P.copy_(P0)
+            V.copy_(V0)
+            api.nbody_leapfrog_batched(O, P, V, M, E, 2.0 ** -8, 8, config=k)
+
+        t = [_time(lambda k=k: run(k), 3) for k in range(nb_shapes)]
+        k = int(np.argmin(t))
+        log(f"batched max {nmax}: " + " ".join(f"{i}:{x * 1e3:.2f}ms" for i, x in enumerate(t)) + f" -> {k}")
+        fam_max.append(int(np.diff(off).max()))
+        bwin.append(k)
+    for n_min, k in _rules(fam_max, bwin):
+        lines.append(f"batched {n_min} {k}")
     with open(out, "w") as f:
         f.write("\n".join(lines) + "\n")
     rc = lib.nbody_tune_load(out.encode())

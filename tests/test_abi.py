@@ -95,15 +95,18 @@ def test_tune_table_parse_and_query(lib, tmp_path):
     rejection of malformed lines and out-of-range shapes (table unchanged)."""
     EINVAL = -1
     good = tmp_path / "t.txt"
-    good.write_text("# comment\nforce 0 0 3\nforce 0 5000 2\nforce 1 0 0\nvjp 0 1\nvjp 100000 2\nbatched 3\n")
-    assert lib.nbody_tune_load(str(good).encode()) == 6
+    good.write_text("# comment\nforce 0 0 3\nforce 0 5000 2\nforce 1 0 0\nvjp 0 1\nvjp 100000 2\nbatched 3\n"
+                    "batched 1024 0\n")
+    assert lib.nbody_tune_load(str(good).encode()) == 7
     assert lib.nbody_tuned_shape(0, 10, 0) == 3
     assert lib.nbody_tuned_shape(0, 5000, 0) == 2
     assert lib.nbody_tuned_shape(0, 10 ** 7, 1) == 0
     assert lib.nbody_tuned_shape(1, 99999, 0) == 1
     assert lib.nbody_tuned_shape(1, 100000, 0) == 2
-    assert lib.nbody_tuned_shape(2, 4096, 0) == 3
-    for bad in ("force 0 0 99\n", "force 2 0 1\n", "vjp -5 1\n", "nonsense 1 2\n", "force 0\n"):
+    assert lib.nbody_tuned_shape(2, 1023, 0) == 3  # batched rules key on the largest system
+    assert lib.nbody_tuned_shape(2, 4096, 0) == 0
+    for bad in ("force 0 0 99\n", "force 2 0 1\n", "vjp -5 1\n", "nonsense 1 2\n", "force 0\n", "batched 0 9\n",
+                "batched -1 0\n"):
         f = tmp_path / "bad.txt"
         f.write_text(bad)
         assert lib.nbody_tune_load(str(f).encode()) == EINVAL
