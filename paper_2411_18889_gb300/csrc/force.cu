@@ -323,14 +323,16 @@ __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
 }
 
 // Adds the per-CTA partial sums of every i-block that a slice boundary cut,
-// in CTA order.  One CTA per i-block; blocks covered by one CTA return at once.
+// in CTA order.  Grid (i-block, chunk of blockDim.x bodies of the block), so
+// a few large blocks still spread over many SMs; blocks covered by one CTA
+// return at once.
 __global__ void fixup_kernel(const KParams p, int C, int pot_on) {
     const int64_t b = blockIdx.x;
     const int64_t u0 = b * p.ntile, u1 = u0 + p.ntile - 1;
     const int64_t c_lo = ((u0 + 1) * p.nctas - 1) / p.units;
     const int64_t c_hi = ((u1 + 1) * p.nctas - 1) / p.units;
     if (c_lo == c_hi) return;
-    for (int lb = threadIdx.x; lb < C; lb += blockDim.x) {
+    for (int lb = blockIdx.y * blockDim.x + threadIdx.x; lb < C; lb += gridDim.y * blockDim.x) {
         const int64_t g = b * C + lb;
         if (g >= p.n) break;
         double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0;
@@ -497,7 +499,8 @@ cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t ntile, int64_t nctas, i
     p.pot = out1;
     p.partial = const_cast<double*>(partial);
     p.err = err;
-    fixup_kernel<<<(unsigned)nblk, 256, 0, st>>>(p, block, out1 != nullptr ? 1 : 0);
+    fixup_kernel<<<dim3((unsigned)nblk, (unsigned)((block + 255) / 256)), 256, 0, st>>>(p, block,
+                                                                                         out1 != nullptr ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -542,7 +545,7 @@ cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st
     *launched = 1;
     if (ev1 != nullptr) cudaEventRecord(ev1, st);
     if (p.nctas > 1) {  // a single CTA covers every i-block whole
-        fixup_kernel<<<(unsigned)p.nblk, 256, 0, st>>>(p, C, pot);
+        fixup_kernel<<<dim3((unsigned)p.nblk, (unsigned)((C + 255) / 256)), 256, 0, st>>>(p, C, pot);
         err = cudaGetLastError();
         if (err == cudaSuccess) *launched = 2;
     }

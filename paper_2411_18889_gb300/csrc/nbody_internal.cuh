@@ -220,6 +220,7 @@ cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st
 // applying a kick (vel += kick * acc) and a drift (pos += drift * vel) first.
 // All FP64 state arithmetic for the mixed path happens here.
 // perm (optional): slot k of the packed array holds body perm[k].
+int pack_threads(int block);
 cudaError_t pack_f64(int64_t n, int64_t npad, int block, double* pos, double* vel, const float* acc,
                      const float* mass, double kick, double drift, bool plain, float* jdup,
                      double* centres, cudaStream_t st, const int* perm = nullptr, int* err = nullptr);

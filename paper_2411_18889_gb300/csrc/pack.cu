@@ -28,13 +28,13 @@ __device__ __forceinline__ double warp_sum(double v) {
 // One CTA per cell.  Kick (vel += kick*acc), drift (pos += drift*vel), cell
 // centre, packed offsets.  kick/drift == 0 or vel/acc == nullptr skip them;
 // mass == nullptr packs zero masses (sinks that exert nothing).
-__global__ void __launch_bounds__(256) pack_f64_kernel(int64_t n, int block, double* __restrict__ pos,
+__global__ void __launch_bounds__(1024) pack_f64_kernel(int64_t n, int block, double* __restrict__ pos,
                                                        double* __restrict__ vel, const float* __restrict__ acc,
                                                        const float* __restrict__ mass, double kick, double drift,
                                                        int plain, float* __restrict__ jdup,
                                                        double* __restrict__ centres, const int* __restrict__ perm,
                                                        int* __restrict__ err) {
-    __shared__ double red[3][8];
+    __shared__ double red[3][32];
     __shared__ double cen[3];
     const int64_t base = (int64_t)blockIdx.x * block;
     const int tid = threadIdx.x;
@@ -145,6 +145,14 @@ __global__ void kick_kernel(int64_t n3, V* __restrict__ vel, const float* __rest
         vel[k] += kick * (V)acc[k];
 }
 
+}  // namespace
+
+// Threads of a one-CTA-per-cell pack kernel: a thread per body up to 1024, so
+// a few large cells still keep many loads in flight.
+int pack_threads(int block) { return block >= 1024 ? 1024 : (block < 32 ? 32 : block); }
+
+namespace {
+
 unsigned grid_for(int64_t work, int threads) {
     int64_t g = (work + threads - 1) / threads;
     if (g > 152 * 32) g = 152 * 32;
@@ -158,8 +166,8 @@ cudaError_t pack_f64(int64_t n, int64_t npad, int block, double* pos, double* ve
                      const float* mass, double kick, double drift, bool plain, float* jdup, double* centres,
                      cudaStream_t st, const int* perm, int* err) {
     const unsigned nblk = (unsigned)(npad / block);
-    pack_f64_kernel<<<nblk, 256, 0, st>>>(n, block, pos, vel, acc, mass, kick, drift, plain ? 1 : 0, jdup,
-                                          centres, perm, err);
+    pack_f64_kernel<<<nblk, pack_threads(block), 0, st>>>(n, block, pos, vel, acc, mass, kick, drift,
+                                                            plain ? 1 : 0, jdup, centres, perm, err);
     return cudaGetLastError();
 }
 

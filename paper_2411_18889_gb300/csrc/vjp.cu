@@ -287,13 +287,13 @@ __device__ __forceinline__ void store_jv(float* jv, int64_t k, float x, float y,
 // then the VJP's j-array with cotangent kappa * lam, relative to the FP64
 // cell centre (mixed) or absolute (plain).
 template <typename L>
-__global__ void __launch_bounds__(256) pack_vjp_kernel(int64_t n, int block, const double* __restrict__ pos,
+__global__ void __launch_bounds__(1024) pack_vjp_kernel(int64_t n, int block, const double* __restrict__ pos,
                                                        const float* __restrict__ mass, L* __restrict__ lam,
                                                        double* __restrict__ lamx, const float* __restrict__ gprev,
                                                        const float* __restrict__ gmprev, double* __restrict__ gm_acc,
                                                        double drift, double kappa, const float* __restrict__ mu,
                                                        int plain, float* __restrict__ jv, double* __restrict__ centres) {
-    __shared__ double red[3][8];
+    __shared__ double red[3][32];
     __shared__ double cen[3];
     const int64_t base = (int64_t)blockIdx.x * block;
     const int tid = threadIdx.x;
@@ -434,11 +434,13 @@ cudaError_t pack_vjp(int64_t n, int64_t npad, int block, const double* pos, cons
                      cudaStream_t st) {
     const unsigned nblk = (unsigned)(npad / block);
     if (lam_f64 != nullptr)
-        pack_vjp_kernel<double><<<nblk, 256, 0, st>>>(n, block, pos, mass, lam_f64, lamx, gprev, gmprev, gm_acc, drift,
-                                                       kappa, mu, plain ? 1 : 0, jv, centres);
+        pack_vjp_kernel<double><<<nblk, pack_threads(block), 0, st>>>(n, block, pos, mass, lam_f64, lamx, gprev,
+                                                                      gmprev, gm_acc, drift, kappa, mu,
+                                                                      plain ? 1 : 0, jv, centres);
     else
-        pack_vjp_kernel<const float><<<nblk, 256, 0, st>>>(n, block, pos, mass, lam_f32, nullptr, nullptr, nullptr,
-                                                            nullptr, 0.0, kappa, mu, plain ? 1 : 0, jv, centres);
+        pack_vjp_kernel<const float><<<nblk, pack_threads(block), 0, st>>>(n, block, pos, mass, lam_f32, nullptr,
+                                                                           nullptr, nullptr, nullptr, 0.0, kappa, mu,
+                                                                           plain ? 1 : 0, jv, centres);
     return cudaGetLastError();
 }
 

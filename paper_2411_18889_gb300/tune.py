@@ -49,7 +49,8 @@ def _rules(sizes, winners):
     return out
 
 
-def survey(sizes=(1024, 4096, 16384, 65536, 262144, 1048576), vjp_sizes=(1024, 4096, 16384, 65536, 262144),
+def survey(sizes=(1024, 4096, 16384, 32768, 65536, 262144, 1048576),
+           vjp_sizes=(1024, 4096, 16384, 32768, 65536, 262144),
            out=DEFAULT_OUT, log=print):
     import torch
 
