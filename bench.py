@@ -18,6 +18,8 @@ Legs (one JSON line on rank 0):
   roofline    the force kernel alone: its summed CUDA-event time over the timed
               region / launches, against the FP32 ALU peak.
   cpu_baseline the FP64 oracle on the host cores, on a bounded subsample.
+  accuracy    that subsample's FP64 sums against the library's force on the
+              initial state (mixed and plain): median and max relative error.
 ``--impl reference`` times the oracle alone (the reference arm of this
 comparison) and prints its own line.  Under torchrun each rank runs an
 independent replica (the force does not shard without a position exchange
@@ -146,9 +148,10 @@ def oracle_rate(w, target_s: float, max_sample: int = 1 << 14):
     while True:
         idx = ni.subsample(w.n, k, 77)
         t0 = time.perf_counter()
-        oracle.accel_subset(w.pos, w.mass, w.eps, idx, with_pot=False)
+        ref, _ = oracle.accel_subset(w.pos, w.mass, w.eps, idx, with_pot=False)
         dt = time.perf_counter() - t0
         if dt >= target_s or k >= max_sample:
+            oracle_rate.last = (idx, ref)  # the timed sum, kept for the accuracy check
             return k * w.n / dt / 1e9, k, dt, oracle.num_threads()
         k = min(max_sample, max(2 * k, int(k * target_s / max(dt, 1e-3))))
 
@@ -446,10 +449,21 @@ def main():
     adjoint = adjoint_leg(nb, dev, args)
 
     cpu = None
+    accuracy = None
     if rank == 0 and not args.no_cpu:
         rate, k, dt, cores = oracle_rate(w, 12.0)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{k} sink bodies x all {n} sources, one FP64 force sum ({dt:.1f} s)"}
+        # The same FP64 sums against the library's force on the workload's
+        # initial state, mixed and plain: per-body relative error of a_i.
+        idx, ref = oracle_rate.last
+        acc = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        accuracy = {"sample": f"{k} seeded bodies of the initial state", "target": "median <= 2e-6, max <= 1e-4"}
+        for name, prec in (("mixed", nb.NBODY_PREC_MIXED), ("plain", nb.NBODY_PREC_PLAIN)):
+            nb.nbody_accel(P0, M, w.eps, acc, None, precision=prec)
+            got = acc.cpu().numpy().astype(np.float64)[idx]
+            e = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+            accuracy[name] = {"median_rel_err": float(np.median(e)), "max_rel_err": float(e.max())}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -459,7 +473,8 @@ def main():
         "plain": {"value": plain_value, "unit": UNIT, "pct_fp32_peak": plain_value * 1e9 / peak_int_s * 100,
                   "precision": "FP32 absolute coordinates (fails the accuracy target at this offset by design)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "batched": batched, "adjoint": adjoint,
+        "roofline": roofline, "cpu_baseline": cpu, "accuracy": accuracy, "clocks": clocks, "batched": batched,
+        "adjoint": adjoint,
         "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
         "wall_s_timed_region": wall_s, "step_ms": [s * 1e3 for s in per_step],
     }

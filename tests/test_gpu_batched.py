@@ -104,6 +104,32 @@ def test_leapfrog_batched_matches_oracle(nb, oracle_mod):
             assert abs(eg - er) <= 1e-5 * abs(e0), s
 
 
+@pytest.mark.parametrize("shape", range(4))
+def test_largest_system_every_shape(nb, oracle_mod, shape):
+    """A system of NBODY_BATCH_MAX_N (12288) bodies, the largest a batch may
+    hold (192 KiB of shared memory), beside small ones, with every kernel shape;
+    one more body is rejected."""
+    import torch
+    nmax = 12288
+    off, pos, vel, mass, eps = make_batch([5, nmax, 70], 61 + shape)
+    acc, pot = gpu_accel_batched(nb, off, pos, mass, eps, config=shape)
+    assert nb.nbody_last_device_error() == 0
+    for s, pick in ((0, None), (1, ni.subsample(nmax, 512, 62)), (2, None)):
+        a, b = off[s], off[s + 1]
+        idx = np.arange(b - a) if pick is None else pick
+        ra, rp = oracle_mod.accel_subset(pos[a:b], mass[a:b], eps[s], idx)
+        e = rel(acc[a:b][idx], ra)
+        assert np.median(e) <= ACC_MED and e.max() <= ACC_MAX, (shape, s, np.median(e), e.max())
+        assert rel(pot[a:b][idx], rp).max() <= POT_MAX, (shape, s)
+    o = np.asarray([0, 10, 10 + nmax + 1], dtype=np.int64)
+    n = int(o[-1])
+    z = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    with pytest.raises(nb.NbodyError) as ei:
+        nb.nbody_accel_batched(o, z, torch.ones(n, dtype=torch.float32, device="cuda"),
+                               torch.full((2,), 0.1, dtype=torch.float32, device="cuda"), torch.empty_like(z))
+    assert ei.value.code == nb.NBODY_EINVAL
+
+
 def test_batched_deterministic_and_host_arrays(nb):
     off, pos, vel, mass, eps = make_batch([100, 2000, 3, 700], 41)
     a1, p1 = gpu_accel_batched(nb, off, pos, mass, eps)
