@@ -20,6 +20,9 @@ Legs (one JSON line on rank 0):
   cpu_baseline the FP64 oracle on the host cores, on a bounded subsample.
   accuracy    that subsample's FP64 sums against the library's force on the
               initial state (mixed and plain): median and max relative error.
+  batched, throughput_plain, adjoint
+              the ragged ensemble (4096 systems, 64 steps), the N = 65536 FP32
+              run of 128 steps, and the adjoint of 64 steps at N = 16384.
 ``--impl reference`` times the oracle alone (the reference arm of this
 comparison) and prints its own line.  Under torchrun each rank runs an
 independent replica (the force does not shard without a position exchange
@@ -279,6 +282,40 @@ def batched_leg(nb, dev, sms, peak_int_s, args):
             "per_system_launches": int(len(sizes) * (3 * (steps + 1) + 1))}
 
 
+def throughput_leg(nb, dev, peak_int_s, args):
+    """Plain FP32 throughput workload: N = 65536 equal-mass Plummer sphere,
+    eps = dt = 2^-8, 128 KDK steps in one nbody_leapfrog_f32 call (129 force
+    evaluations); the relative energy drift over the run comes from the
+    library's FP64 energy diagnostic."""
+    import torch
+    import nbody_inputs as ni
+    w = ni.throughput_plain()
+    n, steps = w.n, w.steps
+    P0 = torch.from_numpy(w.pos.astype(np.float32)).to(dev)
+    V0 = torch.from_numpy(w.vel.astype(np.float32)).to(dev)
+    M = torch.from_numpy(w.mass.astype(np.float32)).to(dev)
+    e0 = nb.nbody_energy_f32(P0, V0, M, np.float32(w.eps))["E"]
+    P, V = P0.clone(), V0.clone()
+    nb.nbody_leapfrog_f32(P, V, M, np.float32(w.eps), np.float32(w.dt), steps)  # warm-up
+    ts = []
+    for _ in range(max(1, min(args.steps, 3))):
+        P.copy_(P0)
+        V.copy_(V0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        nb.nbody_leapfrog_f32(P, V, M, np.float32(w.eps), np.float32(w.dt), steps)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    e1 = nb.nbody_energy_f32(P, V, M, np.float32(w.eps))["E"]
+    t = statistics.median(ts)
+    value = (steps + 1) * n * n / t / 1e9
+    return {"workload": "plummer_n65536_equal_mass_fp32_eps2^-8_kdk128_dt2^-8", "value": value, "unit": UNIT,
+            "pct_fp32_peak": value * 1e9 / peak_int_s * 100, "ms_per_call": t * 1e3,
+            "energy_drift_128_steps": abs(e1 - e0) / abs(e0)}
+
+
 def adjoint_leg(nb, dev, args):
     """Adjoint workload: N = 16384 Plummer, eps = 2^-7, dt = 2^-8, K = 64 KDK
     steps, checkpoints every 8 steps.  Forward = nbody_leapfrog_record (the run
@@ -446,6 +483,7 @@ def main():
         roofline["frac_at_measured_clock"] = achieved_tflops / (peak_tflops * clocks["sm_mhz"] / SM_MAX_MHZ_DEFAULT)
 
     batched = batched_leg(nb, dev, sms, peak_int_s, args)
+    throughput = throughput_leg(nb, dev, peak_int_s, args)
     adjoint = adjoint_leg(nb, dev, args)
 
     cpu = None
@@ -474,7 +512,7 @@ def main():
                   "precision": "FP32 absolute coordinates (fails the accuracy target at this offset by design)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": roofline, "cpu_baseline": cpu, "accuracy": accuracy, "clocks": clocks, "batched": batched,
-        "adjoint": adjoint,
+        "throughput_plain": throughput, "adjoint": adjoint,
         "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
         "wall_s_timed_region": wall_s, "step_ms": [s * 1e3 for s in per_step],
     }

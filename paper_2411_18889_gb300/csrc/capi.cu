@@ -159,6 +159,7 @@ enum BufId {
     B_ICENTRES,
     B_PERM,
     B_ORDS,
+    B_UNI,
     B_STAGE0,
     NBUF = B_STAGE0 + 8
 };
@@ -483,7 +484,25 @@ struct ForcePlan {
     int num_sms;
     int* perm = nullptr;            // spatial order of the bodies (mixed precision), or none
     void* order_scratch = nullptr;
+    int* uni = nullptr;             // device word: all source masses equal (set by issue_uniform)
 };
+
+// The equal-mass check: when every source has the same mass the force
+// kernels of the plan take the pair loop without m_j.  plan_uniform sizes the
+// flag (outside any graph capture); issue_uniform queues the check, once per
+// call (the masses do not change between the evaluations of a call).
+int plan_uniform(Workspace* ws, ForcePlan* fp) {
+    void* p;
+    NB_CHECK(ensure(ws, B_UNI, sizeof(int), &p));
+    fp->uni = (int*)p;
+    return NBODY_OK;
+}
+
+int issue_uniform(const ForcePlan& fp, int64_t n, const float* mass, cudaStream_t st) {
+    count(1);
+    NB_CUDA(nbk::uniform_mass_flag(n, mass, fp.uni, st));
+    return NBODY_OK;
+}
 
 // Buffers of the spatial order (mixed precision sorts the bodies along a
 // Morton curve so that each cell is a compact region).
@@ -537,6 +556,7 @@ int run_force(const ForcePlan& fp, int64_t n, float eps2, bool mixed, int summat
     a.err = fp.err;
     a.summation = summation;
     a.perm = fp.perm;
+    a.uni = fp.uni;
     ProfPair pp;
     const bool timed = prof_pair(&pp);
     int launched = 0;
@@ -576,6 +596,8 @@ int accel_f64_dev(Ctx& c, int64_t n, const double* pos, const float* mass, doubl
         NB_CHECK(plan_order(c.ws, n, &fp));
         NB_CHECK(issue_order(fp, n, pos, c.o.stream));
     }
+    NB_CHECK(plan_uniform(c.ws, &fp));
+    NB_CHECK(issue_uniform(fp, n, mass, c.o.stream));
     count(1);
     NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, const_cast<double*>(pos), nullptr, nullptr, mass, 0.0, 0.0, plain,
                           fp.jdup, fp.centres, c.o.stream, fp.perm, fp.err));
@@ -586,6 +608,8 @@ int accel_f64_dev(Ctx& c, int64_t n, const double* pos, const float* mass, doubl
 int accel_f32_dev(Ctx& c, int64_t n, const float* pos, const float* mass, float eps, float* acc, float* pot) {
     ForcePlan fp;
     NB_CHECK(plan_force(c.ws, n, shape_for(c, n, pot != nullptr), c.sms, &fp));
+    NB_CHECK(plan_uniform(c.ws, &fp));
+    NB_CHECK(issue_uniform(fp, n, mass, c.o.stream));
     count(1);
     NB_CUDA(nbk::pack_f32(n, fp.npad, const_cast<float*>(pos), nullptr, nullptr, mass, 0.0f, 0.0f, fp.jdup,
                           c.o.stream));
@@ -681,6 +705,7 @@ static int leapfrog_issue(int64_t n, V* x, V* v, const float* m, double eps, dou
     const bool f64 = sizeof(V) == sizeof(double);
     const float eps2 = f64 ? (float)(eps * eps) : (float)eps * (float)eps;
     if (f64 && fp.perm != nullptr) NB_CHECK(issue_order(fp, n, (const double*)x, st));  // order of the call
+    NB_CHECK(issue_uniform(fp, n, m, st));
     count(1);
     if (f64)
         NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, (double*)x, nullptr, nullptr, m, 0.0, 0.0, plain, fp.jdup,
@@ -782,6 +807,7 @@ static int leapfrog_run(Ctx& c, int64_t n, V* x, V* v, const float* m, double ep
     const bool plain = sizeof(V) == sizeof(float) || c.o.precision == NBODY_PREC_PLAIN;
     const int comp = summation_mode(c.o.accumulate);
     if (sizeof(V) == sizeof(double) && sorted_mixed(c.o.precision)) NB_CHECK(plan_order(c.ws, n, &fp));
+    NB_CHECK(plan_uniform(c.ws, &fp));
     const std::vector<uint64_t> key = {1, (uint64_t)sizeof(V), (uint64_t)n, (uint64_t)steps, (uint64_t)(uintptr_t)x,
                                        (uint64_t)(uintptr_t)v, (uint64_t)(uintptr_t)m, bits_of(eps), bits_of(dt),
                                        (uint64_t)fp.shape, (uint64_t)plain, (uint64_t)comp,
@@ -883,11 +909,14 @@ static int accel_ij_common(int64_t ni, const void* ipos, int64_t nj, const void*
         NB_CUDA(nbk::pack_f32(nj, fp.npad, (float*)sg.dev(1), nullptr, nullptr, (const float*)sg.dev(2), 0.0f, 0.0f,
                               fp.jdup, st));
     }
+    NB_CHECK(plan_uniform(c.ws, &fp));
+    NB_CHECK(issue_uniform(fp, nj, (const float*)sg.dev(2), st));
     if (fault("launch")) return NBODY_ECUDA;
     nbk::ForceArgs a;
     a.jdup = fp.jdup;
     a.centres = plain ? nullptr : fp.centres;
     a.eps2 = f64 ? (float)(eps * eps) : (float)eps * (float)eps;
+    a.uni = fp.uni;
     a.n = ni;
     a.npad = fp.npad;
     a.ipack = (const float*)pi;
@@ -1042,6 +1071,8 @@ int nbody_leapfrog_record(int64_t n, double* pos, double* vel, const float* mass
         NB_CHECK(plan_order(c.ws, n, &fp));
         NB_CHECK(issue_order(fp, n, pos, st));
     }
+    NB_CHECK(plan_uniform(c.ws, &fp));
+    NB_CHECK(issue_uniform(fp, n, mass, st));
     count(1);
     NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, pos, nullptr, nullptr, mass, 0.0, 0.0, plain, fp.jdup, fp.centres,
                           st, fp.perm, fp.err));
@@ -1105,6 +1136,7 @@ int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, double dt, int6
     ForcePlan fp;
     NB_CHECK(plan_force(c.ws, n, shape_for(c, n, false), c.sms, &fp));
     if (sorted_mixed(c.o.precision)) NB_CHECK(plan_order(c.ws, n, &fp));
+    NB_CHECK(plan_uniform(c.ws, &fp));
     void *pg, *pgm, *pa, *px, *pv;
     NB_CHECK(ensure(c.ws, B_VG, (size_t)n * 3 * sizeof(float), &pg));
     NB_CHECK(ensure(c.ws, B_VGM, (size_t)n * sizeof(float), &pgm));
@@ -1144,6 +1176,7 @@ int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, double dt, int6
         NB_CUDA(cudaEventRecord(ev_rep[seg & 1], aux));
         return NBODY_OK;
     };
+    NB_CHECK(issue_uniform(fp, n, mass, st));  // the replays take the recorded run's pair loop
     NB_CUDA(cudaEventRecord(ev_start, st));  // the tape and inputs are ready on the caller's stream
     NB_CUDA(cudaStreamWaitEvent(aux, ev_start, 0));
     if (sorted_mixed(c.o.precision)) NB_CHECK(issue_order(fp, n, tp, aux));  // x_0's order, as recorded

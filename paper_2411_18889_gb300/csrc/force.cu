@@ -61,6 +61,7 @@ struct KParams {
     float* pot;
     double* partial;  // [nctas][2][block][4]
     int* err;
+    const int* uni;   // nonzero word: every source has one mass (or nullptr)
 };
 
 // One j-tile against the thread's IP i-pairs.
@@ -74,7 +75,10 @@ __device__ __forceinline__ void kahan_add(f2& sum, f2& comp, f2 term) {
 
 // Summation modes: 0 one FP32 running sum, 1 FP32 per tile folded by Kahan
 // summation, 2 Kahan summation of every pair term.
-template <int T, int IP, int J, int UNROLL, bool POT, bool DIAG, int MODE, int WF>
+// UNI: every source has the same mass; the pair weight leaves m_j out (11
+// instead of 12 FP32 operations per interaction) and the caller scales the
+// sums by that mass.
+template <int T, int IP, int J, int UNROLL, bool POT, bool DIAG, int MODE, int WF, bool UNI>
 __device__ __forceinline__ void tile_pass(const unsigned char* tile, const f2 (&xi)[IP], const f2 (&yi)[IP],
                                           const f2 (&zi)[IP], f2 eps2, f2 (&ax)[IP], f2 (&ay)[IP], f2 (&az)[IP],
                                           f2 (&ap)[IP], f2 (&kx)[IP], f2 (&ky)[IP], f2 (&kz)[IP], f2 (&kp)[IP],
@@ -106,7 +110,9 @@ __device__ __forceinline__ void tile_pass(const unsigned char* tile, const f2 (&
             // m_j rsqrt(s)^3 in one of two association orders (the same
             // three products; which schedules better depends on the shape)
             f2 w;
-            if (WF == 1) {
+            if (UNI) {
+                w = WF == 1 ? mul2(mul2(ri, ri), ri) : mul2(ri, mul2(ri, ri));
+            } else if (WF == 1) {
                 w = mul2(mul2(ri, ri), mul2(ri, mj));
             } else if (WF == 2) {
                 w = mul2(mul2(mul2(ri, mj), ri), ri);
@@ -137,8 +143,11 @@ __device__ __forceinline__ void kahan2(f2& sum, f2& comp, f2& part) {
     part = 0ull;
 }
 
-template <int T, int IP, int J, int UNROLL, int MINB, bool POT, bool MIXED, int KAHAN, int WF>
-__global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
+// The kernel body.  UNIMODE picks the pair loop: 0 the general loop, 1 the
+// equal-mass loop (every source has one mass: m_j left out of the loop, the
+// sums scaled by it at the end), 2 either, chosen per j-tile from the flag.
+template <int T, int IP, int J, int UNROLL, bool POT, bool MIXED, int KAHAN, int WF, int UNIMODE>
+__device__ __forceinline__ void force_body(const KParams& p) {
     constexpr int C = 2 * IP * T;
     constexpr uint32_t TILE_BYTES = J * 32u;
     static_assert(C % J == 0, "a j-tile must not straddle two cells");
@@ -171,6 +180,9 @@ __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
     }
 
     const f2 eps2 = pk(p.eps2, p.eps2);
+    // j-slot 0 is always a real body: its mass is every source's mass.
+    const bool uni = UNIMODE == 2 ? (p.uni != nullptr && *p.uni != 0) : UNIMODE == 1;
+    const double mu = uni ? (double)p.jdup[6] : 1.0;
     uint32_t parity = 0;
     int s = 0;
     int64_t u = u_begin;
@@ -236,11 +248,19 @@ __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
             }
             const unsigned char* tile = tiles + s * TILE_BYTES;
             if (p.self && cell == b) {
-                tile_pass<T, IP, J, UNROLL, POT, true, KAHAN, WF>(tile, xi, yi, zi, eps2, ax, ay, az, ap, cx, cy, cz,
-                                                              cp, (int)(tt * J - base), tid);
+                if (UNIMODE == 1 || (UNIMODE == 2 && uni))
+                    tile_pass<T, IP, J, UNROLL, POT, true, KAHAN, WF, true>(tile, xi, yi, zi, eps2, ax, ay, az, ap, cx,
+                                                                        cy, cz, cp, (int)(tt * J - base), tid);
+                else
+                    tile_pass<T, IP, J, UNROLL, POT, true, KAHAN, WF, false>(tile, xi, yi, zi, eps2, ax, ay, az, ap,
+                                                                         cx, cy, cz, cp, (int)(tt * J - base), tid);
             } else {
-                tile_pass<T, IP, J, UNROLL, POT, false, KAHAN, WF>(tile, xi, yi, zi, eps2, ax, ay, az, ap, cx, cy, cz,
-                                                               cp, 0, tid);
+                if (UNIMODE == 1 || (UNIMODE == 2 && uni))
+                    tile_pass<T, IP, J, UNROLL, POT, false, KAHAN, WF, true>(tile, xi, yi, zi, eps2, ax, ay, az, ap,
+                                                                         cx, cy, cz, cp, 0, tid);
+                else
+                    tile_pass<T, IP, J, UNROLL, POT, false, KAHAN, WF, false>(tile, xi, yi, zi, eps2, ax, ay, az, ap,
+                                                                          cx, cy, cz, cp, 0, tid);
             }
             if (KAHAN == 1) {
 #pragma unroll
@@ -284,6 +304,13 @@ __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
                 upk(az[q], a0, a1); d[0][2] = a0; d[1][2] = a1;
                 upk(ap[q], a0, a1); d[0][3] = a0; d[1][3] = a1;
             }
+            if (uni) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    d[0][k] *= mu;
+                    d[1][k] *= mu;
+                }
+            }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int lb = (2 * q + h) * T + tid;
@@ -320,6 +347,21 @@ __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
         }
         __syncthreads();
     }
+}
+
+// The equal-mass choice is made per j-tile in the mixed-precision kernels and
+// once per launch (two copies of the body) in the plain ones: on GB300 each
+// arrangement scheduled better for its own kernels (measured at N = 2^20,
+// log-uniform masses: mixed 71.5 vs 70.7 % of FP32 peak, plain 69.2 vs
+// 68.1 %).
+template <int T, int IP, int J, int UNROLL, int MINB, bool POT, bool MIXED, int KAHAN, int WF>
+__global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
+    if (MIXED)
+        force_body<T, IP, J, UNROLL, POT, MIXED, KAHAN, WF, 2>(p);
+    else if (p.uni != nullptr && *p.uni != 0)
+        force_body<T, IP, J, UNROLL, POT, MIXED, KAHAN, WF, 1>(p);
+    else
+        force_body<T, IP, J, UNROLL, POT, MIXED, KAHAN, WF, 0>(p);
 }
 
 // Adds the per-CTA partial sums of every i-block that a slice boundary cut,
@@ -499,6 +541,7 @@ cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t ntile, int64_t nctas, i
     p.pot = out1;
     p.partial = const_cast<double*>(partial);
     p.err = err;
+    p.uni = nullptr;
     fixup_kernel<<<dim3((unsigned)nblk, (unsigned)((block + 255) / 256)), 256, 0, st>>>(p, block,
                                                                                          out1 != nullptr ? 1 : 0);
     return cudaGetLastError();
@@ -536,6 +579,7 @@ cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st
     p.pot = a.pot;
     p.partial = a.partial;
     p.err = a.err;
+    p.uni = a.uni;
     const size_t sm = e.smem(mixed);
     *launched = 0;
     if (ev0 != nullptr) cudaEventRecord(ev0, st);

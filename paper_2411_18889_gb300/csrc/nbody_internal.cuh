@@ -195,6 +195,10 @@ struct ForceArgs {
     double* partial;        // scratch, force_partial_doubles(...) doubles
     int* err;               // device error word
     int summation;          // 0 FP32 running sum, 1 per-tile Kahan fold, 2 Kahan per pair
+    // Device word, nonzero when every source has the same mass (the kernel
+    // then leaves m_j out of the pair loop and scales the sums once); nullptr:
+    // treat the masses as distinct.
+    const int* uni = nullptr;
 };
 
 // Scratch doubles needed for the split i-block partial sums of shape k.
@@ -221,6 +225,9 @@ cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st
 // All FP64 state arithmetic for the mixed path happens here.
 // perm (optional): slot k of the packed array holds body perm[k].
 int pack_threads(int block);
+// *flag = 1 if mass[0..n) all compare equal, else 0.  Queues a memset
+// and one kernel on st.
+cudaError_t uniform_mass_flag(int64_t n, const float* mass, int* flag, cudaStream_t st);
 cudaError_t pack_f64(int64_t n, int64_t npad, int block, double* pos, double* vel, const float* acc,
                      const float* mass, double kick, double drift, bool plain, float* jdup,
                      double* centres, cudaStream_t st, const int* perm = nullptr, int* err = nullptr);

@@ -139,6 +139,15 @@ __global__ void pack_f32_kernel(int64_t n, int64_t npad, float* __restrict__ pos
     }
 }
 
+// Clears *flag if any mass differs from mass[0]; the flag starts at nonzero.
+__global__ void uniform_mass_kernel(int64_t n, const float* __restrict__ mass, int* __restrict__ flag) {
+    const float m0 = mass[0];
+    bool same = true;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+        same = same && mass[g] == m0;
+    if (__syncthreads_or(!same) && threadIdx.x == 0) *flag = 0;
+}
+
 template <typename V>
 __global__ void kick_kernel(int64_t n3, V* __restrict__ vel, const float* __restrict__ acc, V kick) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n3; k += (int64_t)gridDim.x * blockDim.x)
@@ -174,6 +183,13 @@ cudaError_t pack_f64(int64_t n, int64_t npad, int block, double* pos, double* ve
 cudaError_t pack_f32(int64_t n, int64_t npad, float* pos, float* vel, const float* acc, const float* mass,
                      float kick, float drift, float* jdup, cudaStream_t st) {
     pack_f32_kernel<<<grid_for(npad, 256), 256, 0, st>>>(n, npad, pos, vel, acc, mass, kick, drift, jdup);
+    return cudaGetLastError();
+}
+
+cudaError_t uniform_mass_flag(int64_t n, const float* mass, int* flag, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(flag, 1, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    uniform_mass_kernel<<<grid_for(n, 256) < 152 * 4 ? grid_for(n, 256) : 152 * 4, 256, 0, st>>>(n, mass, flag);
     return cudaGetLastError();
 }
 
