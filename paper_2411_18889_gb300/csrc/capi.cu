@@ -958,6 +958,7 @@ struct VjpPlan {
     double* centres;
     double* partial;
     int* err;
+    int* uni = nullptr;  // device word: all masses equal (the flag of the call's force plan)
 };
 
 static int plan_vjp(Workspace* ws, int64_t n, int shape, int num_sms, VjpPlan* vp) {
@@ -991,6 +992,7 @@ static int run_vjp(const VjpPlan& vp, int64_t n, float eps2, bool mixed, bool ha
     a.g_mass = g_mass;
     a.partial = vp.partial;
     a.err = vp.err;
+    a.uni = vp.uni;
     int launched = 0;
     cudaError_t e = nbk::vjp_launch(vp.shape, a, num_sms, st, &launched);
     count(launched);
@@ -1020,6 +1022,13 @@ int nbody_accel_vjp(int64_t n, const double* pos, const float* mass, double eps,
     VjpPlan vp;
     NB_CHECK(plan_vjp(c.ws, n, c.o.config >= 0 ? c.o.config : choose_vjp_shape(n), c.sms, &vp));
     const bool plain = c.o.precision == NBODY_PREC_PLAIN;
+    {
+        void* pu;
+        NB_CHECK(ensure(c.ws, B_UNI, sizeof(int), &pu));
+        vp.uni = (int*)pu;
+        count(1);
+        NB_CUDA(nbk::uniform_mass_flag(n, (const float*)sg.dev(1), vp.uni, c.o.stream));
+    }
     count(1);
     NB_CUDA(nbk::pack_vjp(n, vp.npad, vp.block, (const double*)sg.dev(0), (const float*)sg.dev(1),
                           (const float*)sg.dev(2), nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, 1.0,
@@ -1177,6 +1186,7 @@ int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, double dt, int6
         return NBODY_OK;
     };
     NB_CHECK(issue_uniform(fp, n, mass, st));  // the replays take the recorded run's pair loop
+    vp.uni = fp.uni;                           // and the VJPs the equal-mass loop when it applies
     NB_CUDA(cudaEventRecord(ev_start, st));  // the tape and inputs are ready on the caller's stream
     NB_CUDA(cudaStreamWaitEvent(aux, ev_start, 0));
     if (sorted_mixed(c.o.precision)) NB_CHECK(issue_order(fp, n, tp, aux));  // x_0's order, as recorded

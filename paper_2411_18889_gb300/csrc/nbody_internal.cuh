@@ -290,6 +290,9 @@ struct VjpArgs {
     float* g_mass;          // [n]
     double* partial;
     int* err;
+    // Device word, nonzero when every body has the same mass (the pair loop
+    // then forms u = mu (lam_j - lam_k) without the masses); nullptr: no.
+    const int* uni = nullptr;
 };
 int vjp_num_shapes();
 VjpShape vjp_shape(int k);

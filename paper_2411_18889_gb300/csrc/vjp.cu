@@ -43,9 +43,13 @@ struct VParams {
     float* g_mass;
     double* partial;
     int* err;
+    const int* uni;  // nonzero word: every body has one mass (or nullptr)
 };
 
-template <int T, int IP, int J, int UNROLL, bool MU, bool DIAG>
+// UNI: every body has the same mass mu; u = m_k lam_j - m_j lam_k becomes
+// mu (lam_j - lam_k), formed without the masses (27 instead of 30 packed
+// operations per pair), and the caller scales the position gradient by mu.
+template <int T, int IP, int J, int UNROLL, bool MU, bool DIAG, bool UNI>
 __device__ __forceinline__ void vjp_tile(const unsigned char* tile, const f2 (&xi)[IP], const f2 (&yi)[IP],
                                          const f2 (&zi)[IP], const f2 (&nlx)[IP], const f2 (&nly)[IP],
                                          const f2 (&nlz)[IP], const f2 (&mi)[IP], const f2 (&nmi)[IP],
@@ -81,10 +85,10 @@ __device__ __forceinline__ void vjp_tile(const unsigned char* tile, const f2 (&x
             const f2 ri2 = mul2(ri, ri);
             const f2 r3 = mul2(ri, ri2);
             const f2 r5m3 = mul2(r3, mul2(ri2, m3));  // -3 s^{-5/2}
-            // u = m_k lam_j - m_j lam_k
-            const f2 ux = fma2(mi[q], lxj, mul2(mj, nlx[q]));
-            const f2 uy = fma2(mi[q], lyj, mul2(mj, nly[q]));
-            const f2 uz = fma2(mi[q], lzj, mul2(mj, nlz[q]));
+            // u = m_k lam_j - m_j lam_k (UNI: lam_j - lam_k, times mu later)
+            const f2 ux = UNI ? add2(lxj, nlx[q]) : fma2(mi[q], lxj, mul2(mj, nlx[q]));
+            const f2 uy = UNI ? add2(lyj, nly[q]) : fma2(mi[q], lyj, mul2(mj, nly[q]));
+            const f2 uz = UNI ? add2(lzj, nlz[q]) : fma2(mi[q], lzj, mul2(mj, nlz[q]));
             f2 du = mul2(dx, ux);
             du = fma2(dy, uy, du);
             du = fma2(dz, uz, du);
@@ -99,7 +103,7 @@ __device__ __forceinline__ void vjp_tile(const unsigned char* tile, const f2 (&x
             if (MU) {
                 // -s^{-3/2} d (mu_j m_k + mu_k m_j) with d = r_j - r_k, and mu_j s^{-1/2};
                 // nmi, nmui hold -m_k, -mu_k
-                const f2 cm = mul2(r3, fma2(muj, nmi[q], mul2(nmui[q], mj)));
+                const f2 cm = UNI ? mul2(r3, sub2(nmui[q], muj)) : mul2(r3, fma2(muj, nmi[q], mul2(nmui[q], mj)));
                 gx[q] = fma2(cm, dx, gx[q]);
                 gy[q] = fma2(cm, dy, gy[q]);
                 gz[q] = fma2(cm, dz, gz[q]);
@@ -141,6 +145,10 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
         if (u_begin + 1 < u_end) issue(1, u_begin + 1);
     }
     const f2 eps2 = pk(p.eps2, p.eps2);
+    // One mass for every body (j-slot 0 is always a real body): the pair loop
+    // leaves the masses out of u and the position gradient is scaled by mu.
+    const bool uni = p.uni != nullptr && *p.uni != 0;
+    const float mu = uni ? p.jv[6] : 1.0f;
     uint32_t parity = 0;
     int s = 0;
     int64_t u = u_begin;
@@ -203,12 +211,21 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
                 }
             }
             const unsigned char* tile = tiles + s * TILE_BYTES;
-            if (cell == b)
-                vjp_tile<T, IP, J, UNROLL, MU, true>(tile, xi, yi, zi, nlx, nly, nlz, mi, nmi, nmui, eps2, gx, gy, gz, gm,
-                                                     (int)(tt * J - base), tid);
-            else
-                vjp_tile<T, IP, J, UNROLL, MU, false>(tile, xi, yi, zi, nlx, nly, nlz, mi, nmi, nmui, eps2, gx, gy, gz,
-                                                      gm, 0, tid);
+            if (cell == b) {
+                if (uni)
+                    vjp_tile<T, IP, J, UNROLL, MU, true, true>(tile, xi, yi, zi, nlx, nly, nlz, mi, nmi, nmui, eps2, gx,
+                                                               gy, gz, gm, (int)(tt * J - base), tid);
+                else
+                    vjp_tile<T, IP, J, UNROLL, MU, true, false>(tile, xi, yi, zi, nlx, nly, nlz, mi, nmi, nmui, eps2,
+                                                                gx, gy, gz, gm, (int)(tt * J - base), tid);
+            } else {
+                if (uni)
+                    vjp_tile<T, IP, J, UNROLL, MU, false, true>(tile, xi, yi, zi, nlx, nly, nlz, mi, nmi, nmui, eps2,
+                                                                gx, gy, gz, gm, 0, tid);
+                else
+                    vjp_tile<T, IP, J, UNROLL, MU, false, false>(tile, xi, yi, zi, nlx, nly, nlz, mi, nmi, nmui, eps2,
+                                                                 gx, gy, gz, gm, 0, tid);
+            }
 #pragma unroll
             for (int q = 0; q < IP; ++q) {
                 tx[q] = add2(tx[q], gx[q]);
@@ -232,6 +249,13 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
             upk(ty[q], v[0][1], v[1][1]);
             upk(tz[q], v[0][2], v[1][2]);
             upk(tm[q], v[0][3], v[1][3]);
+            if (uni) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    v[0][k] *= mu;
+                    v[1][k] *= mu;
+                }
+            }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int lb = (2 * q + h) * T + tid;
@@ -470,6 +494,7 @@ cudaError_t vjp_launch(int k, const VjpArgs& a, int num_sms, cudaStream_t st, in
     p.g_mass = a.g_mass;
     p.partial = a.partial;
     p.err = a.err;
+    p.uni = a.uni;
     *launched = 0;
     e.fn[mu][mixed]<<<(unsigned)p.nctas, e.shape.threads, e.smem(mixed), st>>>(p);
     cudaError_t err = cudaGetLastError();

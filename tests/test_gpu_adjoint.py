@@ -40,10 +40,13 @@ def gpu_vjp(nb, pos, mass32, eps, lam32, mu32=None, **kw):
     return gp.cpu().numpy(), gm.cpu().numpy()
 
 
+@pytest.mark.parametrize("masses", ["loguniform", "equal"])
 @pytest.mark.parametrize("with_mu", [False, True])
 @pytest.mark.parametrize("n", [2, 33, 1000, 3001])
-def test_force_vjp_matches_oracle(nb, oracle_mod, n, with_mu):
-    p, _, m = ni.plummer(n, 700 + n, masses="loguniform")
+def test_force_vjp_matches_oracle(nb, oracle_mod, n, with_mu, masses):
+    """Equal masses take the VJP's loop that forms u = mu (lam_j - lam_k)
+    without the masses; distinct masses the general loop."""
+    p, _, m = ni.plummer(n, 700 + n, masses=masses)
     m32 = m.astype(np.float32)
     lam = ni.gaussian((n, 3), 701).astype(np.float32)
     mu = ni.gaussian((n,), 702).astype(np.float32) if with_mu else None

@@ -265,3 +265,38 @@ def test_morton_order_shrinks_close_pair_errors(nb, oracle_mod):
           f"caller's order median {np.median(eu):.3g} max {eu.max():.3g}")
     check(acc_s, pot_s, ra, rp)
     assert es.max() < 0.5 * eu.max()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "plain"])
+def test_equal_mass_loop_matches_general_loop(nb, precision):
+    """Equal masses take the pair loops without m_j (force and VJP, the sums
+    scaled once); raising one body's mass by one FP32 ulp sends the same
+    inputs through the general loops.  The two agree to FP32 rounding."""
+    import torch
+    n = 5000
+    p, _, m = ni.plummer(n, 7100)
+    m32 = m.astype(np.float32)
+    assert np.all(m32 == m32[0])
+    m_gen = m32.copy()
+    m_gen[-1] = np.nextafter(m_gen[-1], np.float32(1.0))
+    prec = nb.NBODY_PREC_MIXED if precision == "mixed" else nb.NBODY_PREC_PLAIN
+    P = torch.from_numpy(p).cuda()
+    out = []
+    for mm in (m32, m_gen):
+        acc = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        pot = torch.empty((n,), dtype=torch.float32, device="cuda")
+        nb.nbody_accel(P, torch.from_numpy(mm).cuda(), 2.0 ** -8, acc, pot, precision=prec)
+        lam = torch.from_numpy(ni.gaussian((n, 3), 7101).astype(np.float32)).cuda()
+        gp = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        gm = torch.empty((n,), dtype=torch.float32, device="cuda")
+        nb.nbody_accel_vjp(P, torch.from_numpy(mm).cuda(), 2.0 ** -8, lam, None, gp, gm, precision=prec)
+        torch.cuda.synchronize()
+        out.append([x.cpu().numpy().astype(np.float64) for x in (acc, pot, gp, gm)])
+    (a0, p0, g0, h0), (a1, p1, g1, h1) = out
+    ea = np.linalg.norm(a0 - a1, axis=1) / np.linalg.norm(a1, axis=1)
+    assert np.median(ea) <= 1e-6 and ea.max() <= 1e-4, (np.median(ea), ea.max())
+    assert (np.abs(p0 - p1) / np.abs(p1)).max() <= 1e-5
+    eg = np.linalg.norm(g0 - g1, axis=1)
+    assert np.median(eg / np.linalg.norm(g1, axis=1)) <= 1e-5, np.median(eg / np.linalg.norm(g1, axis=1))
+    assert np.median(np.abs(h0 - h1) / np.abs(h1)) <= 1e-5
+    assert nb.nbody_last_device_error() == 0
