@@ -374,13 +374,15 @@ __global__ void fixup_kernel(const KParams p, int C, int pot_on) {
     const int64_t c_lo = ((u0 + 1) * p.nctas - 1) / p.units;
     const int64_t c_hi = ((u1 + 1) * p.nctas - 1) / p.units;
     if (c_lo == c_hi) return;
+    // Every CTA after c_lo starts its slice inside block b (partial slot 0);
+    // c_lo does only if its slice starts exactly at the block's first unit.
+    const int slot_lo = (c_lo * p.units / p.nctas == u0) ? 0 : 1;
     for (int lb = blockIdx.y * blockDim.x + threadIdx.x; lb < C; lb += gridDim.y * blockDim.x) {
         const int64_t g = b * C + lb;
         if (g >= p.n) break;
         double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0;
         for (int64_t c = c_lo; c <= c_hi; ++c) {
-            const int64_t ub = c * p.units / p.nctas;
-            const int slot = (ub / p.ntile == b) ? 0 : 1;
+            const int slot = c == c_lo ? slot_lo : 0;
             const int64_t pi = (c * 2 + slot) * C + lb;
             if (!in_range(pi, p.nctas * 2 * C, p.err)) continue;
             const double4 v = reinterpret_cast<const double4*>(p.partial)[pi];
