@@ -198,12 +198,26 @@ def workload_config(w):
 
 
 def profile_case(n: int, kind: str = "force") -> int:
-    """Two launches of one kernel for ncu captures."""
+    """A small case for ncu captures: two launches of the force, VJP or batched
+    kernel, or one run of the adjoint workload (record + gradient)."""
     import torch
     import nbody_inputs as ni
     import paper_2411_18889_gb300 as nb
     nb.load()
-    if kind == "batched":
+    if kind == "adjoint":  # the adjoint workload once (N = 16384 fixed): record, then the gradient
+        w = ni.adjoint_case()
+        n, K, ck = w.n, w.steps, w.extra["ckpt_every"]
+        M = torch.from_numpy(w.mass.astype(np.float32)).cuda()
+        tape = torch.empty(nb.nbody_tape_bytes(n, K, ck), dtype=torch.uint8, device="cuda")
+        P = torch.from_numpy(w.pos).cuda()
+        V = torch.from_numpy(w.vel).cuda()
+        nb.nbody_leapfrog_record(P, V, M, w.eps, w.dt, K, ck, tape)
+        gxT = 2.0 * M.double()[:, None] * (P - torch.from_numpy(w.extra["target"]).cuda())
+        acc = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        gv0 = torch.empty_like(acc)
+        gm = torch.empty((n,), dtype=torch.float64, device="cuda")
+        nb.nbody_leapfrog_vjp(M, w.eps, w.dt, K, ck, tape, gxT, torch.zeros_like(acc), acc, gv0, gm)
+    elif kind == "batched":
         off, pos, _, mass, eps = ni.ragged_batch(nsys=n)
         O = torch.from_numpy(off).cuda()
         P = torch.from_numpy(pos.astype(np.float32)).cuda()
@@ -373,8 +387,9 @@ def main():
     ap.add_argument("--profile-case", type=int, default=0, metavar="N",
                     help="only run one kernel twice at size N, for profilers: the force (nbody_accel, mixed, "
                          "no potential, the precision workload's recipe), the VJP (nbody_accel_vjp) or the "
-                         "batched force (the ragged recipe with N systems)")
-    ap.add_argument("--profile-kind", default="force", choices=["force", "vjp", "batched"])
+                         "batched force (the ragged recipe with N systems); 'adjoint' runs the adjoint workload "
+                         "once (record + gradient; N is ignored)")
+    ap.add_argument("--profile-kind", default="force", choices=["force", "vjp", "batched", "adjoint"])
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

@@ -76,6 +76,26 @@ def test_accel_every_shape_in_bounds(nb, checked_lib, n, precision):
         both(nb, checked_lib, lambda: accel_f64(nb, p, m, 2.0 ** -9, config=k, precision=precision))
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_equal_mass_loops_in_bounds(nb, checked_lib, precision):
+    """Equal masses: the force and VJP kernels take their loops without m_j."""
+    import torch
+    n = 4099
+    p, _, m = ni.plummer(n, 915)
+    lam = ni.gaussian((n, 3), 916)
+    for k in range(nb.nbody_num_configs()):
+        both(nb, checked_lib, lambda: accel_f64(nb, p, m, 2.0 ** -9, config=k, precision=precision))
+    for k in range(4):
+        def run():
+            gp = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+            gm = torch.empty((n,), dtype=torch.float32, device="cuda")
+            nb.nbody_accel_vjp(t(p, np.float64), t(m, np.float32), 2.0 ** -7, t(lam, np.float32), None, gp, gm,
+                               config=k, precision=precision)
+            return gp.cpu().numpy(), gm.cpu().numpy()
+
+        both(nb, checked_lib, run)
+
+
 @pytest.mark.parametrize("accumulate", [1, 2])
 def test_accel_summation_modes_in_bounds(nb, checked_lib, accumulate):
     p, _, m = ni.plummer(5003, 910, masses="loguniform")
