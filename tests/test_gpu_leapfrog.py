@@ -148,3 +148,28 @@ def test_repeated_calls_replay_a_cuda_graph(nb):
         nb.nbody_leapfrog_f32(Q2, W2, m32, 0.01, 2.0 ** -8, 2)
     torch.cuda.synchronize()
     assert torch.equal(Q1, Q2) and torch.equal(W1, W2)
+
+
+def test_graph_replay_rechecks_equal_masses(nb):
+    """The equal-mass check runs inside the captured sequence: when the caller
+    changes the masses in place between two identical calls, the replayed
+    graph takes the general loop (and back), bit-identical to calls that
+    never repeat their arguments."""
+    import torch
+    n = 3000
+    p, v, m = ni.plummer(n, 18)
+    equal = m.astype(np.float32)
+    mixed = equal.copy()
+    mixed[::7] *= np.float32(3.0)
+    M = t(equal, np.float32)
+    P1, V1 = t(p, np.float64), t(v, np.float64)
+    for masses in (equal, equal, mixed, mixed, equal):  # calls 2.. replay the graph of call 2
+        M.copy_(torch.from_numpy(masses))
+        nb.nbody_leapfrog(P1, V1, M, 0.01, 2.0 ** -8, 2)
+    P2, V2 = t(p, np.float64), t(v, np.float64)
+    for masses in (equal, equal, mixed, mixed, equal):
+        P2, V2 = P2.clone(), V2.clone()  # new arrays: never captured
+        nb.nbody_leapfrog(P2, V2, t(masses, np.float32), 0.01, 2.0 ** -8, 2)
+    torch.cuda.synchronize()
+    assert torch.equal(P1, P2) and torch.equal(V1, V2)
+    assert nb.nbody_last_device_error() == 0
