@@ -10,11 +10,12 @@
 // every force evaluation and every kick and drift of all steps happen without
 // another launch.
 //
-// Shapes.  For batches whose largest system has a thousand bodies or more, one
-// 512-thread CTA per SM owns a system (16 warps on one system, i-passes of 2048
-// bodies); below that, two 256-thread CTAs per SM hold one system each.  On
-// GB300 the single large CTA ran the ragged 64-to-4096-body workload at 71.7 %
-// of FP32 peak against 66.1 % for two 256-thread CTAs.
+// Shapes (chosen by the largest system of the batch through the tune table).
+// From about 760 bodies up one 512-thread CTA per SM owns a system (16 warps
+// on one system, i-passes of 2048 bodies); smaller batches run 256- or
+// 128-thread CTAs, several per SM, each on its own system.  On GB300 the
+// single large CTA ran the ragged 64-to-4096-body workload at 71.7 % of FP32
+// peak against 66.1 % for two 256-thread CTAs per SM.
 //
 // Layout.  Shared memory holds the system as j-pairs (x0,x1,y0,y1,z0,z1,m0,m1):
 // 16 bytes per body, so a 4096-body system takes 64 KiB.  Each thread keeps I
