@@ -118,3 +118,39 @@ def test_throughput_workload_energy(nb, oracle_mod):
     e_dev = nb.nbody_energy_f32(P, V, M, np.float32(w.eps))["E"]
     assert abs(e_dev - e_ref) <= 1e-5 * abs(e0)
     assert np.abs(P.cpu().numpy() - p_ref).max() <= 1e-5
+
+
+def test_four_million_bodies(nb, oracle_mod):
+    """Beyond the benchmark's size: N = 2^22 + 777 (a ragged last cell) with the
+    precision recipe (offset centre, log-uniform masses), one mixed-precision
+    force evaluation with the potential and one leapfrog step, checked on 512
+    seeded bodies against the oracle: the 64-bit indexing of the grids, the
+    Morton order and the result stores at 4.2 million bodies."""
+    import torch
+    n = (1 << 22) + 777
+    p, v, m = ni.plummer(n, 31, masses="loguniform", offset=ni.plummer_offset())
+    m32 = m.astype(np.float32)
+    P, M = t(p, np.float64), t(m32, np.float32)
+    acc = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    pot = torch.empty((n,), dtype=torch.float32, device="cuda")
+    nb.nbody_accel(P, M, 2.0 ** -9, acc, pot)
+    torch.cuda.synchronize()
+    assert nb.nbody_last_device_error() == 0
+    idx = ni.subsample(n, 512, 32)
+    ra, rp = oracle_mod.accel_subset(p, m32.astype(np.float64), 2.0 ** -9, idx)
+    e = rel(acc.cpu().numpy()[idx], ra)
+    ep = np.abs(pot.cpu().numpy()[idx] - rp) / np.abs(rp)
+    assert np.median(e) <= 2e-6 and e.max() <= 1e-4, (np.median(e), e.max())
+    assert ep.max() <= 1e-5
+    V = t(v, np.float64)
+    nb.nbody_leapfrog(P, V, M, 2.0 ** -9, 2.0 ** -9, 1)
+    torch.cuda.synchronize()
+    assert nb.nbody_last_device_error() == 0
+    # one KDK step: x1 = x0 + dt v0 + dt^2/2 a(x0), so the sampled bodies moved
+    # as their oracle accelerations say, to the accelerations' accuracy and a
+    # few FP64 ulps of the offset coordinates
+    x1 = P.cpu().numpy()[idx]
+    h2 = 0.5 * 2.0 ** -18
+    expect = p[idx] + 2.0 ** -9 * v[idx] + h2 * ra
+    tol = h2 * 2e-4 * np.linalg.norm(ra, axis=1)[:, None] + 8 * np.spacing(np.abs(p[idx]))
+    assert np.all(np.abs(x1 - expect) <= tol)
