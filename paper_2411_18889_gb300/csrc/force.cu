@@ -403,30 +403,35 @@ __global__ void fixup_kernel(const KParams p, int C, int pot_on) {
 typedef void (*KernelFn)(const KParams);
 
 struct ShapeEntry {
-    ForceShape shape;
+    ForceShape shape;  // shape.jtile: the mixed-precision kernels' j-tile
+    int jt[2];         // j-tile of the [plain, mixed] kernels
     int cap;  // most CTAs per SM the persistent grid uses (16 warps per SM)
     KernelFn fn[2][2][3];  // [pot][mixed][summation mode]
     size_t smem(bool mixed) const {
-        return 2u * shape.jtile * 32u + (mixed ? (size_t)shape.ipairs * 3 * shape.threads * 8 : 0);
+        return 2u * jt[mixed ? 1 : 0] * 32u + (mixed ? (size_t)shape.ipairs * 3 * shape.threads * 8 : 0);
     }
 };
 
 // WF0: association order of m_j rsqrt(s)^3 in the kernels without the
-// potential (those with it use order 0).
-template <int T, int IP, int J, int UNROLL, int MINB, int WF0 = 0>
+// potential (those with it use order 0).  J, UNROLL: j-tile and j-unroll of
+// the mixed-precision kernels; JP, UP: of the plain ones (the best pair
+// differs between the two on some shapes).
+template <int T, int IP, int J, int UNROLL, int MINB, int WF0 = 0, int JP = J, int UP = UNROLL>
 ShapeEntry make_entry() {
     ShapeEntry e;
     e.shape = ForceShape{T, IP, J, 2 * IP * T};
+    e.jt[0] = JP;
+    e.jt[1] = J;
     e.cap = T >= 512 ? 1 : 512 / T;
-    e.fn[0][0][0] = force_kernel<T, IP, J, UNROLL, MINB, false, false, 0, WF0>;
-    e.fn[0][0][1] = force_kernel<T, IP, J, UNROLL, MINB, false, false, 1, WF0>;
-    e.fn[0][0][2] = force_kernel<T, IP, J, UNROLL, MINB, false, false, 2, WF0>;
+    e.fn[0][0][0] = force_kernel<T, IP, JP, UP, MINB, false, false, 0, WF0>;
+    e.fn[0][0][1] = force_kernel<T, IP, JP, UP, MINB, false, false, 1, WF0>;
+    e.fn[0][0][2] = force_kernel<T, IP, JP, UP, MINB, false, false, 2, WF0>;
     e.fn[0][1][0] = force_kernel<T, IP, J, UNROLL, MINB, false, true, 0, WF0>;
     e.fn[0][1][1] = force_kernel<T, IP, J, UNROLL, MINB, false, true, 1, WF0>;
     e.fn[0][1][2] = force_kernel<T, IP, J, UNROLL, MINB, false, true, 2, WF0>;
-    e.fn[1][0][0] = force_kernel<T, IP, J, UNROLL, MINB, true, false, 0, 0>;
-    e.fn[1][0][1] = force_kernel<T, IP, J, UNROLL, MINB, true, false, 1, 0>;
-    e.fn[1][0][2] = force_kernel<T, IP, J, UNROLL, MINB, true, false, 2, 0>;
+    e.fn[1][0][0] = force_kernel<T, IP, JP, UP, MINB, true, false, 0, 0>;
+    e.fn[1][0][1] = force_kernel<T, IP, JP, UP, MINB, true, false, 1, 0>;
+    e.fn[1][0][2] = force_kernel<T, IP, JP, UP, MINB, true, false, 2, 0>;
     e.fn[1][1][0] = force_kernel<T, IP, J, UNROLL, MINB, true, true, 0, 0>;
     e.fn[1][1][1] = force_kernel<T, IP, J, UNROLL, MINB, true, true, 1, 0>;
     e.fn[1][1][2] = force_kernel<T, IP, J, UNROLL, MINB, true, true, 2, 0>;
@@ -437,7 +442,7 @@ const ShapeEntry* shapes() {
     static const ShapeEntry table[] = {
         make_entry<256, 4, 256, 4, 0>(),  // 0: 2048-body blocks (fastest with the potential)
         make_entry<256, 2, 256, 4, 0>(),  // 1: 1024
-        make_entry<512, 2, 512, 4, 0, 1>(),  // 2: 2048 (fastest without the potential)
+        make_entry<512, 2, 1024, 2, 0, 1, 512, 4>(),  // 2: 2048 (fastest without the potential)
         make_entry<128, 2, 128, 2, 0>(),  // 3: 512
         make_entry<128, 1, 64, 2, 0>(),   // 4: 256 (small n)
 #ifdef NBODY_EXTRA_SHAPES
@@ -473,12 +478,13 @@ const ShapeEntry* shapes() {
         make_entry<128, 2, 256, 4, 0, 1>(),   // 34
         make_entry<256, 2, 512, 4, 0, 1>(),   // 35
         make_entry<512, 4, 256, 4, 0, 1>(),   // 36
+        make_entry<512, 2, 512, 4, 0, 1>(),   // 37 (shape 2 before 1024-body j-tiles)
 #endif
     };
     return table;
 }
 #ifdef NBODY_EXTRA_SHAPES
-constexpr int kNumShapes = 37;
+constexpr int kNumShapes = 38;
 #else
 constexpr int kNumShapes = 5;
 #endif
@@ -552,7 +558,7 @@ cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t ntile, int64_t nctas, i
 size_t force_partial_doubles_for(int k, bool pot, bool mixed, bool compensated, int64_t npad, int num_sms) {
     const ShapeEntry& e = shapes()[k];
     const int occ = std::min(occupancy(k, pot ? 1 : 0, mixed ? 1 : 0, compensated ? 1 : 0), e.cap);  // mode 0 or 1
-    const int64_t units = (npad / e.shape.block) * (npad / e.shape.jtile);
+    const int64_t units = (npad / e.shape.block) * (npad / e.jt[mixed ? 1 : 0]);
     const int64_t nctas = std::min<int64_t>((int64_t)num_sms * occ, units);
     return (size_t)nctas * 2u * (size_t)e.shape.block * 4u;
 }
@@ -572,7 +578,7 @@ cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st
     p.eps2 = a.eps2;
     p.n = a.n;
     p.nblk = (a.ipack != nullptr ? a.nipad : a.npad) / C;
-    p.ntile = a.npad / e.shape.jtile;
+    p.ntile = a.npad / e.jt[mixed];
     p.units = p.nblk * p.ntile;
     int occ = occupancy(k, pot, mixed, kahan);
     occ = std::min(occ, e.cap);
