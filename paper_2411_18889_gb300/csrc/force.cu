@@ -328,8 +328,8 @@ __device__ __forceinline__ void force_body(const KParams& p) {
                 } else {
                     const int64_t pi = (cta * 2 + slot) * C + lb;
                     if (!in_range(pi, p.nctas * 2 * C, p.err)) continue;
-                    double4* dst = reinterpret_cast<double4*>(p.partial) + pi;
-                    *dst = make_double4(d[h][0], d[h][1], d[h][2], d[h][3]);
+                    double4_16a* dst = reinterpret_cast<double4_16a*>(p.partial) + pi;
+                    *dst = make_double4_16a(d[h][0], d[h][1], d[h][2], d[h][3]);
                 }
             }
         }
@@ -385,7 +385,7 @@ __global__ void fixup_kernel(const KParams p, int C, int pot_on) {
             const int slot = c == c_lo ? slot_lo : 0;
             const int64_t pi = (c * 2 + slot) * C + lb;
             if (!in_range(pi, p.nctas * 2 * C, p.err)) continue;
-            const double4 v = reinterpret_cast<const double4*>(p.partial)[pi];
+            const double4_16a v = reinterpret_cast<const double4_16a*>(p.partial)[pi];
             sx += v.x;
             sy += v.y;
             sz += v.z;

@@ -271,8 +271,8 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
                 } else {
                     const int64_t pi = (cta * 2 + slot) * C + lb;
                     if (!in_range(pi, p.nctas * 2 * C, p.err)) continue;
-                    double4* dst = reinterpret_cast<double4*>(p.partial) + pi;
-                    *dst = make_double4(v[h][0], v[h][1], v[h][2], v[h][3]);
+                    double4_16a* dst = reinterpret_cast<double4_16a*>(p.partial) + pi;
+                    *dst = make_double4_16a(v[h][0], v[h][1], v[h][2], v[h][3]);
                 }
             }
         }
