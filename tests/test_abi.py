@@ -133,3 +133,21 @@ def test_tune_table_fault_injection(lib, tmp_path, monkeypatch):
     assert lib.nbody_tune_load(str(good).encode()) == 3
     assert lib.nbody_tuned_shape(0, 10, 0) == 3
     assert lib.nbody_tune_load(None) >= 0
+
+
+def test_tuner_rules_round_trip(lib, tmp_path):
+    """The survey's size ladder becomes rules that start each winner at the
+    midpoint below its size and merge repeats; written in the table format,
+    the library reads them back and answers with the same winners."""
+    from paper_2411_18889_gb300.tune import _rules
+    sizes = [1024, 4096, 16384, 32768, 65536]
+    winners = [4, 4, 3, 2, 2]
+    rules = _rules(sizes, winners)
+    assert rules == [(0, 4), (10240, 3), (24576, 2)]
+    f = tmp_path / "t.txt"
+    f.write_text("".join(f"force 0 {a} {k}\n" for a, k in rules) + "".join(f"batched {a} {min(k, 3)}\n" for a, k in rules))
+    assert lib.nbody_tune_load(str(f).encode()) == 2 * len(rules)
+    for n, k in zip(sizes, winners):
+        assert lib.nbody_tuned_shape(0, n, 0) == k
+        assert lib.nbody_tuned_shape(2, n, 0) == min(k, 3)
+    assert lib.nbody_tune_load(None) >= 0
