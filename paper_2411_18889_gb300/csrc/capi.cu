@@ -321,13 +321,14 @@ bool g_tune_loaded = false;
 void tune_defaults(std::vector<TuneRule>& r) {
     r.clear();
     r.push_back({0, 0, 0, 4});
-    r.push_back({0, 0, 24576, 2});
+    r.push_back({0, 0, 10240, 3});
+    r.push_back({0, 0, 49152, 2});
     r.push_back({0, 1, 0, 4});
-    r.push_back({0, 1, 10240, 3});
     r.push_back({0, 1, 24576, 1});
     r.push_back({0, 1, 49152, 0});
     r.push_back({1, 0, 0, 3});
-    r.push_back({1, 0, 2560, 1});
+    r.push_back({1, 0, 2560, 2});
+    r.push_back({1, 0, 10240, 1});
     r.push_back({1, 0, 24576, 0});
     r.push_back({2, 0, 0, 3});
     r.push_back({2, 0, 320, 2});
