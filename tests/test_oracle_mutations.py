@@ -2,8 +2,8 @@
 
 Each case copies oracle.c to a temporary directory, plants one mistake in the
 copy (on the CPU, never in the committed file), rebuilds it and runs the pin
-tests (forward, integrator and adjoint) against the mutant; every mutant must
-fail at least one pin.
+tests (forward, integrator, adjoint and the random-system properties) against
+the mutant; every mutant must fail at least one pin.
 """
 import os
 import shutil
@@ -47,10 +47,11 @@ def test_mutant_is_caught(tmp_path, name):
     shutil.copytree(os.path.join(ROOT, "nbody_inputs"), tmp_path / "nbody_inputs",
                     ignore=shutil.ignore_patterns("__pycache__"))
     os.makedirs(tmp_path / "tests")
-    for f in ("conftest.py", "test_oracle_pins.py", "test_oracle_integrator.py", "test_oracle_adjoint.py"):
+    for f in ("conftest.py", "test_oracle_pins.py", "test_oracle_integrator.py", "test_oracle_adjoint.py",
+              "test_oracle_properties.py"):
         shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                         "tests/test_oracle_pins.py", "tests/test_oracle_integrator.py",
-                        "tests/test_oracle_adjoint.py"],
+                        "tests/test_oracle_adjoint.py", "tests/test_oracle_properties.py"],
                        cwd=tmp_path, capture_output=True, text=True, timeout=300)
     assert r.returncode == 1, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
