@@ -151,3 +151,21 @@ def test_tuner_rules_round_trip(lib, tmp_path):
         assert lib.nbody_tuned_shape(0, n, 0) == k
         assert lib.nbody_tuned_shape(2, n, 0) == min(k, 3)
     assert lib.nbody_tune_load(None) >= 0
+
+
+def test_product_path_does_not_use_the_oracle():
+    """The package and its CUDA sources never import, load or name the oracle
+    (it is test infrastructure), and loading fails loudly without the built
+    library instead of falling back to anything."""
+    import glob
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_2411_18889_gb300")
+    files = glob.glob(os.path.join(pkg, "*.py")) + glob.glob(os.path.join(pkg, "csrc", "*"))
+    assert files
+    for f in files:
+        src = open(f, errors="replace").read()
+        assert not re.search(r"\boracle\b", src), f
+    from paper_2411_18889_gb300 import _lib
+    with pytest.raises(ImportError):
+        _lib.open_library(os.path.join(pkg, "no_such_libnbody.so"))
