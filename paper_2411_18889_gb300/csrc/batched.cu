@@ -30,10 +30,14 @@
 // an FP32 total (two-level summation), so a 4096-term sum carries the rounding
 // of two 64-term sums instead of one 4096-term running sum.
 //
-// Self term.  With eps > 0 the pair j = i adds exactly 0 to the acceleration
-// (its difference vector is exactly zero) and a known m_i/eps to the potential,
-// which is subtracted in the same FP32 arithmetic.  Systems with eps == 0 take
-// a masked loop that skips j = i.
+// Self term.  The pair j = i is excluded exactly, as Eq. 1 states, wherever
+// it would change a result: in the potential (it would add m_i/eps, and once
+// a partial sum holds that, every later add rounds at its ulp) and for
+// eps == 0 (where it is 0 * inf).  A warp's bodies of one pass slot are 32
+// consecutive bodies, so their self pairs all fall in one 64-pair block of the
+// j-loop; only that block runs the masked loop (the choice is warp-uniform).
+// Leapfrog evaluations with eps > 0 need no mask: the difference vector of the
+// self pair is exactly zero, so it adds exactly 0 to the acceleration.
 #include <algorithm>
 #include <mutex>
 
@@ -60,19 +64,62 @@ struct BParams {
     int* err;                // error word (checked builds record index faults)
 };
 
-// UNI: every body of the system has the mass mu; the pair loop then leaves
-// out the multiplication by m_j (11 instead of 12 FP32 operations per
-// interaction) and the sums are scaled by mu once per body.
+// One block of j-pairs [jb, je) against the thread's I i-bodies.  M: zero the
+// pair whose j equals the i-body (ib[k]).  UNI: every body of the system has
+// the mass mu; the pair weight then leaves out the multiplication by m_j (11
+// instead of 12 FP32 operations per interaction) and the sums are scaled by
+// mu once per body.
+template <int I, bool POT, bool M, bool UNI, int U>
+__device__ __forceinline__ void jblock(const ulonglong2* __restrict__ sp, int jb, int je, const f2 (&xi)[I],
+                                       const f2 (&yi)[I], const f2 (&zi)[I], const int (&ib)[I], f2 eps2,
+                                       f2 (&ax)[I], f2 (&ay)[I], f2 (&az)[I], f2 (&ap)[I]) {
+#pragma unroll U
+    for (int jp = jb; jp < je; ++jp) {
+        const ulonglong2 A = sp[2 * jp];
+        const ulonglong2 B = sp[2 * jp + 1];
+        const f2 xj = A.x, yj = A.y, zj = B.x, mj = B.y;
+#pragma unroll
+        for (int k = 0; k < I; ++k) {
+            const f2 dx = sub2(xj, xi[k]);
+            const f2 dy = sub2(yj, yi[k]);
+            const f2 dz = sub2(zj, zi[k]);
+            f2 r2 = fma2(dx, dx, eps2);
+            r2 = fma2(dy, dy, r2);
+            r2 = fma2(dz, dz, r2);
+            float s0, s1;
+            upk(r2, s0, s1);
+            float q0 = rsqrt_approx(s0);
+            float q1 = rsqrt_approx(s1);
+            if (M) {
+                if (2 * jp == ib[k]) q0 = 0.0f;
+                if (2 * jp + 1 == ib[k]) q1 = 0.0f;
+            }
+            const f2 ri = pk(q0, q1);
+            f2 w = mul2(ri, mul2(ri, ri));
+            if (!UNI) w = mul2(w, mj);
+            ax[k] = fma2(dx, w, ax[k]);
+            ay[k] = fma2(dy, w, ay[k]);
+            az[k] = fma2(dz, w, az[k]);
+            if (POT) ap[k] = fma2(r2, w, ap[k]);
+        }
+    }
+}
+
+// One pass: I i-bodies per thread (slot k of thread t is body base + k*T + t)
+// against every j-pair of the system.  MASK: exclude the self pair, in the
+// 64-pair block holding the warp's bodies of each slot.
 template <int T, int I, bool POT, bool MASK, bool UNI, int U, int JB>
 __device__ __forceinline__ void eval_pass(const float* __restrict__ sj, int npair, int ns, int base, f2 eps2,
-                                          const BParams& p, int64_t off, int64_t ev, float kick, bool drift,
-                                          float eps2s, float mu) {
+                                          const BParams& p, int64_t off, float kick, bool drift, float mu) {
+    static_assert(T % 32 == 0 && JB % 16 == 0, "a warp's 32 bodies of a slot lie in one j-block");
     const int tid = threadIdx.x;
     f2 xi[I], yi[I], zi[I];
     int ib[I];
+    int selfblk[I];  // first j-pair of the block holding this warp's bodies of slot k
 #pragma unroll
     for (int k = 0; k < I; ++k) {
         ib[k] = base + k * T + tid;
+        selfblk[k] = (((base + k * T + 32 * (tid >> 5)) >> 1) / JB) * JB;
         const int b = ib[k] < ns ? ib[k] : 0;  // threads past the end repeat body 0 and write nothing
         const float* s = sj + (b >> 1) * 8 + (b & 1);
         xi[k] = pk(s[0], s[0]);
@@ -88,36 +135,15 @@ __device__ __forceinline__ void eval_pass(const float* __restrict__ sj, int npai
         f2 ax[I], ay[I], az[I], ap[I];
 #pragma unroll
         for (int k = 0; k < I; ++k) ax[k] = ay[k] = az[k] = ap[k] = 0ull;
-#pragma unroll U
-        for (int jp = jb; jp < je; ++jp) {
-            const ulonglong2 A = sp[2 * jp];
-            const ulonglong2 B = sp[2 * jp + 1];
-            const f2 xj = A.x, yj = A.y, zj = B.x, mj = B.y;
+        bool own = false;
+        if (MASK) {
 #pragma unroll
-            for (int k = 0; k < I; ++k) {
-                const f2 dx = sub2(xj, xi[k]);
-                const f2 dy = sub2(yj, yi[k]);
-                const f2 dz = sub2(zj, zi[k]);
-                f2 r2 = fma2(dx, dx, eps2);
-                r2 = fma2(dy, dy, r2);
-                r2 = fma2(dz, dz, r2);
-                float s0, s1;
-                upk(r2, s0, s1);
-                float q0 = rsqrt_approx(s0);
-                float q1 = rsqrt_approx(s1);
-                if (MASK) {
-                    if (2 * jp == ib[k]) q0 = 0.0f;
-                    if (2 * jp + 1 == ib[k]) q1 = 0.0f;
-                }
-                const f2 ri = pk(q0, q1);
-                f2 w = mul2(ri, mul2(ri, ri));
-                if (!UNI) w = mul2(w, mj);
-                ax[k] = fma2(dx, w, ax[k]);
-                ay[k] = fma2(dy, w, ay[k]);
-                az[k] = fma2(dz, w, az[k]);
-                if (POT) ap[k] = fma2(r2, w, ap[k]);
-            }
+            for (int k = 0; k < I; ++k) own = own || selfblk[k] == jb;
         }
+        if (own)
+            jblock<I, POT, true, UNI, U>(sp, jb, je, xi, yi, zi, ib, eps2, ax, ay, az, ap);
+        else
+            jblock<I, POT, false, UNI, U>(sp, jb, je, xi, yi, zi, ib, eps2, ax, ay, az, ap);
 #pragma unroll
         for (int k = 0; k < I; ++k) {
             tx[k] = add2(tx[k], ax[k]);
@@ -150,17 +176,6 @@ __device__ __forceinline__ void eval_pass(const float* __restrict__ sj, int npai
             if (POT) {
                 upk(tp[k], a0, a1);
                 float s = a0 + a1;
-                if (!MASK) {  // remove the self pair's m_i/eps, computed as the loop did
-                    const int b = ib[k];
-                    const float mi = UNI ? 1.0f : sj[(b >> 1) * 8 + 6 + (b & 1)];
-                    const float r = rsqrt_approx(eps2s);
-                    float w;
-                    asm("mul.rn.ftz.f32 %0, %1, %2;" : "=f"(w) : "f"(r), "f"(r));
-                    asm("mul.rn.ftz.f32 %0, %1, %2;" : "=f"(w) : "f"(r), "f"(w));
-                    asm("mul.rn.ftz.f32 %0, %1, %2;" : "=f"(w) : "f"(w), "f"(mi));
-                    asm("mul.rn.ftz.f32 %0, %1, %2;" : "=f"(w) : "f"(eps2s), "f"(w));
-                    s -= w;
-                }
                 if (UNI) s *= mu;
                 p.pot[g] = -s;
             }
@@ -179,25 +194,21 @@ __device__ __forceinline__ void eval_pass(const float* __restrict__ sj, int npai
             }
         }
     }
-    (void)ev;
 }
 
 // eval_pass with I' = min(I, left) i-bodies per thread.
 template <int T, int I, bool POT, bool MASK, bool UNI, int U, int JB>
 __device__ __forceinline__ void pass_dispatch(int left, const float* __restrict__ sj, int npair, int ns, int base,
-                                              f2 eps2, const BParams& p, int64_t off, int64_t ev, float kick,
-                                              bool drift, float eps2s, float mu) {
+                                              f2 eps2, const BParams& p, int64_t off, float kick, bool drift,
+                                              float mu) {
     if (I >= 4 && left >= 4) {
-        eval_pass<T, (I >= 4 ? 4 : 1), POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, ev, kick, drift, eps2s,
-                                                       mu);
+        eval_pass<T, (I >= 4 ? 4 : 1), POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, kick, drift, mu);
     } else if (I >= 3 && left >= 3) {
-        eval_pass<T, (I >= 3 ? 3 : 1), POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, ev, kick, drift, eps2s,
-                                                       mu);
+        eval_pass<T, (I >= 3 ? 3 : 1), POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, kick, drift, mu);
     } else if (I >= 2 && left >= 2) {
-        eval_pass<T, (I >= 2 ? 2 : 1), POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, ev, kick, drift, eps2s,
-                                                       mu);
+        eval_pass<T, (I >= 2 ? 2 : 1), POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, kick, drift, mu);
     } else {
-        eval_pass<T, 1, POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, ev, kick, drift, eps2s, mu);
+        eval_pass<T, 1, POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, kick, drift, mu);
     }
 }
 
@@ -261,20 +272,20 @@ __global__ void __launch_bounds__(T) batched_kernel(const BParams p) {
                 const int lw = ns - base - 32 * (int)(threadIdx.x >> 5);
                 const int left = lw <= 0 ? 0 : (lw + T - 1) / T;
                 if (left == 0) {
-                } else if (eps2s == 0.0f) {
+                } else if (POT || eps2s == 0.0f) {  // the self pair must be excluded
                     if (uni)
-                        pass_dispatch<T, I, POT, true, true, U, JB>(left, sj, npair, ns, base, eps2, p, off, ev, kick,
-                                                             drift, eps2s, mu);
+                        pass_dispatch<T, I, POT, true, true, U, JB>(left, sj, npair, ns, base, eps2, p, off, kick,
+                                                                    drift, mu);
                     else
-                        pass_dispatch<T, I, POT, true, false, U, JB>(left, sj, npair, ns, base, eps2, p, off, ev, kick,
-                                                              drift, eps2s, mu);
+                        pass_dispatch<T, I, POT, true, false, U, JB>(left, sj, npair, ns, base, eps2, p, off, kick,
+                                                                     drift, mu);
                 } else {
                     if (uni)
-                        pass_dispatch<T, I, POT, false, true, U, JB>(left, sj, npair, ns, base, eps2, p, off, ev, kick,
-                                                              drift, eps2s, mu);
+                        pass_dispatch<T, I, POT, false, true, U, JB>(left, sj, npair, ns, base, eps2, p, off, kick,
+                                                                     drift, mu);
                     else
-                        pass_dispatch<T, I, POT, false, false, U, JB>(left, sj, npair, ns, base, eps2, p, off, ev, kick,
-                                                               drift, eps2s, mu);
+                        pass_dispatch<T, I, POT, false, false, U, JB>(left, sj, npair, ns, base, eps2, p, off, kick,
+                                                                      drift, mu);
                 }
             }
             __syncthreads();

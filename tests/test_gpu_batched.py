@@ -68,6 +68,30 @@ def test_accel_batched_matches_oracle(nb, oracle_mod, shape):
         assert rel(pot[a:b], rp).max() <= POT_MAX, (s, b - a)
 
 
+@pytest.mark.parametrize("shape", range(4))
+def test_accel_batched_small_softening(nb, oracle_mod, shape):
+    """Softenings far below the interparticle spacing (1e-6, 1e-5, 2^-12) beside
+    eps = 4/sqrt(n), every kernel shape.  The self pair would add m_i/eps to the
+    potential (3.3e3 for m = 1/300 at eps = 1e-6); Eq. 1 excludes it, and it must
+    be excluded exactly, not subtracted afterwards, or the rounding at the ulp of
+    m_i/eps alone breaks the 1e-5 potential tolerance."""
+    sizes, eps = [], []
+    for e in (1e-6, 1e-5, 2.0 ** -12, None):
+        for n in (300, 1000, 2049, 4096):
+            sizes.append(n)
+            eps.append(4.0 / np.sqrt(n) if e is None else e)
+    off, pos, vel, mass, _ = make_batch(sizes, 71 + shape)
+    eps = np.asarray(eps, dtype=np.float32).astype(np.float64)
+    acc, pot = gpu_accel_batched(nb, off, pos, mass, eps, config=shape)
+    assert nb.nbody_last_device_error() == 0
+    for s in range(len(sizes)):
+        a, b = off[s], off[s + 1]
+        ra, rp = oracle_mod.accel(pos[a:b], mass[a:b], eps[s])
+        e = rel(acc[a:b], ra)
+        assert np.median(e) <= ACC_MED and e.max() <= ACC_MAX, (shape, s, eps[s], np.median(e), e.max())
+        assert rel(pot[a:b], rp).max() <= POT_MAX, (shape, s, eps[s], rel(pot[a:b], rp).max())
+
+
 def test_accel_batched_zero_softening(nb, oracle_mod):
     off, pos, vel, mass, eps = make_batch([300, 1, 77, 1024], 21, eps_rule=0.0)
     acc, pot = gpu_accel_batched(nb, off, pos, mass, eps)
