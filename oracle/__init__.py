@@ -46,6 +46,9 @@ def _load():
         lib.oracle_accel_ij.argtypes = [i64, vp, i64, vp, vp, dbl, vp, vp]
         lib.oracle_accel_vjp.argtypes = [i64, vp, vp, dbl, vp, vp, vp, vp]
         lib.oracle_leapfrog_vjp.argtypes = [i64, vp, vp, vp, dbl, dbl, i64, vp, vp, vp, vp, vp]
+        flt = ctypes.c_float
+        lib.oracle_accel_listing_f32.argtypes = [i64, vp, vp, flt, vp, vp]
+        lib.oracle_accel_listing_f32_subset.argtypes = [i64, vp, vp, flt, i64, vp, vp, vp]
         _lib = lib
     return _lib
 
@@ -93,6 +96,31 @@ def accel_subset(pos, mass, eps, idx, with_pot: bool = True):
     acc = np.zeros((ns, 3))
     pot = np.zeros(ns) if with_pot else None
     _load().oracle_accel_subset(n, _p(pos), _p(mass), float(eps), ns, _p(idx), _p(acc), _p(pot))
+    return acc, pot
+
+
+def accel_listing_f32(pos, mass, eps, with_pot: bool = True, idx=None):
+    """Listing 4's FP32 arithmetic, every operation correctly rounded, one
+    running FP32 sum per body in j order, self pair skipped: (acc (n,3),
+    pot (n,) or None) as float32.  Positions, masses and eps are rounded to
+    FP32 first.  With ``idx``, only the listed bodies (each against all)."""
+    pos = _c(pos, dtype=np.float32)
+    n = pos.shape[0]
+    pos = _c(pos, dtype=np.float32, shape=(n, 3))
+    mass = _c(mass, dtype=np.float32, shape=(n,))
+    if idx is None:
+        acc = np.zeros((n, 3), np.float32)
+        pot = np.zeros(n, np.float32) if with_pot else None
+        _load().oracle_accel_listing_f32(n, _p(pos), _p(mass), float(np.float32(eps)), _p(acc), _p(pot))
+        return acc, pot
+    idx = _c(idx, dtype=np.int64)
+    if idx.size and (idx.min() < 0 or idx.max() >= n):
+        raise IndexError("subset index out of range")
+    ns = idx.shape[0]
+    acc = np.zeros((ns, 3), np.float32)
+    pot = np.zeros(ns, np.float32) if with_pot else None
+    _load().oracle_accel_listing_f32_subset(n, _p(pos), _p(mass), float(np.float32(eps)), ns, _p(idx), _p(acc),
+                                            _p(pot))
     return acc, pot
 
 

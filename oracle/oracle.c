@@ -282,3 +282,60 @@ void oracle_leapfrog_vjp(int64_t n, const double* pos0, const double* vel0, cons
     free(gxk);
     free(gmk);
 }
+
+/*
+ * Single-precision restatement of Listing 4 (Sec. III.A): a second, CPU
+ * reference that evaluates the listing's own FP32 arithmetic with every
+ * operation correctly rounded (IEEE binary32, no approximate reciprocal
+ * square root, no flush-to-zero), in the listing's order:
+ *   d = r_j - r_i                              three FP32 subtractions
+ *   r2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps^2)))   eps^2 = eps * eps in FP32
+ *   w = 1 / sqrt(r2)                           correctly rounded sqrt, then division
+ *   w = w * (w * w);  w = w * m_j
+ *   a += fma(d, w, a) per component, p = fma(r2, w, p)   one FP32 running sum in j order
+ * p accumulates m_j / r as the listing does; it is returned negated (the
+ * physical potential).  The sinks are the sources here, so the pair j == i is
+ * skipped (Eq. 1; the listing has no such test, which for eps > 0 changes
+ * only the potential, by +m_i/eps).  This is the error an exactly rounded
+ * FP32 evaluation of the listing has; the GPU kernels differ from it by the
+ * hardware reciprocal-square-root approximation and their summation order.
+ */
+static void body_sum_listing_f32(int64_t i, int64_t n, const float* pos, const float* mass, float eps2,
+                                 float* a3, float* phi) {
+    const float xi = pos[3 * i + 0], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
+    float ax = 0.0f, ay = 0.0f, az = 0.0f, p = 0.0f;
+    for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        const float dx = pos[3 * j + 0] - xi;
+        const float dy = pos[3 * j + 1] - yi;
+        const float dz = pos[3 * j + 2] - zi;
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+        float w = 1.0f / sqrtf(r2);
+        w = w * (w * w);
+        w = w * mass[j];
+        ax = fmaf(dx, w, ax);
+        ay = fmaf(dy, w, ay);
+        az = fmaf(dz, w, az);
+        p = fmaf(r2, w, p);
+    }
+    a3[0] = ax;
+    a3[1] = ay;
+    a3[2] = az;
+    if (phi) *phi = -p;
+}
+
+/* acc (n,3) and pot (n, may be NULL) in FP32 for all n bodies. */
+void oracle_accel_listing_f32(int64_t n, const float* pos, const float* mass, float eps, float* acc, float* pot) {
+    const float eps2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) body_sum_listing_f32(i, n, pos, mass, eps2, acc + 3 * i, pot ? pot + i : NULL);
+}
+
+/* The same for the ns bodies listed in idx, each against all n bodies. */
+void oracle_accel_listing_f32_subset(int64_t n, const float* pos, const float* mass, float eps, int64_t ns,
+                                     const int64_t* idx, float* acc, float* pot) {
+    const float eps2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t k = 0; k < ns; ++k)
+        body_sum_listing_f32(idx[k], n, pos, mass, eps2, acc + 3 * k, pot ? pot + k : NULL);
+}

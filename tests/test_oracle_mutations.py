@@ -2,7 +2,8 @@
 
 Each case copies oracle.c to a temporary directory, plants one mistake in the
 copy (on the CPU, never in the committed file), rebuilds it and runs the pin
-tests (forward, integrator, adjoint and the random-system properties) against
+tests (forward, integrator, adjoint, the random-system properties and the FP32
+listing restatement) against
 the mutant; every mutant must fail at least one pin.
 """
 import os
@@ -33,6 +34,10 @@ MUTANTS = {
     "adjoint_drift_uses_half_step": ("lv[k] += dt * gx0[k];", "lv[k] += h * gx0[k];"),
     "sink_source_pot_sign": ("p -= jmass[j] * rinv;", "p += jmass[j] * rinv;"),
     "sink_source_coordinate": ("jpos[3 * j + 2] - ipos[3 * i + 2]", "jpos[3 * j + 2] - ipos[3 * i + 1]"),
+    "listing_fma_chain_reordered": ("fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)))",
+                                    "fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)))"),
+    "listing_weight_not_cubed": ("        w = w * (w * w);", "        w = w * w;"),
+    "listing_rsqrt_rounded_once_in_fp64": ("float w = 1.0f / sqrtf(r2);", "float w = (float)(1.0 / sqrt((double)r2));"),
 }
 
 
@@ -48,10 +53,11 @@ def test_mutant_is_caught(tmp_path, name):
                     ignore=shutil.ignore_patterns("__pycache__"))
     os.makedirs(tmp_path / "tests")
     for f in ("conftest.py", "test_oracle_pins.py", "test_oracle_integrator.py", "test_oracle_adjoint.py",
-              "test_oracle_properties.py"):
+              "test_oracle_properties.py", "test_oracle_listing_f32.py"):
         shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                         "tests/test_oracle_pins.py", "tests/test_oracle_integrator.py",
-                        "tests/test_oracle_adjoint.py", "tests/test_oracle_properties.py"],
+                        "tests/test_oracle_adjoint.py", "tests/test_oracle_properties.py",
+                        "tests/test_oracle_listing_f32.py"],
                        cwd=tmp_path, capture_output=True, text=True, timeout=300)
     assert r.returncode == 1, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
