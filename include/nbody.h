@@ -274,9 +274,11 @@ NBODY_API const char* nbody_strerror(int code);
 NBODY_API int nbody_selftest_wait(double limit_seconds, const nbody_opts* opts);
 
 /*
- * nbody_accel_noalloc -- nbody_accel (mixed precision with cells in the
- * caller's order as NBODY_PREC_MIXED_UNSORTED, compensated sums, the potential
- * when pot != NULL) for callers that cannot allocate GPU memory.
+ * nbody_accel_noalloc -- nbody_accel with its default options (mixed
+ * precision on cells of bodies in Morton order, compensated sums) and kernel
+ * shape 1 (opts->config = 1), the potential when pot != NULL, for callers that
+ * cannot allocate GPU memory.  Its results are bit-identical to that
+ * nbody_accel call's.
  * The paper has no counterpart; this is a deployment variant of the same
  * force evaluation.
  *
@@ -288,8 +290,8 @@ NBODY_API int nbody_selftest_wait(double limit_seconds, const nbody_opts* opts);
  * anything (no cudaMalloc, cudaFree or allocating library routine).
  *
  * Its scratch is one fixed array in the library's device module,
- * 22 MiB + 4.25 KiB, which every GPU that loads the library holds until the
- * process exits.  Limits: n <= NBODY_NOALLOC_MAX_N (65536); larger n returns
+ * 24,449,280 bytes (23.3 MiB), which every GPU that loads the library holds
+ * until the process exits.  Limits: n <= NBODY_NOALLOC_MAX_N (65536); larger n returns
  * NBODY_EINVAL without queuing work.  If the device needs more partial-sum
  * scratch than the array holds (a GPU with more SMs than it was sized for),
  * the call returns NBODY_ENOMEM.

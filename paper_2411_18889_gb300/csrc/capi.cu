@@ -8,7 +8,6 @@
 #include <string.h>
 
 #include <dlfcn.h>
-#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -49,15 +48,6 @@ bool fault(const char* what) {
     return f != nullptr && strcmp(f, what) == 0;
 }
 
-// An NVTX range around each public call, so that a timeline tool shows the
-// library's calls by name around their kernels (a no-op without a tool).
-struct NvtxRange {
-    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
-    ~NvtxRange() { nvtxRangePop(); }
-    NvtxRange(const NvtxRange&) = delete;
-    NvtxRange& operator=(const NvtxRange&) = delete;
-};
-#define NB_RANGE(name) NvtxRange nb_range_(name)
 
 // ---------------------------------------------------------------------------
 // Launch accounting and optional force-kernel timing (for benchmarks).

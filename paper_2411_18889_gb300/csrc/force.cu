@@ -37,6 +37,7 @@
 // a masked variant that zeroes the pair whose j equals i, so j = i is excluded
 // exactly (Eq. 1) and eps = 0 is valid for distinct positions.
 #include <algorithm>
+#include <map>
 #include <mutex>
 
 #include "nbody_internal.cuh"
@@ -489,21 +490,26 @@ constexpr int kNumShapes = 38;
 constexpr int kNumShapes = 5;
 #endif
 
-// Resident CTAs per SM for each kernel variant, queried once.
-std::mutex g_occ_mu;
-int g_occ[kNumShapes][2][2][3];
-bool g_occ_init = false;
-
-int occupancy(int k, int pot, int mixed, int kahan) {
-    std::lock_guard<std::mutex> lk(g_occ_mu);
-    if (!g_occ_init) {
+// Resident CTAs per SM for each kernel variant, queried once per device (the
+// dynamic shared-memory limit each variant needs is a per-device attribute,
+// set on the device that is current at the first launch there).
+struct OccTable {
+    int v[kNumShapes][2][2][3];
+    OccTable() {
         for (int a = 0; a < kNumShapes; ++a)
             for (int b = 0; b < 2; ++b)
                 for (int c = 0; c < 2; ++c)
-                    for (int d = 0; d < 3; ++d) g_occ[a][b][c][d] = -1;
-        g_occ_init = true;
+                    for (int d = 0; d < 3; ++d) v[a][b][c][d] = -1;
     }
-    int& o = g_occ[k][pot][mixed][kahan];
+};
+std::mutex g_occ_mu;
+std::map<int, OccTable> g_occ;
+
+int occupancy(int k, int pot, int mixed, int kahan) {
+    int dev = 0;
+    (void)cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    int& o = g_occ[dev].v[k][pot][mixed][kahan];
     if (o < 0) {
         const ShapeEntry& e = shapes()[k];
         const size_t sm = e.smem(mixed);

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/nbody.h"
@@ -166,6 +167,25 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     }
 }
 
+// An NVTX range around each public call, so that a timeline tool shows the
+// library's calls by name around their kernels (a no-op without a tool).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define NB_RANGE(name) ::nbk::NvtxRange nb_range_(name)
+
+// SM count of the current device (grid caps of the grid-stride O(n) kernels);
+// 1 if it cannot be read, which only narrows those grids.
+inline int current_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 1;
+    return sms;
+}
+
 // ---------------------------------------------------------------------------
 // Host-side launch interfaces (implemented in force.cu / pack.cu / reduce.cu).
 // ---------------------------------------------------------------------------
@@ -314,6 +334,12 @@ cudaError_t vjp_launch(int k, const VjpArgs& a, int num_sms, cudaStream_t st, in
 // index within equal keys).  `scratch` holds order_scratch_bytes(n) bytes.
 size_t order_scratch_bytes(int64_t n);
 cudaError_t spatial_order(int64_t n, const double* pos, int* perm, void* scratch, cudaStream_t st);
+// One stable pass of the same radix sort: (key_out, val_out) = (key_in, val_in)
+// ordered by the 8-bit digit (key >> shift) & 255, ties in index order.
+// `hist` holds sort_pass_hist_ints(n) ints.  Three kernels on st.
+size_t sort_pass_hist_ints(int64_t n);
+cudaError_t sort_pass(int64_t n, const unsigned* key_in, const int* val_in, int shift, unsigned* key_out,
+                      int* val_out, int* hist, cudaStream_t st);
 
 // One CTA waits on an mbarrier nothing completes, for limit_ns, then sets *err.
 cudaError_t selftest_wait(uint64_t limit_ns, int* err, cudaStream_t st);

@@ -1,6 +1,8 @@
-// noalloc.cu -- nbody_accel_noalloc: the mixed-precision force evaluation of
-// nbody_accel with every scratch buffer in one fixed device array, for callers
-// that must not allocate GPU memory.
+// noalloc.cu -- nbody_accel_noalloc: the force evaluation of nbody_accel with
+// its default options (mixed precision, cells of bodies in Morton order,
+// compensated sums) on the 1024-body-block kernel shape, with every scratch
+// buffer in one fixed device array, for callers that must not allocate GPU
+// memory.
 //
 // Who needs it: code that runs where cudaMalloc is off limits -- inside a
 // framework's memory pool or allocator callback (allocating there can
@@ -11,7 +13,7 @@
 // never does.
 //
 // The scratch is `g_scratch` below, a file-scope __device__ array of
-// kScratchBytes (22 MiB + 4.25 KiB).  Every GPU on which the library's module
+// kScratchBytes (23.3 MiB).  Every GPU on which the library's module
 // is loaded holds its own copy until the process exits.  In host code the name
 // g_scratch is only a host-side stand-in for the symbol, not a device address:
 // the set-up looks up the real address once per device with
@@ -31,10 +33,18 @@ constexpr int kShape = 1;                           // 1024-body i-blocks, 256-b
 constexpr int kBlock = 1024;
 constexpr size_t kJdupBytes = (size_t)kMaxN * nbk::kJdupFloats * sizeof(float);  // 2 MiB
 constexpr size_t kCentreBytes = 4096;               // >= (kMaxN / kBlock) cells x 3 doubles
-constexpr size_t kStatusBytes = 256;                // timeout word when the caller passes none
+constexpr size_t kWordBytes = 256;                  // error word (when the caller passes none), equal-mass flag
+constexpr size_t kPermBytes = (size_t)kMaxN * sizeof(int);                       // Morton permutation
+constexpr size_t kOrderBytes = (size_t)kMaxN * 16 + ((size_t)64 << 10);         // radix-sort scratch
 constexpr size_t kPartialBytes = (size_t)20 << 20;  // split i-block partial sums
-constexpr size_t kScratchBytes = kJdupBytes + kCentreBytes + kStatusBytes + kPartialBytes;
+constexpr size_t kOffCentres = kJdupBytes;
+constexpr size_t kOffWords = kOffCentres + kCentreBytes;
+constexpr size_t kOffPerm = kOffWords + kWordBytes;
+constexpr size_t kOffOrder = kOffPerm + kPermBytes;
+constexpr size_t kOffPartial = kOffOrder + kOrderBytes;
+constexpr size_t kScratchBytes = kOffPartial + kPartialBytes;
 static_assert((kMaxN / kBlock) * 3 * sizeof(double) <= kCentreBytes, "centre area too small");
+static_assert(kOffPerm % 256 == 0 && kOffOrder % 256 == 0 && kOffPartial % 256 == 0, "areas stay 256-byte aligned");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -94,6 +104,7 @@ bool device_ptr(const void* p) {
 
 extern "C" int nbody_accel_noalloc(int64_t n, const double* pos, const float* mass, double eps, float* acc,
                                    float* pot, int* status, void* stream) {
+    NB_RANGE("nbody_accel_noalloc");
     if (n < 0 || n > kMaxN || !isfinite(eps) || eps < 0.0) return NBODY_EINVAL;
     if (n > 0 && (pos == nullptr || mass == nullptr || acc == nullptr)) return NBODY_EINVAL;
     if (n == 0) return NBODY_OK;
@@ -112,24 +123,29 @@ extern "C" int nbody_accel_noalloc(int64_t n, const double* pos, const float* ma
     const int64_t npad = (n + kBlock - 1) / kBlock * kBlock;
     const size_t need = nbk::force_partial_doubles_for(kShape, pot != nullptr, true, true, npad, d->num_sms) *
                         sizeof(double);
-    if (need > kPartialBytes) return NBODY_ENOMEM;  // a device with more SMs than the array was sized for
+    // a device with more SMs than the partial-sum area was sized for
+    if (need > kPartialBytes || nbk::order_scratch_bytes(n) > kOrderBytes) return NBODY_ENOMEM;
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned char* base = d->base;
     float* jdup = reinterpret_cast<float*>(base);
-    double* centres = reinterpret_cast<double*>(base + kJdupBytes);
-    int* word = status ? status : reinterpret_cast<int*>(base + kJdupBytes + kCentreBytes);
-    double* partial = reinterpret_cast<double*>(base + kJdupBytes + kCentreBytes + kStatusBytes);
+    double* centres = reinterpret_cast<double*>(base + kOffCentres);
+    int* word = status ? status : reinterpret_cast<int*>(base + kOffWords);
+    int* uni = reinterpret_cast<int*>(base + kOffWords + 128);
+    int* perm = reinterpret_cast<int*>(base + kOffPerm);
+    void* order_scratch = base + kOffOrder;
+    double* partial = reinterpret_cast<double*>(base + kOffPartial);
 
-    // Only the timeout word must start at zero: the pack kernel writes every
-    // j-array entry and centre, and each partial slot is written before the
-    // fixup reads it.
-    if (cudaMemsetAsync(word, 0, sizeof(int), st) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return NBODY_ECUDA;
-    }
-    if (nbk::pack_f64(n, npad, kBlock, const_cast<double*>(pos), nullptr, nullptr, mass, 0.0, 0.0, false, jdup,
-                      centres, st) != cudaSuccess) {
+    // The same sequence nbody_accel queues for these options.  Only the error
+    // word must start at zero: the sort, the equal-mass check and the pack
+    // kernel write everything they later read, and each partial slot is
+    // written before the fixup reads it.
+    bool ok = cudaMemsetAsync(word, 0, sizeof(int), st) == cudaSuccess;
+    ok = ok && nbk::spatial_order(n, pos, perm, order_scratch, st) == cudaSuccess;
+    ok = ok && nbk::uniform_mass_flag(n, mass, uni, st) == cudaSuccess;
+    ok = ok && nbk::pack_f64(n, npad, kBlock, const_cast<double*>(pos), nullptr, nullptr, mass, 0.0, 0.0, false,
+                             jdup, centres, st, perm, word) == cudaSuccess;
+    if (!ok) {
         (void)cudaGetLastError();
         return NBODY_ECUDA;
     }
@@ -139,11 +155,13 @@ extern "C" int nbody_accel_noalloc(int64_t n, const double* pos, const float* ma
     a.eps2 = (float)(eps * eps);
     a.n = n;
     a.npad = npad;
+    a.perm = perm;
     a.acc = acc;
     a.pot = pot;
     a.partial = partial;
     a.err = word;
     a.summation = 1;
+    a.uni = uni;
     int launched = 0;
     if (nbk::force_launch(kShape, a, d->num_sms, st, &launched) != cudaSuccess) {
         (void)cudaGetLastError();

@@ -167,7 +167,8 @@ __global__ void __launch_bounds__(kTileThreads) scatter_kernel(int64_t n, const 
 
 unsigned grid_for(int64_t work) {
     int64_t g = (work + 255) / 256;
-    if (g > 152 * 16) g = 152 * 16;
+    const int64_t cap = (int64_t)current_sms() * 16;
+    if (g > cap) g = cap;
     return (unsigned)(g < 1 ? 1 : g);
 }
 
@@ -201,6 +202,18 @@ cudaError_t spatial_order(int64_t n, const double* pos, int* perm, void* scratch
         scan_kernel<<<1, 1024, 0, st>>>(hist, ntile * kRadix);
         scatter_kernel<<<ntile, kTileThreads, 0, st>>>(n, kin, vin, shift, ntile, hist, kout, vout);
     }
+    return cudaGetLastError();
+}
+
+size_t sort_pass_hist_ints(int64_t n) { return (size_t)((n + kTile - 1) / kTile) * kRadix; }
+
+cudaError_t sort_pass(int64_t n, const unsigned* key_in, const int* val_in, int shift, unsigned* key_out,
+                      int* val_out, int* hist, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int ntile = (int)((n + kTile - 1) / kTile);
+    hist_kernel<<<ntile, kTileThreads, 0, st>>>(n, key_in, shift, ntile, hist);
+    scan_kernel<<<1, 1024, 0, st>>>(hist, ntile * kRadix);
+    scatter_kernel<<<ntile, kTileThreads, 0, st>>>(n, key_in, val_in, shift, ntile, hist, key_out, val_out);
     return cudaGetLastError();
 }
 

@@ -164,7 +164,8 @@ namespace {
 
 unsigned grid_for(int64_t work, int threads) {
     int64_t g = (work + threads - 1) / threads;
-    if (g > 152 * 32) g = 152 * 32;
+    const int64_t cap = (int64_t)current_sms() * 32;
+    if (g > cap) g = cap;
     if (g < 1) g = 1;
     return (unsigned)g;
 }
@@ -189,7 +190,9 @@ cudaError_t pack_f32(int64_t n, int64_t npad, float* pos, float* vel, const floa
 cudaError_t uniform_mass_flag(int64_t n, const float* mass, int* flag, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(flag, 1, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    uniform_mass_kernel<<<grid_for(n, 256) < 152 * 4 ? grid_for(n, 256) : 152 * 4, 256, 0, st>>>(n, mass, flag);
+    const unsigned cap = (unsigned)current_sms() * 4u;
+    const unsigned g = grid_for(n, 256);
+    uniform_mass_kernel<<<g < cap ? g : cap, 256, 0, st>>>(n, mass, flag);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@
 // tiles for j = k, FP64 cell centres for mixed precision, and per-tile FP32
 // partials folded into FP32 totals (two-level summation).
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <type_traits>
 
@@ -416,19 +417,24 @@ const VShapeEntry* vshapes() {
 }
 constexpr int kNumVShapes = 4;
 
-std::mutex g_vocc_mu;
-int g_vocc[kNumVShapes][2][2];
-bool g_vocc_init = false;
-
-int vocc(int k, int mu, int mixed) {
-    std::lock_guard<std::mutex> lk(g_vocc_mu);
-    if (!g_vocc_init) {
+// Resident CTAs per SM for each variant, queried once per device (the
+// shared-memory attribute is set per device).
+struct VOccTable {
+    int v[kNumVShapes][2][2];
+    VOccTable() {
         for (int a = 0; a < kNumVShapes; ++a)
             for (int b = 0; b < 2; ++b)
-                for (int c = 0; c < 2; ++c) g_vocc[a][b][c] = -1;
-        g_vocc_init = true;
+                for (int c = 0; c < 2; ++c) v[a][b][c] = -1;
     }
-    int& o = g_vocc[k][mu][mixed];
+};
+std::mutex g_vocc_mu;
+std::map<int, VOccTable> g_vocc;
+
+int vocc(int k, int mu, int mixed) {
+    int dev = 0;
+    (void)cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_vocc_mu);
+    int& o = g_vocc[dev].v[k][mu][mixed];
     if (o < 0) {
         const VShapeEntry& e = vshapes()[k];
         const size_t sm = e.smem(mixed);
@@ -471,7 +477,8 @@ cudaError_t pack_vjp(int64_t n, int64_t npad, int block, const double* pos, cons
 cudaError_t adjoint_accumulate(int64_t n, double* lamx, const float* g, double* gm_acc, const float* gm,
                                cudaStream_t st) {
     int64_t grid = (3 * n + 255) / 256;
-    if (grid > 152 * 16) grid = 152 * 16;
+    const int64_t cap = (int64_t)current_sms() * 16;
+    if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
     adjoint_accumulate_kernel<<<(unsigned)grid, 256, 0, st>>>(n, lamx, g, gm_acc, gm);
     return cudaGetLastError();

@@ -2,15 +2,14 @@
 GPU memory (allocator callbacks, real-time loops, fully pre-reserved
 processes), with all scratch in the library's fixed device array.
 
-Called through the C ABI (ctypes) on device arrays and compared with
-nbody_accel's output on two calls in a row, within the parity tolerances of
-the other GPU tests.  nbody_accel runs with the same kernel shape (1024-body
-i-blocks) and cell order (the caller's) as the static-scratch variant: bodies with a neighbour far inside
-the softening length carry FP32 coordinate-rounding errors of up to ~2e-4
-relative in every shape, and two shapes that round differently would compare
-those errors with each other rather than the two entry points.  The file
-sorts last so that a run stopping at the first failure has already run every
-other test.
+Called through the C ABI (ctypes) on device arrays, on two calls in a row:
+its output must equal, bit for bit, that of the allocating entry point
+nbody_accel with the same options (default precision and summation, kernel
+shape 1) -- both queue the same kernels, so any difference would be a wrong
+layout of the fixed scratch -- and it is checked against the FP64 oracle
+(Eq. 1) within the parity tolerances of the other GPU tests.  The file sorts
+last so that a run stopping at the first failure has already run every other
+test.
 """
 import ctypes
 
@@ -38,21 +37,26 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
-@pytest.mark.parametrize("n,with_pot", [(MAX_N, True), (5000, False), (1, True)])
-def test_noalloc_matches_accel_twice(nb, n, with_pot):
+@pytest.mark.parametrize("n,with_pot,masses", [(MAX_N, True, "loguniform"), (5000, False, "equal"),
+                                                (4099, True, "equal"), (1, True, "equal")])
+def test_noalloc_matches_accel_and_oracle_twice(nb, oracle_mod, n, with_pot, masses):
     import torch
     lib = nb.load()
-    p, _, m = ni.plummer(n, 4242 + n, masses="loguniform", offset=(1e4, -3e3, 7e2))
+    p, _, m = ni.plummer(n, 4242 + n, masses=masses, offset=(1e4, -3e3, 7e2))
+    m = m.astype(np.float32).astype(np.float64)
     P = torch.from_numpy(p).cuda()
     M = torch.from_numpy(m.astype(np.float32)).cuda()
     eps = 2.0 ** -9
-    # reference: the allocating entry point
+    # the allocating entry point with the same options
     acc_ref = torch.empty((n, 3), dtype=torch.float32, device="cuda")
     pot_ref = torch.empty((n,), dtype=torch.float32, device="cuda") if with_pot else None
-    nb.nbody_accel(P, M, eps, acc_ref, pot_ref, config=NOALLOC_SHAPE, precision=nb.NBODY_PREC_MIXED_UNSORTED)
+    nb.nbody_accel(P, M, eps, acc_ref, pot_ref, config=NOALLOC_SHAPE)
     torch.cuda.synchronize()
     acc_ref = acc_ref.cpu().numpy()
     pot_ref = pot_ref.cpu().numpy() if with_pot else None
+    # the FP64 oracle on a seeded subsample (every body for small n)
+    idx = np.arange(n) if n <= 8192 else ni.subsample(n, 2048, 77)
+    ra, rp = oracle_mod.accel_subset(p, m, eps, idx)
 
     acc = torch.empty((n, 3), dtype=torch.float32, device="cuda")
     pot = torch.empty((n,), dtype=torch.float32, device="cuda") if with_pot else None
@@ -68,15 +72,17 @@ def test_noalloc_matches_accel_twice(nb, n, with_pot):
         torch.cuda.synchronize()
         assert int(status.item()) == 0
         a = acc.cpu().numpy()
-        assert np.all(np.isfinite(a))
+        assert np.array_equal(a, acc_ref), (call, np.abs(a - acc_ref).max())
+        if with_pot:
+            assert np.array_equal(pot.cpu().numpy(), pot_ref), call
         if n == 1:
-            assert np.all(a == 0) and np.all(acc_ref == 0)
+            assert np.all(a == 0)
             assert float(pot.cpu()[0]) == 0.0
             continue
-        e = _rel(a, acc_ref)
+        e = _rel(a[idx], ra)
         assert np.median(e) <= ACC_MED and e.max() <= ACC_MAX, (call, np.median(e), e.max())
         if with_pot:
-            ep = _rel(pot.cpu().numpy(), pot_ref)
+            ep = _rel(pot.cpu().numpy()[idx], rp)
             assert ep.max() <= POT_MAX, (call, ep.max())
 
 
