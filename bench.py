@@ -20,9 +20,17 @@ Legs (one JSON line on rank 0):
   cpu_baseline the FP64 oracle on the host cores, on a bounded subsample.
   accuracy    that subsample's FP64 sums against the library's force on the
               initial state (mixed and plain): median and max relative error.
+  with_potential  one nbody_accel call with the potential at N = 2^20.
+  integrator  the pack (kick + drift + packed j-array) and closing-kick
+              kernels of the timed steps: achieved GB/s against the measured
+              copy bandwidth.
   batched, throughput_plain, adjoint
               the ragged ensemble (4096 systems, 64 steps), the N = 65536 FP32
               run of 128 steps, and the adjoint of 64 steps at N = 16384.
+  oracle_check (inside each leg) that leg's results against the FP64 oracle,
+              computed in the CPU leg.
+  cpu_baseline_listing_f32  the oracle's FP32 restatement of Listing 4 on the
+              host cores: the paper's own single-precision arithmetic.
 ``--impl reference`` times the oracle alone (the reference arm of this
 comparison) and prints its own line.  Under torchrun each rank runs an
 independent replica (the force does not shard without a position exchange
@@ -215,7 +223,7 @@ def profile_case(n: int, kind: str = "force") -> int:
         acc = torch.empty((n, 3), dtype=torch.float64, device="cuda")
         gv0 = torch.empty_like(acc)
         gm = torch.empty((n,), dtype=torch.float64, device="cuda")
-        nb.nbody_leapfrog_vjp(M, w.eps, w.dt, K, ck, tape, gxT, torch.zeros_like(acc), acc, gv0, gm)
+        nb.nbody_leapfrog_vjp_tape(M, w.eps, w.dt, K, ck, tape, gxT, torch.zeros_like(acc), acc, gv0, gm)
     elif kind == "batched":
         off, pos, _, mass, eps = ni.ragged_batch(nsys=n)
         O = torch.from_numpy(off).cuda()
@@ -287,12 +295,20 @@ def batched_leg(nb, dev, sms, peak_int_s, args):
     torch.cuda.synchronize()
     t_s = time.perf_counter() - t0
     value = inter / t_b / 1e9
+    # the state after one timed call (64 steps from the initial state), kept for the oracle check
+    P.copy_(P0)
+    V.copy_(V0)
+    nb.nbody_leapfrog_batched(O, P, V, M, E, dt, steps)
+    torch.cuda.synchronize()
+    check = {"off": off, "pos": pos, "vel": vel, "mass": mass, "eps": eps, "dt": dt, "steps": steps,
+             "pos_gpu": P.cpu().numpy().astype(np.float64), "vel_gpu": V.cpu().numpy().astype(np.float64)}
     return {"workload": "ragged_4096_systems_n64_4096_loguniform_eps4_over_sqrtn_kdk64_dt2^-8",
             "value": value, "unit": UNIT, "pct_fp32_peak": value * 1e9 / peak_int_s * 100,
             "ms_per_call": t_b * 1e3, "interactions_per_call": inter,
             "per_system_calls_value": inter / t_s / 1e9, "per_system_calls_ms": t_s * 1e3,
-            "speedup_vs_per_system_calls": t_s / t_b, "launches_per_call": 1,
-            "per_system_launches": int(len(sizes) * (3 * (steps + 1) + 1))}
+            "speedup_vs_per_system_calls": t_s / t_b, "launches_per_call": 6,
+            "launches_note": "4 planning kernels (keys, one radix pass of 3 kernels) and the persistent kernel",
+            "per_system_launches": int(len(sizes) * (3 * (steps + 1) + 1))}, check
 
 
 def throughput_leg(nb, dev, peak_int_s, args):
@@ -324,15 +340,21 @@ def throughput_leg(nb, dev, peak_int_s, args):
     e1 = nb.nbody_energy_f32(P, V, M, np.float32(w.eps))["E"]
     t = statistics.median(ts)
     value = (steps + 1) * n * n / t / 1e9
+    # the first 4 steps alone, for the energy against the oracle's own 4-step run
+    P.copy_(P0)
+    V.copy_(V0)
+    nb.nbody_leapfrog_f32(P, V, M, np.float32(w.eps), np.float32(w.dt), 4)
+    torch.cuda.synchronize()
+    check = {"w": w, "pos4": P.cpu().numpy().astype(np.float64), "vel4": V.cpu().numpy().astype(np.float64)}
     return {"workload": "plummer_n65536_equal_mass_fp32_eps2^-8_kdk128_dt2^-8", "value": value, "unit": UNIT,
             "pct_fp32_peak": value * 1e9 / peak_int_s * 100, "ms_per_call": t * 1e3,
-            "energy_drift_128_steps": abs(e1 - e0) / abs(e0)}
+            "energy_drift_128_steps": abs(e1 - e0) / abs(e0)}, check
 
 
 def adjoint_leg(nb, dev, args):
     """Adjoint workload: N = 16384 Plummer, eps = 2^-7, dt = 2^-8, K = 64 KDK
     steps, checkpoints every 8 steps.  Forward = nbody_leapfrog_record (the run
-    that produces x(T) and the tape); gradient = nbody_leapfrog_vjp (replay of
+    that produces x(T) and the tape); gradient = nbody_leapfrog_vjp_tape (replay of
     each segment from its checkpoint + one force VJP per force evaluation)."""
     import torch
     import nbody_inputs as ni
@@ -358,7 +380,7 @@ def adjoint_leg(nb, dev, args):
         torch.cuda.synchronize()
         e1b = torch.cuda.Event(enable_timing=True)
         e1b.record()
-        nb.nbody_leapfrog_vjp(M, w.eps, w.dt, K, ckpt, tape, gxT, zero, gx0, gv0, gm)
+        nb.nbody_leapfrog_vjp_tape(M, w.eps, w.dt, K, ckpt, tape, gxT, zero, gx0, gv0, gm)
         e2.record()
         torch.cuda.synchronize()
         if it > 0:
@@ -366,11 +388,175 @@ def adjoint_leg(nb, dev, args):
             bw.append(e1b.elapsed_time(e2) / 1e3)
     f, g = statistics.median(fw), statistics.median(bw)
     inter = (K + 1) * n * n
+    xT = P.cpu().numpy()
+    check = {"w": w, "xT": xT, "gx": gx0.cpu().numpy(), "gv": gv0.cpu().numpy(),
+             "gm": gm.cpu().numpy() + ((xT - w.extra["target"]) ** 2).sum(axis=1)}
+    # a smaller case of the same recipe for the oracle's FP64 adjoint (n = 2048)
+    ws_ = ni.adjoint_case(n=2048, seed=15, target_seed=16)
+    Ms = torch.from_numpy(ws_.mass.astype(np.float32)).to(dev)
+    Ps, Vs = torch.from_numpy(ws_.pos).to(dev), torch.from_numpy(ws_.vel).to(dev)
+    tp = torch.empty(nb.nbody_tape_bytes(2048, K, ckpt), dtype=torch.uint8, device=dev)
+    nb.nbody_leapfrog_record(Ps, Vs, Ms, ws_.eps, ws_.dt, K, ckpt, tp)
+    ys = torch.from_numpy(ws_.extra["target"]).to(dev)
+    gxs, gvs = torch.empty((2048, 3), dtype=torch.float64, device=dev), torch.empty((2048, 3), dtype=torch.float64, device=dev)
+    gms = torch.empty((2048,), dtype=torch.float64, device=dev)
+    nb.nbody_leapfrog_vjp_tape(Ms, ws_.eps, ws_.dt, K, ckpt, tp, 2.0 * Ms.double()[:, None] * (Ps - ys),
+                               torch.zeros_like(gxs), gxs, gvs, gms)
+    torch.cuda.synchronize()
+    check["small"] = {"w": ws_, "gx": gxs.cpu().numpy(), "gv": gvs.cpu().numpy(), "gm": gms.cpu().numpy()}
     return {"workload": "plummer_n16384_eps2^-7_kdk64_dt2^-8_ckpt8_loss_sum_m_x_minus_y_sq",
             "forward_ms": f * 1e3, "gradient_ms": g * 1e3, "adjoint_to_forward": g / f,
-            "forward_gints": inter / f / 1e9,
+            "forward_gints": inter / f / 1e9, "forward_pct_fp32_peak": None,
             "note": "gradient = replay of 48 force evaluations from 8 checkpoints (on a second stream, two "
-                    "segments ahead) + 65 force VJPs"}
+                    "segments ahead) + 65 force VJPs"}, check
+
+
+def with_potential_leg(nb, dev, P0, M, w, peak_int_s, reps):
+    """nbody_accel with the potential (Eq. 1 and Listing 4's CALCULATE_POTENTIAL
+    term) at N = 2^20 on the precision workload's initial state: one force
+    evaluation per call, CUDA events around the force kernel."""
+    import torch
+    n = w.n
+    acc = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    pot = torch.empty((n,), dtype=torch.float32, device=dev)
+    nb.nbody_accel(P0, M, w.eps, acc, pot)  # warm-up
+    torch.cuda.synchronize()
+    nb.nbody_profile_read()
+    nb.nbody_profile_enable(True)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        nb.nbody_accel(P0, M, w.eps, acc, pot)
+    b.record()
+    torch.cuda.synchronize()
+    nb.nbody_profile_enable(False)
+    kms, kl, _ = nb.nbody_profile_read()
+    call = a.elapsed_time(b) / 1e3 / reps
+    kern = kms / 1e3 / max(kl, 1)
+    value = n * n / call / 1e9
+    check = {"acc": acc.cpu().numpy().astype(np.float64), "pot": pot.cpu().numpy().astype(np.float64)}
+    return {"workload": "plummer_n1048576_offset1e4_loguniform_mass_eps2^-9_accel_and_potential",
+            "value": value, "unit": UNIT, "pct_fp32_peak": value * 1e9 / peak_int_s * 100,
+            "ms_per_call": call * 1e3, "force_kernel_ms": kern * 1e3,
+            "force_kernel_pct_fp32_peak": n * n / kern / peak_int_s * 100,
+            "kernel_ceiling_pct": 100.0 * 10.0 / 13.0,
+            "ceiling_basis": "13 FP32 lane-ops per interaction with the potential (20-flop convention)"}, check
+
+
+def _rel_rows(a, ref):
+    a = np.asarray(a, np.float64)
+    if ref.ndim == 2:
+        return np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    return np.abs(a - ref) / np.abs(ref)
+
+
+def oracle_checks(nb, dev, legs, checks, sample_idx, ref_acc):
+    """Every leg's result against the oracle (the CPU leg: rank 0, FP64 oracle on
+    the host cores).  Fills an "oracle_check" entry into each leg's dict."""
+    import json as _json
+    import torch
+    import nbody_inputs as ni
+    import oracle
+    out = {}
+    # with the potential: acceleration and potential on 2048 of the accuracy sample's bodies
+    if "with_potential" in checks:
+        w = checks["precision_w"]
+        idx = sample_idx[:2048]
+        ra, rp = oracle.accel_subset(w.pos, w.mass, w.eps, idx)
+        c = checks["with_potential"]
+        e = _rel_rows(c["acc"][idx], ra)
+        ep = _rel_rows(c["pot"][idx], rp)
+        legs["with_potential"]["oracle_check"] = {
+            "sample": f"{len(idx)} seeded bodies, FP64 sums over all {w.n}", "median_rel_acc_err": float(np.median(e)),
+            "max_rel_acc_err": float(e.max()), "max_rel_pot_err": float(ep.max()),
+            "target": "acc median <= 2e-6, max <= 1e-4; pot max <= 1e-5"}
+    # throughput workload: energy after 4 steps against the oracle's own 4-step run
+    c = checks["throughput"]
+    w = c["w"]
+    pr, vr, _ = oracle.leapfrog(w.pos, w.vel, w.mass, w.eps, w.dt, 4)
+    e0 = oracle.energy(w.pos, w.vel, w.mass, w.eps)["E"]
+    er = oracle.energy(pr, vr, w.mass, w.eps)["E"]
+    eg = oracle.energy(c["pos4"], c["vel4"], w.mass, w.eps)["E"]
+    legs["throughput_plain"]["oracle_check"] = {
+        "energy_vs_oracle_4_steps": abs(eg - er) / abs(e0), "max_abs_pos_err_4_steps": float(np.abs(c["pos4"] - pr).max()),
+        "target": "|E_gpu(4) - E_oracle(4)| / |E(0)| <= 1e-5", "energy_of": "the oracle's FP64 energy of each state"}
+    # ragged batch: 32 seeded systems after 64 steps against the oracle's leapfrog
+    c = checks["batched"]
+    off = c["off"]
+    worst_e, worst_x = 0.0, 0.0
+    for s_ in ni.subsample(len(off) - 1, 32, 404):
+        a_, b_ = off[s_], off[s_ + 1]
+        pr, vr, _ = oracle.leapfrog(c["pos"][a_:b_], c["vel"][a_:b_], c["mass"][a_:b_], c["eps"][s_], c["dt"], c["steps"])
+        e0 = oracle.energy(c["pos"][a_:b_], c["vel"][a_:b_], c["mass"][a_:b_], c["eps"][s_])["E"]
+        er = oracle.energy(pr, vr, c["mass"][a_:b_], c["eps"][s_])["E"]
+        eg = oracle.energy(c["pos_gpu"][a_:b_], c["vel_gpu"][a_:b_], c["mass"][a_:b_], c["eps"][s_])["E"]
+        worst_e = max(worst_e, abs(eg - er) / abs(e0))
+        worst_x = max(worst_x, float(np.abs(c["pos_gpu"][a_:b_] - pr).max()))
+    legs["batched"]["oracle_check"] = {"sample": "32 seeded systems after the 64 steps",
+                                       "max_rel_energy_err": worst_e, "max_abs_pos_err": worst_x,
+                                       "target": "energy within 1e-5 of |E(0)|, positions within 1e-4"}
+    # adjoint: the 32 stored finite differences of the workload, and the oracle's adjoint at n = 2048
+    c = checks["adjoint"]
+    doc = _json.load(open(os.path.join(ROOT, "tests", "golden", "adjoint_fd_n16384.json")))
+    errs = []
+    for r in doc["rows"]:
+        g = {"x0": c["gx"], "v0": c["gv"]}[r["kind"]][r["body"], r["component"]] if r["kind"] != "m" else c["gm"][r["body"]]
+        errs.append(abs(g - r["fd"]) / abs(r["fd"]))
+    sm = c["small"]
+    ws_ = sm["w"]
+    K = ws_.steps
+    xT, _, _ = oracle.leapfrog(ws_.pos, ws_.vel, ws_.mass, ws_.eps, ws_.dt, K)
+    rx, rv, rm = oracle.leapfrog_vjp(ws_.pos, ws_.vel, ws_.mass, ws_.eps, ws_.dt, K,
+                                     2 * ws_.mass[:, None] * (xT - ws_.extra["target"]), np.zeros_like(xT))
+
+    def rr(a, ref):  # per-body error relative to the body, never to less than a tenth of the median body
+        a = np.asarray(a, np.float64)
+        err = np.linalg.norm(a - ref, axis=1) if ref.ndim == 2 else np.abs(a - ref)
+        mag = np.linalg.norm(ref, axis=1) if ref.ndim == 2 else np.abs(ref)
+        return err / np.maximum(mag, 0.1 * np.median(mag))
+    ex, ev, em = rr(sm["gx"], rx), rr(sm["gv"], rv), rr(sm["gm"], rm)
+    legs["adjoint"]["oracle_check"] = {
+        "fd_32_coordinates_max_rel_err": float(max(errs)), "fd_32_coordinates_median_rel_err": float(np.median(errs)),
+        "fd_source": "tests/golden/adjoint_fd_n16384.json (FP64 central differences, h = 1e-6, of the oracle)",
+        "vs_oracle_adjoint_n2048": {"median_rel_err_x0": float(np.median(ex)), "median_rel_err_v0": float(np.median(ev)),
+                                    "median_rel_err_m": float(np.median(em)),
+                                    "max_rel_err": float(max(ex.max(), ev.max(), em.max()))},
+        "target": "FD within 1e-4 relative on 32 coordinates; FP64 adjoint median <= 1e-5"}
+    return out
+
+
+def listing_f32_point(w_plain, nb, dev, target_s=5.0):
+    """The second CPU point: the oracle's correctly rounded FP32 restatement of
+    Listing 4 (the paper's own single-precision arithmetic, run on the host
+    cores), its rate on a subsample of the FP32 throughput workload, and its
+    error against the FP64 oracle beside the GPU's plain FP32 result on the
+    same bodies."""
+    import torch
+    import nbody_inputs as ni
+    import oracle
+    w = w_plain
+    k = 64
+    while True:
+        idx = ni.subsample(w.n, k, 88)
+        t0 = time.perf_counter()
+        la, _ = oracle.accel_listing_f32(w.pos, w.mass, w.eps, with_pot=False, idx=idx)
+        dt = time.perf_counter() - t0
+        if dt >= target_s or k >= 8192:
+            break
+        k = min(8192, max(2 * k, int(k * target_s / max(dt, 1e-3))))
+    ra, _ = oracle.accel_subset(w.pos, w.mass, w.eps, idx, with_pot=False)
+    acc = torch.empty((w.n, 3), dtype=torch.float32, device=dev)
+    P = torch.from_numpy(w.pos.astype(np.float32)).to(dev)
+    M = torch.from_numpy(w.mass.astype(np.float32)).to(dev)
+    nb.nbody_accel_f32(P, M, np.float32(w.eps), acc, None)
+    g = acc.cpu().numpy().astype(np.float64)[idx]
+    el = _rel_rows(la, ra)
+    eg = _rel_rows(g, ra)
+    return {"value": k * w.n / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "listing_f32",
+            "sample": f"{k} sink bodies x all {w.n} sources of the N = 65536 FP32 workload ({dt:.1f} s)",
+            "listing_f32_vs_fp64": {"median_rel_err": float(np.median(el)), "max_rel_err": float(el.max())},
+            "gpu_plain_f32_vs_fp64": {"median_rel_err": float(np.median(eg)), "max_rel_err": float(eg.max())}}
 
 
 # ---------------------------------------------------------------------------
@@ -426,6 +612,8 @@ def main():
             nb.nbody_leapfrog(P, V, M, w.eps, w.dt, w.steps, precision=precision)
         torch.cuda.synchronize()
         nb.nbody_profile_read()  # reset counters
+        for kind in ("pack", "kick"):
+            nb.nbody_profile_read_kind(kind)
         nb.nbody_profile_enable(True)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         barrier(ws)
@@ -441,6 +629,7 @@ def main():
         wall = time.perf_counter() - t0
         nb.nbody_profile_enable(False)
         kms, klaunch, alllaunch = nb.nbody_profile_read()
+        timed_leg.integrator = {kind: nb.nbody_profile_read_kind(kind) for kind in ("pack", "kick")}
         step_s = [a.elapsed_time(b) / 1e3 for a, b in evs]
         assert nb.nbody_last_device_error() == 0
         return sum(step_s), wall, kms / 1e3, klaunch, alllaunch, step_s
@@ -448,6 +637,7 @@ def main():
     with ClockSampler(local) as clk:
         dev_s, wall_s, kern_s, klaunch, launches, per_step = timed_leg(nb.NBODY_PREC_MIXED, args.steps, args.warmup)
     clocks = clk.summary()
+    integ = timed_leg.integrator
     t_max = reduce_max(dev_s, ws)
     value = ws * args.steps * inter_per_step / t_max / 1e9
     peak_int_s = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_DEFAULT * 1e6 / FLOP_PER_INTERACTION
@@ -496,11 +686,37 @@ def main():
     if clocks.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved_tflops / (peak_tflops * clocks["sm_mhz"] / SM_MAX_MHZ_DEFAULT)
 
-    batched = batched_leg(nb, dev, sms, peak_int_s, args)
-    throughput = throughput_leg(nb, dev, peak_int_s, args)
-    adjoint = adjoint_leg(nb, dev, args)
+    # integrator kernels of the timed steps (CUDA events around each launch):
+    # algorithmic bytes per body -- pack: read x (24), v (24), a (12), m (4) and
+    # the Morton permutation (4), write x, v (48) and the packed j-entry (32);
+    # kick: read v (24), a (12), write v (24)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs")
+    hbm_basis = "measured copy bandwidth (MEASURED_PEAKS.json)" if hbm else "fallback 6800 GB/s (no measured file)"
+    hbm = hbm or 6800.0
+    integrator = {"peak_gbs": hbm, "peak_basis": hbm_basis}
+    for kind, bpb in (("pack", 148), ("kick", 60)):
+        ms, nl = integ[kind]
+        if nl:
+            us = ms * 1e3 / nl
+            gbs = n * bpb / (us * 1e-6) / 1e9
+            integrator[kind + "_kernel"] = {"bytes_per_body": bpb, "launches": nl, "us_per_launch": us,
+                                            "achieved_gbs": gbs, "frac": gbs / hbm}
+    integrator["note"] = ("times from CUDA events around each launch (a few microseconds of event overhead "
+                          "included); the pack kernel gathers x and v through the Morton permutation")
+
+    with_pot, wp_check = with_potential_leg(nb, dev, P0, M, w, peak_int_s, max(1, min(args.steps, 3)))
+    batched, b_check = batched_leg(nb, dev, sms, peak_int_s, args)
+    throughput, t_check = throughput_leg(nb, dev, peak_int_s, args)
+    adjoint, a_check = adjoint_leg(nb, dev, args)
+    adjoint["forward_pct_fp32_peak"] = adjoint["forward_gints"] * 1e9 / peak_int_s * 100
 
     cpu = None
+    cpu_listing = None
     accuracy = None
     if rank == 0 and not args.no_cpu:
         rate, k, dt, cores = oracle_rate(w, 12.0)
@@ -516,6 +732,10 @@ def main():
             got = acc.cpu().numpy().astype(np.float64)[idx]
             e = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
             accuracy[name] = {"median_rel_err": float(np.median(e)), "max_rel_err": float(e.max())}
+        legs = {"with_potential": with_pot, "throughput_plain": throughput, "batched": batched, "adjoint": adjoint}
+        oracle_checks(nb, dev, legs, {"with_potential": wp_check, "precision_w": w, "throughput": t_check,
+                                      "batched": b_check, "adjoint": a_check}, idx, ref)
+        cpu_listing = listing_f32_point(t_check["w"], nb, dev)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -526,7 +746,8 @@ def main():
         "plain": {"value": plain_value, "unit": UNIT, "pct_fp32_peak": plain_value * 1e9 / peak_int_s * 100,
                   "precision": "FP32 absolute coordinates (fails the accuracy target at this offset by design)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "roofline": roofline, "cpu_baseline": cpu, "accuracy": accuracy, "clocks": clocks, "batched": batched,
+        "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_listing_f32": cpu_listing, "accuracy": accuracy,
+        "clocks": clocks, "with_potential": with_pot, "integrator": integrator, "batched": batched,
         "throughput_plain": throughput, "adjoint": adjoint,
         "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
         "wall_s_timed_region": wall_s, "step_ms": [s * 1e3 for s in per_step],

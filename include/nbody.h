@@ -156,24 +156,35 @@ NBODY_API int nbody_energy_f32(int64_t n, const float* pos, const float* vel, co
  * Ragged batches: nsys independent systems in one persistent launch.  System s
  * owns bodies [offsets[s], offsets[s+1]) of the concatenated arrays; each has
  * its own softening eps[s] and interacts only with itself (Eq. 1 per system).
- *  offsets [nsys+1] int64, offsets[0] == 0, non-decreasing, every system at
- *          most NBODY_BATCH_MAX_N bodies (else NBODY_EINVAL); read on the host
- *          (a device array is copied back, which waits for the stream)
+ *  offsets [nsys+1] int64: offsets[0] == 0, non-decreasing, every system below
+ *          2^31 bodies; any system size is accepted.  A system that fits one
+ *          CTA's shared memory (about 14,000 bodies on GB300) is owned by one
+ *          CTA for the whole call; a larger one is split over several CTAs
+ *          that stream its bodies through shared memory and meet at a
+ *          barrier of their own between the phases of each step.
  *  pos [N][3] float, mass [N] float, eps [nsys] float (>= 0, finite)
  *  acc [N][3] float written; pot [N] float or NULL.
- * FP32 state and pair arithmetic; per-body sums in two levels (64-pair blocks).
- * opts->config selects the batched kernel shape (0 .. 3), -1 = default;
+ * Offsets and softenings in device memory are checked on the device: the
+ * call returns at once (asynchronous like every call on device arrays) and a
+ * bad batch is skipped, nothing written, and reported as NBODY_EINVAL by
+ * nbody_last_device_error().  Those in host memory are checked on the host
+ * (NBODY_EINVAL before any work is queued).  The largest-first order of the
+ * systems is computed on the device in both cases.
+ * FP32 state and pair arithmetic; per-body sums in two levels (64-pair
+ * blocks), plus a Kahan fold per tile for systems split over several CTAs.
+ * opts->config selects the batched kernel shape (0 .. 3), -1 = the tuned
+ * choice for the largest system when the offsets are host memory, else 0;
  * precision and accumulate are ignored.
  */
-#define NBODY_BATCH_MAX_N 12288
-NBODY_API int nbody_accel_batched(int64_t nsys, const int64_t* offsets, const float* pos, const float* mass, const float* eps,
-                        float* acc, float* pot, const nbody_opts* opts);
+NBODY_API int nbody_accel_batched(int64_t nsys, const int64_t* offsets, const float* pos, const float* mass,
+                                  const float* eps, float* acc, float* pot, const nbody_opts* opts);
 
 /* Kick-drift-kick leapfrog of every system of a ragged batch, all steps inside
  * one persistent kernel (steps + 1 force evaluations per system); pos, vel
- * [N][3] float updated in place. */
-NBODY_API int nbody_leapfrog_batched(int64_t nsys, const int64_t* offsets, float* pos, float* vel, const float* mass,
-                           const float* eps, float dt, int64_t steps, const nbody_opts* opts);
+ * [N][3] float updated in place, dt rounded to FP32 for the FP32 state. */
+NBODY_API int nbody_leapfrog_batched(int64_t nsys, const int64_t* offsets, float* pos, float* vel,
+                                     const float* mass, const float* eps, double dt, int64_t steps,
+                                     const nbody_opts* opts);
 
 /*
  * Separate sinks and sources: Listing 4's own form calc_acc(Ni, ipos, iacc,
@@ -210,26 +221,40 @@ NBODY_API int nbody_accel_vjp(int64_t n, const double* pos, const float* mass, d
                     const float* g_pot, float* g_pos, float* g_mass, const nbody_opts* opts);
 
 /*
- * Differentiating a leapfrog trajectory, checkpointed:
+ * Differentiating a leapfrog trajectory, checkpointed (not in the paper; the
+ * exact discrete adjoint of the kick-drift-kick steps nbody_leapfrog takes).
+ *
+ * nbody_leapfrog_vjp: for cotangents g_posT = dL/dx(T) and g_velT = dL/dv(T)
+ * of a run of `steps` steps from pos0, vel0, returns the gradients
+ * dL/dx(0), dL/dv(0) and the dynamics' part of dL/dm (FP64; a loss that also
+ * depends on m directly adds its own term).  pos0, vel0 [n][3] double and
+ * mass [n] float are inputs only (the run is recorded on copies in the
+ * library's workspace, with checkpoints every ckpt_every steps); every array
+ * may be host or device memory.  Cost: one forward run plus the sweep below.
+ *
+ * The same in two calls, for a caller that makes the forward run anyway:
  * nbody_leapfrog_record runs nbody_leapfrog (FP64 state, in place) and writes
  * a tape: for every checkpoint step k = 0, c, 2c, ... < steps (c = ckpt_every)
  * the positions x_k and half-step velocities v_{k+1/2}, then x_steps
  * (nbody_tape_bytes(n, steps, c) bytes of device memory, caller-owned).
- * nbody_leapfrog_vjp then returns, for cotangents g_posT = dL/dx(T) and
- * g_velT = dL/dv(T), the gradients dL/dx(0), dL/dv(0) and the dynamics' part
- * of dL/dm (FP64).  It is the exact discrete adjoint of the recorded steps:
- * the sweep runs newest segment first, replays each segment's positions from
- * its checkpoint (the same kernels, so the same bits), and applies one force
- * VJP per force evaluation of the forward run.  The tape and mass must be
- * device memory; the cotangent and gradient arrays may be host or device.
- * nbody_tape_bytes returns -1 for invalid sizes.
+ * nbody_leapfrog_vjp_tape is the reverse sweep from that tape: newest segment
+ * first, it replays each segment's positions from its checkpoint (the same
+ * kernels, so the same bits) and applies one force VJP per force evaluation
+ * of the forward run.  The tape and mass must be device memory; the cotangent
+ * and gradient arrays may be host or device.  nbody_tape_bytes returns -1
+ * for invalid sizes.
  */
+NBODY_API int nbody_leapfrog_vjp(int64_t n, const double* pos0, const double* vel0, const float* mass, double eps,
+                                 double dt, int64_t steps, int64_t ckpt_every, const double* g_posT,
+                                 const double* g_velT, double* g_pos0, double* g_vel0, double* g_mass,
+                                 const nbody_opts* opts);
 NBODY_API int64_t nbody_tape_bytes(int64_t n, int64_t steps, int64_t ckpt_every);
 NBODY_API int nbody_leapfrog_record(int64_t n, double* pos, double* vel, const float* mass, double eps, double dt,
-                          int64_t steps, int64_t ckpt_every, void* tape, const nbody_opts* opts);
-NBODY_API int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, double dt, int64_t steps, int64_t ckpt_every,
-                       const void* tape, const double* g_posT, const double* g_velT, double* g_pos0, double* g_vel0,
-                       double* g_mass, const nbody_opts* opts);
+                                    int64_t steps, int64_t ckpt_every, void* tape, const nbody_opts* opts);
+NBODY_API int nbody_leapfrog_vjp_tape(int64_t n, const float* mass, double eps, double dt, int64_t steps,
+                                      int64_t ckpt_every, const void* tape, const double* g_posT,
+                                      const double* g_velT, double* g_pos0, double* g_vel0, double* g_mass,
+                                      const nbody_opts* opts);
 
 /* Number of force-kernel shapes compiled in (for opts->config) and the
  * bodies per i-block of shape k (0 if k is out of range). */
@@ -254,10 +279,11 @@ NBODY_API int nbody_tune_load(const char* path);
 NBODY_API int nbody_tuned_shape(int kind, int64_t n, int pot);
 
 /* Synchronise the current device and report whether any kernel since the
- * last call hit a bounded-wait timeout (NBODY_ETIMEOUT) or, in a checked
- * build, an index out of range (NBODY_EBOUNDS; the access was skipped) --
- * the flag is then cleared -- or a CUDA error (NBODY_ECUDA); NBODY_OK
- * otherwise. */
+ * last call hit a bounded-wait timeout (NBODY_ETIMEOUT), found a ragged
+ * batch's device offsets or softenings invalid (NBODY_EINVAL; that batch was
+ * skipped) or, in a checked build, an index out of range (NBODY_EBOUNDS; the
+ * access was skipped) -- the flag is then cleared -- or a CUDA error
+ * (NBODY_ECUDA); NBODY_OK otherwise. */
 NBODY_API int nbody_last_device_error(void);
 
 /* The last CUDA runtime error code seen by the library on this thread. */
@@ -321,9 +347,15 @@ NBODY_API int nbody_accel_noalloc(int64_t n, const double* pos, const float* mas
  * bracketed by a pair of CUDA events recorded on its own stream.
  * nbody_profile_read waits for those events and returns the summed device
  * time of the force kernels (ms) and their number since the previous read,
- * plus the number of kernels of every kind the library queued; then resets. */
+ * plus the number of kernels of every kind the library queued; then resets.
+ * The leapfrog's integrator kernels are timed the same way:
+ * nbody_profile_read_kind(kind, &ms, &launches) returns and resets the summed
+ * device time and launch count of kind 0 (force kernel), 1 (pack kernel:
+ * kick, drift and the packed j-array) or 2 (closing kick kernel);
+ * NBODY_EINVAL for another kind. */
 NBODY_API void nbody_profile_enable(int on);
 NBODY_API int nbody_profile_read(double* force_ms, int64_t* force_launches, int64_t* all_launches);
+NBODY_API int nbody_profile_read_kind(int kind, double* ms, int64_t* launches);
 
 /* Free every cached workspace on every device (synchronises each device). */
 NBODY_API void nbody_finalize(void);

@@ -52,13 +52,14 @@ SIGNATURES = {
     "nbody_energy": (_int, [_i64, _vp, _vp, _vp, _dbl, _vp, _OPTS]),
     "nbody_energy_f32": (_int, [_i64, _vp, _vp, _vp, _flt, _vp, _OPTS]),
     "nbody_accel_batched": (_int, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _OPTS]),
-    "nbody_leapfrog_batched": (_int, [_i64, _vp, _vp, _vp, _vp, _vp, _flt, _i64, _OPTS]),
+    "nbody_leapfrog_batched": (_int, [_i64, _vp, _vp, _vp, _vp, _vp, _dbl, _i64, _OPTS]),
     "nbody_accel_ij": (_int, [_i64, _vp, _i64, _vp, _vp, _dbl, _vp, _vp, _OPTS]),
     "nbody_accel_ij_f32": (_int, [_i64, _vp, _i64, _vp, _vp, _flt, _vp, _vp, _OPTS]),
     "nbody_accel_vjp": (_int, [_i64, _vp, _vp, _dbl, _vp, _vp, _vp, _vp, _OPTS]),
     "nbody_tape_bytes": (_i64, [_i64, _i64, _i64]),
     "nbody_leapfrog_record": (_int, [_i64, _vp, _vp, _vp, _dbl, _dbl, _i64, _i64, _vp, _OPTS]),
-    "nbody_leapfrog_vjp": (_int, [_i64, _vp, _dbl, _dbl, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _OPTS]),
+    "nbody_leapfrog_vjp_tape": (_int, [_i64, _vp, _dbl, _dbl, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _OPTS]),
+    "nbody_leapfrog_vjp": (_int, [_i64, _vp, _vp, _vp, _dbl, _dbl, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _OPTS]),
     "nbody_tune_load": (_int, [ctypes.c_char_p]),
     "nbody_tuned_shape": (_int, [_int, _i64, _int]),
     "nbody_num_configs": (_int, []),
@@ -70,6 +71,7 @@ SIGNATURES = {
     "nbody_accel_noalloc": (_int, [_i64, _vp, _vp, _dbl, _vp, _vp, _vp, _vp]),
     "nbody_profile_enable": (None, [_int]),
     "nbody_profile_read": (_int, [ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "nbody_profile_read_kind": (_int, [_int, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]),
     "nbody_finalize": (None, []),
     "nbody_version": (_int, []),
 }

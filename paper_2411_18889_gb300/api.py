@@ -201,13 +201,29 @@ def nbody_leapfrog_record(pos, vel, mass, eps, dt, steps, ckpt_every, tape, **kw
           "nbody_leapfrog_record")
 
 
-def nbody_leapfrog_vjp(mass, eps, dt, steps, ckpt_every, tape, g_posT, g_velT, g_pos0, g_vel0, g_mass, **kw):
-    """nbody_leapfrog_vjp: cotangents g_posT, g_velT (n,3) f64; outputs g_pos0, g_vel0 (n,3) f64 and
-    g_mass (n,) f64 (the dynamics' part of dL/dm)."""
+def nbody_leapfrog_vjp_tape(mass, eps, dt, steps, ckpt_every, tape, g_posT, g_velT, g_pos0, g_vel0, g_mass, **kw):
+    """nbody_leapfrog_vjp_tape: the reverse sweep from a tape of nbody_leapfrog_record; cotangents
+    g_posT, g_velT (n,3) f64; outputs g_pos0, g_vel0 (n,3) f64 and g_mass (n,) f64 (the dynamics'
+    part of dL/dm)."""
     n = int(mass.shape[0])
     o = make_opts((mass, g_posT, g_pos0), **kw)
-    check(load().nbody_leapfrog_vjp(n, _ptr(mass, "f32", (n,), "mass"), float(eps), float(dt), int(steps),
-                                    int(ckpt_every), _tape_ptr(tape), _ptr(g_posT, "f64", (n, 3), "g_posT"),
+    check(load().nbody_leapfrog_vjp_tape(n, _ptr(mass, "f32", (n,), "mass"), float(eps), float(dt), int(steps),
+                                         int(ckpt_every), _tape_ptr(tape), _ptr(g_posT, "f64", (n, 3), "g_posT"),
+                                         _ptr(g_velT, "f64", (n, 3), "g_velT"), _ptr(g_pos0, "f64", (n, 3), "g_pos0"),
+                                         _ptr(g_vel0, "f64", (n, 3), "g_vel0"), _ptr(g_mass, "f64", (n,), "g_mass"),
+                                         ctypes.byref(o)),
+          "nbody_leapfrog_vjp_tape")
+
+
+def nbody_leapfrog_vjp(pos0, vel0, mass, eps, dt, steps, ckpt_every, g_posT, g_velT, g_pos0, g_vel0, g_mass, **kw):
+    """nbody_leapfrog_vjp: gradients of a loss of (x(T), v(T)) with respect to pos0, vel0 (n,3) f64
+    and mass (n,) f32 in one call (forward run recorded in the library's workspace, then swept);
+    outputs g_pos0, g_vel0 (n,3) f64 and g_mass (n,) f64."""
+    n = _n(pos0)
+    o = make_opts((pos0, vel0, mass, g_posT, g_pos0), **kw)
+    check(load().nbody_leapfrog_vjp(n, _ptr(pos0, "f64", (n, 3), "pos0"), _ptr(vel0, "f64", (n, 3), "vel0"),
+                                    _ptr(mass, "f32", (n,), "mass"), float(eps), float(dt), int(steps),
+                                    int(ckpt_every), _ptr(g_posT, "f64", (n, 3), "g_posT"),
                                     _ptr(g_velT, "f64", (n, 3), "g_velT"), _ptr(g_pos0, "f64", (n, 3), "g_pos0"),
                                     _ptr(g_vel0, "f64", (n, 3), "g_vel0"), _ptr(g_mass, "f64", (n,), "g_mass"),
                                     ctypes.byref(o)),
@@ -260,6 +276,18 @@ def nbody_profile_read():
     ms, k, allk = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
     check(load().nbody_profile_read(ctypes.byref(ms), ctypes.byref(k), ctypes.byref(allk)), "nbody_profile_read")
     return ms.value, k.value, allk.value
+
+
+PROFILE_KINDS = {"force": 0, "pack": 1, "kick": 2}
+
+
+def nbody_profile_read_kind(kind):
+    """(ms, launches) of one timed kernel kind since its last read: "force", "pack" (kick, drift
+    and packed j-array of a leapfrog step) or "kick" (the closing half kick)."""
+    ms, k = ctypes.c_double(), ctypes.c_int64()
+    check(load().nbody_profile_read_kind(PROFILE_KINDS[kind], ctypes.byref(ms), ctypes.byref(k)),
+          "nbody_profile_read_kind")
+    return ms.value, k.value
 
 
 def nbody_finalize():

@@ -3,7 +3,7 @@
 ``Trajectory.apply(x0, v0, m, eps, dt, steps, ckpt_every)`` integrates the
 kick-drift-kick leapfrog driven by Eq. 1 (Miki & Hanawa, Sec. III.A) with
 nbody_leapfrog_record and returns (x(T), v(T)); its backward calls
-nbody_leapfrog_vjp, so the gradients of any loss of (x(T), v(T)) with respect
+nbody_leapfrog_vjp_tape on the recorded tape, so the gradients of any loss of (x(T), v(T)) with respect
 to x0, v0 and m come from the library's adjoint kernels.  A loss that also uses
 m directly gets that term from torch's own graph.
 """
@@ -39,5 +39,5 @@ class Trajectory(torch.autograd.Function):
         gv = z() if gv is None else gv.to(torch.float64).contiguous()
         g_x0, g_v0 = z(), z()
         g_m = torch.zeros((n,), dtype=torch.float64, device=m32.device)
-        api.nbody_leapfrog_vjp(m32, eps, dt, steps, ckpt, tape, gx, gv, g_x0, g_v0, g_m)
+        api.nbody_leapfrog_vjp_tape(m32, eps, dt, steps, ckpt, tape, gx, gv, g_x0, g_v0, g_m)
         return g_x0.to(xdt), g_v0.to(vdt), g_m.to(mdt), None, None, None, None

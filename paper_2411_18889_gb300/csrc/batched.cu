@@ -3,32 +3,52 @@
 // Listing 4) for each system, optionally driving a whole kick-drift-kick
 // leapfrog inside the kernel (the integrator is not in the paper).
 //
-// Scheduling.  A persistent grid of CTAs pulls systems from an atomic queue in
-// longest-processing-time-first order (the host sorts by n_s^2), so the few
-// large systems start first and the many small ones fill the tail.  One CTA
-// owns one system for the whole call: its bodies live in shared memory, and
-// every force evaluation and every kick and drift of all steps happen without
-// another launch.
+// Planning on the device.  A call queues a few small kernels before the
+// persistent one, so it never waits for the host: one validates the offsets
+// and softenings (a bad batch sets the error word and nothing is written) and
+// gives every system an 8-bit key, large systems first, then the others by
+// size in steps of 1/8 octave; one stable radix pass orders the systems by
+// that key (longest processing time first, to within 12.5 %); one small
+// kernel counts the workers each large system gets.
 //
-// Shapes (chosen by the largest system of the batch through the tune table).
-// From about 760 bodies up one 512-thread CTA per SM owns a system (16 warps
-// on one system, i-passes of 2048 bodies); smaller batches run 256- or
-// 128-thread CTAs, several per SM, each on its own system.  On GB300 the
-// single large CTA ran the ragged 64-to-4096-body workload at 71.7 % of FP32
-// peak against 66.1 % for two 256-thread CTAs per SM.
+// Scheduling.  A persistent grid of CTAs pulls work items from an atomic
+// queue in that order.  A system that fits the CTA's shared-memory image
+// ("small") is one item: one CTA owns it for the whole call, and every force
+// evaluation and every kick and drift of all steps happen without another
+// launch.  A system larger than the image ("large") is W items, W = the
+// number of 2*T-body i-chunks it has, at most the grid: its W workers each
+// take every W-th chunk and stream the system's bodies through shared
+// memory in tiles; between a step's force evaluation and its drift, and
+// after the drift, the workers meet at a barrier of their own in global
+// memory.  The launch is cooperative whenever a large system can occur, so
+// every CTA of the grid is resident and the items of a large system, which
+// are contiguous in the queue, are all taken by running CTAs.  The barrier's
+// wait is bounded: it gives up (error word, the CTA moves on) only when no
+// CTA of the grid has made progress for 4 s, so a long item elsewhere in the
+// grid cannot end it early.
 //
-// Layout.  Shared memory holds the system as j-pairs (x0,x1,y0,y1,z0,z1,m0,m1):
-// 16 bytes per body, so a 4096-body system takes 64 KiB.  Each thread keeps I
-// i-bodies with their coordinates duplicated in f32x2
-// registers (x_i, x_i); one pair of 16-byte broadcast loads gives two j-bodies
-// and each i-body then takes the 12 (13 with the potential) packed f32x2
-// instructions and two MUFU reciprocal square roots of Listing 4's sequence,
-// for two interactions.  The two halves of each accumulator (even and odd j)
-// are added at the end.
+// Shapes (chosen by the largest system of the batch through the tune table
+// when the host knows the sizes; shape 0 otherwise).  From about 760 bodies
+// up one 512-thread CTA per SM owns a system (16 warps on one system,
+// i-passes of 2048 bodies); smaller batches run 256- or 128-thread CTAs,
+// several per SM, each on its own system.  On GB300 the single large CTA ran
+// the ragged 64-to-4096-body workload at 71.7 % of FP32 peak against 66.1 %
+// for two 256-thread CTAs per SM.
+//
+// Layout.  Shared memory holds the system (or a tile of a large one) as
+// j-pairs (x0,x1,y0,y1,z0,z1,m0,m1): 16 bytes per body, so a 4096-body system
+// takes 64 KiB.  Each thread keeps I i-bodies with their coordinates
+// duplicated in f32x2 registers (x_i, x_i); one pair of 16-byte broadcast
+// loads gives two j-bodies and each i-body then takes the 12 (13 with the
+// potential) packed f32x2 instructions and two MUFU reciprocal square roots
+// of Listing 4's sequence, for two interactions.  The two halves of each
+// accumulator (even and odd j) are added at the end.
 //
 // Accumulation.  FP32 partial sums over blocks of 64 j-pairs are folded into
 // an FP32 total (two-level summation), so a 4096-term sum carries the rounding
-// of two 64-term sums instead of one 4096-term running sum.
+// of two 64-term sums instead of one 4096-term running sum.  Large systems
+// add a third level: each tile's FP32 total is folded into the running sum by
+// Kahan summation.
 //
 // Self term.  The pair j = i is excluded exactly, as Eq. 1 states, wherever
 // it would change a result: in the potential (it would add m_i/eps, and once
@@ -39,36 +59,43 @@
 // Leapfrog evaluations with eps > 0 need no mask: the difference vector of the
 // self pair is exactly zero, so it adds exactly 0 to the acceleration.
 #include <algorithm>
-#include <mutex>
+#include <climits>
 
 #include "nbody_internal.cuh"
 
 namespace nbk {
 namespace {
 
+// Plan words (int64, on the device), written by the planning kernels.
+enum PlanWord { kPlanInvalid = 0, kPlanLarge = 1, kPlanLargeItems = 2, kPlanBodies = 3, kPlanWords = 4 };
 
 struct BParams {
     int64_t nsys;
-    const int64_t* offsets;  // [nsys+1] device
-    const int* order;        // [nsys] LPT order
-    int* queue;              // atomic counter, zeroed before the launch
-    float* pos;              // [N][3]
-    float* vel;              // [N][3] (leapfrog)
-    const float* mass;       // [N]
-    const float* eps;        // [nsys]
-    float* acc;              // [N][3] (force only)
-    float* pot;              // [N] or nullptr (force only)
+    const int64_t* offsets;   // [nsys+1] device
+    const float* eps;         // [nsys]
+    const int* order;         // [nsys] large systems first, then by size, descending
+    const int64_t* plan;      // kPlanWords words
+    const int64_t* lprefix;   // [L+1] prefix sums of the large systems' worker counts
+    unsigned long long* queue;  // item counter, zeroed before the launch
+    unsigned long long* sysbar;  // [nsys] barrier counters of large systems, zeroed before the launch
+    unsigned* heartbeat;      // bumped by every CTA as it makes progress
+    float* pos;               // [N][3]
+    float* vel;               // [N][3] (leapfrog)
+    const float* mass;        // [N]
+    float* acc;               // [N][3] (force only)
+    float* pot;               // [N] or nullptr (force only)
     float dt;
-    int64_t steps;           // 0: force only
-    int64_t ntot;            // bodies over all systems
-    int* err;                // error word (checked builds record index faults)
+    int64_t steps;            // 0: force only
+    int cap;                  // bodies the shared-memory image holds (multiple of 128 when large systems occur)
+    int grid;                 // CTAs of the launch
+    int* err;                 // error word
 };
 
 // One block of j-pairs [jb, je) against the thread's I i-bodies.  M: zero the
-// pair whose j equals the i-body (ib[k]).  UNI: every body of the system has
-// the mass mu; the pair weight then leaves out the multiplication by m_j (11
-// instead of 12 FP32 operations per interaction) and the sums are scaled by
-// mu once per body.
+// pair whose j equals the i-body (ib[k] is its index relative to the first
+// body of the j-array).  UNI: every body of the system has the mass mu; the
+// pair weight then leaves out the multiplication by m_j (11 instead of 12 FP32
+// operations per interaction) and the sums are scaled by mu once per body.
 template <int I, bool POT, bool M, bool UNI, int U>
 __device__ __forceinline__ void jblock(const ulonglong2* __restrict__ sp, int jb, int je, const f2 (&xi)[I],
                                        const f2 (&yi)[I], const f2 (&zi)[I], const int (&ib)[I], f2 eps2,
@@ -105,30 +132,16 @@ __device__ __forceinline__ void jblock(const ulonglong2* __restrict__ sp, int jb
     }
 }
 
-// One pass: I i-bodies per thread (slot k of thread t is body base + k*T + t)
-// against every j-pair of the system.  MASK: exclude the self pair, in the
-// 64-pair block holding the warp's bodies of each slot.
-template <int T, int I, bool POT, bool MASK, bool UNI, int U, int JB>
-__device__ __forceinline__ void eval_pass(const float* __restrict__ sj, int npair, int ns, int base, f2 eps2,
-                                          const BParams& p, int64_t off, float kick, bool drift, float mu) {
-    static_assert(T % 32 == 0 && JB % 16 == 0, "a warp's 32 bodies of a slot lie in one j-block");
-    const int tid = threadIdx.x;
-    f2 xi[I], yi[I], zi[I];
-    int ib[I];
-    int selfblk[I];  // first j-pair of the block holding this warp's bodies of slot k
-#pragma unroll
-    for (int k = 0; k < I; ++k) {
-        ib[k] = base + k * T + tid;
-        selfblk[k] = (((base + k * T + 32 * (tid >> 5)) >> 1) / JB) * JB;
-        const int b = ib[k] < ns ? ib[k] : 0;  // threads past the end repeat body 0 and write nothing
-        const float* s = sj + (b >> 1) * 8 + (b & 1);
-        xi[k] = pk(s[0], s[0]);
-        yi[k] = pk(s[2], s[2]);
-        zi[k] = pk(s[4], s[4]);
-    }
-    f2 tx[I], ty[I], tz[I], tp[I];
-#pragma unroll
-    for (int k = 0; k < I; ++k) tx[k] = ty[k] = tz[k] = tp[k] = 0ull;
+// The pairs of a j-array image of npair pairs against the thread's I
+// i-bodies, into the FP32 totals t*: FP32 partial sums over blocks of JB
+// pairs folded into t*.  MASK: exclude the self pair; ib[k] is body k's index
+// relative to the image and (ws[k] >> 1) its warp's first pair, or negative
+// when the warp's bodies of slot k are not in this image.
+template <int I, bool POT, bool MASK, bool UNI, int U, int JB>
+__device__ __forceinline__ void image_sum(const float* __restrict__ sj, int npair, const f2 (&xi)[I],
+                                          const f2 (&yi)[I], const f2 (&zi)[I], const int (&ib)[I],
+                                          const int (&ws)[I], f2 eps2, f2 (&tx)[I], f2 (&ty)[I], f2 (&tz)[I],
+                                          f2 (&tp)[I]) {
     const ulonglong2* sp = reinterpret_cast<const ulonglong2*>(sj);
     for (int jb = 0; jb < npair; jb += JB) {
         const int je = min(npair, jb + JB);
@@ -138,7 +151,7 @@ __device__ __forceinline__ void eval_pass(const float* __restrict__ sj, int npai
         bool own = false;
         if (MASK) {
 #pragma unroll
-            for (int k = 0; k < I; ++k) own = own || selfblk[k] == jb;
+            for (int k = 0; k < I; ++k) own = own || (ws[k] >= 0 && ((ws[k] >> 1) / JB) * JB == jb);
         }
         if (own)
             jblock<I, POT, true, UNI, U>(sp, jb, je, xi, yi, zi, ib, eps2, ax, ay, az, ap);
@@ -152,77 +165,120 @@ __device__ __forceinline__ void eval_pass(const float* __restrict__ sj, int npai
             if (POT) tp[k] = add2(tp[k], ap[k]);
         }
     }
+}
+
+// Result of one i-body g of the batch from its summed pair halves: the
+// acceleration (and potential) of a force-only call, or the kick (and, for
+// small systems, the drift) of a leapfrog evaluation.
+template <bool POT, bool UNI>
+__device__ __forceinline__ void body_out(const BParams& p, int64_t g, f2 sx, f2 sy, f2 sz, f2 sp, float mu,
+                                         float kick, bool drift) {
+    float a0, a1;
+    upk(sx, a0, a1);
+    float ax = a0 + a1;
+    upk(sy, a0, a1);
+    float ay = a0 + a1;
+    upk(sz, a0, a1);
+    float az = a0 + a1;
+    if (UNI) {
+        ax *= mu;
+        ay *= mu;
+        az *= mu;
+    }
+    if (p.steps == 0) {
+        p.acc[3 * g + 0] = ax;
+        p.acc[3 * g + 1] = ay;
+        p.acc[3 * g + 2] = az;
+        if (POT) {
+            upk(sp, a0, a1);
+            float s = a0 + a1;
+            if (UNI) s *= mu;
+            p.pot[g] = -s;
+        }
+    } else {
+        float vx = p.vel[3 * g + 0], vy = p.vel[3 * g + 1], vz = p.vel[3 * g + 2];
+        vx = fmaf(kick, ax, vx);
+        vy = fmaf(kick, ay, vy);
+        vz = fmaf(kick, az, vz);
+        p.vel[3 * g + 0] = vx;
+        p.vel[3 * g + 1] = vy;
+        p.vel[3 * g + 2] = vz;
+        if (drift) {
+            p.pos[3 * g + 0] = fmaf(p.dt, vx, p.pos[3 * g + 0]);
+            p.pos[3 * g + 1] = fmaf(p.dt, vy, p.pos[3 * g + 1]);
+            p.pos[3 * g + 2] = fmaf(p.dt, vz, p.pos[3 * g + 2]);
+        }
+    }
+}
+
+// Small systems: one pass of I i-bodies per thread (slot k of thread t is
+// body base + k*T + t) against every j-pair of the system's image.
+template <int T, int I, bool POT, bool MASK, bool UNI, int U, int JB>
+__device__ __forceinline__ void eval_pass(const float* __restrict__ sj, int npair, int ns, int base, f2 eps2,
+                                          const BParams& p, int64_t off, int64_t ntot, float kick, bool drift,
+                                          float mu) {
+    static_assert(T % 32 == 0 && JB % 16 == 0, "a warp's 32 bodies of a slot lie in one j-block");
+    const int tid = threadIdx.x;
+    f2 xi[I], yi[I], zi[I];
+    int ib[I], ws[I];
+#pragma unroll
+    for (int k = 0; k < I; ++k) {
+        ib[k] = base + k * T + tid;
+        ws[k] = base + k * T + 32 * (tid >> 5);
+        const int b = ib[k] < ns ? ib[k] : 0;  // threads past the end repeat body 0 and write nothing
+        const float* s = sj + (b >> 1) * 8 + (b & 1);
+        xi[k] = pk(s[0], s[0]);
+        yi[k] = pk(s[2], s[2]);
+        zi[k] = pk(s[4], s[4]);
+    }
+    f2 tx[I], ty[I], tz[I], tp[I];
+#pragma unroll
+    for (int k = 0; k < I; ++k) tx[k] = ty[k] = tz[k] = tp[k] = 0ull;
+    image_sum<I, POT, MASK, UNI, U, JB>(sj, npair, xi, yi, zi, ib, ws, eps2, tx, ty, tz, tp);
 #pragma unroll
     for (int k = 0; k < I; ++k) {
         if (ib[k] >= ns) continue;
-        float a0, a1;
-        upk(tx[k], a0, a1);
-        float ax_ = a0 + a1;
-        upk(ty[k], a0, a1);
-        float ay_ = a0 + a1;
-        upk(tz[k], a0, a1);
-        float az_ = a0 + a1;
-        if (UNI) {
-            ax_ *= mu;
-            ay_ *= mu;
-            az_ *= mu;
-        }
         const int64_t g = off + ib[k];
-        if (!in_range(g, p.ntot, p.err)) continue;
-        if (p.steps == 0) {
-            p.acc[3 * g + 0] = ax_;
-            p.acc[3 * g + 1] = ay_;
-            p.acc[3 * g + 2] = az_;
-            if (POT) {
-                upk(tp[k], a0, a1);
-                float s = a0 + a1;
-                if (UNI) s *= mu;
-                p.pot[g] = -s;
-            }
-        } else {
-            float vx = p.vel[3 * g + 0], vy = p.vel[3 * g + 1], vz = p.vel[3 * g + 2];
-            vx = fmaf(kick, ax_, vx);
-            vy = fmaf(kick, ay_, vy);
-            vz = fmaf(kick, az_, vz);
-            p.vel[3 * g + 0] = vx;
-            p.vel[3 * g + 1] = vy;
-            p.vel[3 * g + 2] = vz;
-            if (drift) {
-                p.pos[3 * g + 0] = fmaf(p.dt, vx, p.pos[3 * g + 0]);
-                p.pos[3 * g + 1] = fmaf(p.dt, vy, p.pos[3 * g + 1]);
-                p.pos[3 * g + 2] = fmaf(p.dt, vz, p.pos[3 * g + 2]);
-            }
-        }
+        if (!in_range(g, ntot, p.err)) continue;
+        body_out<POT, UNI>(p, g, tx[k], ty[k], tz[k], tp[k], mu, kick, drift);
     }
 }
 
 // eval_pass with I' = min(I, left) i-bodies per thread.
 template <int T, int I, bool POT, bool MASK, bool UNI, int U, int JB>
 __device__ __forceinline__ void pass_dispatch(int left, const float* __restrict__ sj, int npair, int ns, int base,
-                                              f2 eps2, const BParams& p, int64_t off, float kick, bool drift,
-                                              float mu) {
+                                              f2 eps2, const BParams& p, int64_t off, int64_t ntot, float kick,
+                                              bool drift, float mu) {
     if (I >= 4 && left >= 4) {
-        eval_pass<T, (I >= 4 ? 4 : 1), POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, kick, drift, mu);
+        eval_pass<T, (I >= 4 ? 4 : 1), POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, ntot, kick, drift, mu);
     } else if (I >= 3 && left >= 3) {
-        eval_pass<T, (I >= 3 ? 3 : 1), POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, kick, drift, mu);
+        eval_pass<T, (I >= 3 ? 3 : 1), POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, ntot, kick, drift, mu);
     } else if (I >= 2 && left >= 2) {
-        eval_pass<T, (I >= 2 ? 2 : 1), POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, kick, drift, mu);
+        eval_pass<T, (I >= 2 ? 2 : 1), POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, ntot, kick, drift, mu);
     } else {
-        eval_pass<T, 1, POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, kick, drift, mu);
+        eval_pass<T, 1, POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, ntot, kick, drift, mu);
     }
 }
 
-// Shared-memory image of system s: j-pairs, an odd count padded with a
-// massless body far away.
-__device__ __forceinline__ void load_system(float* sj, const BParams& p, int64_t off, int ns) {
-    const int nb = (ns + 1) & ~1;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+// Position load; CG: through L2 only (ld.global.cg), for positions another
+// CTA of this launch wrote (the L1 of this SM may still hold older values).
+template <bool CG>
+__device__ __forceinline__ float ld_pos(const float* a) {
+    return CG ? __ldcg(a) : *a;
+}
+
+// Shared-memory image of bodies [g0, g0 + nb) of the batch as j-pairs, an odd
+// count padded with a massless body far away.
+template <bool CG = false>
+__device__ __forceinline__ void load_image(float* sj, const BParams& p, int64_t g0, int nb, int64_t ntot) {
+    const int nbp = (nb + 1) & ~1;
+    for (int b = threadIdx.x; b < nbp; b += blockDim.x) {
         float x = kPadPos, y = kPadPos, z = kPadPos, m = 0.0f;
-        if (b < ns && in_range(off + b, p.ntot, p.err)) {
-            const int64_t g = off + b;
-            x = p.pos[3 * g + 0];
-            y = p.pos[3 * g + 1];
-            z = p.pos[3 * g + 2];
+        if (b < nb && in_range(g0 + b, ntot, p.err)) {
+            const int64_t g = g0 + b;
+            x = ld_pos<CG>(p.pos + 3 * g + 0);
+            y = ld_pos<CG>(p.pos + 3 * g + 1);
+            z = ld_pos<CG>(p.pos + 3 * g + 2);
             m = p.mass[g];
         }
         float* d = sj + (b >> 1) * 8 + (b & 1);
@@ -233,68 +289,357 @@ __device__ __forceinline__ void load_system(float* sj, const BParams& p, int64_t
     }
 }
 
+// Equal masses throughout the system (the usual ensemble member)?  Every
+// thread of the CTA calls this; *mu gets the first body's mass.
+__device__ __forceinline__ bool uniform_system(const BParams& p, int64_t off, int ns, int64_t ntot, float* mu) {
+    float m0 = 0.0f;
+    if (in_range(off, ntot, p.err)) m0 = p.mass[off];
+    bool same = true;
+    for (int b = threadIdx.x; b < ns; b += blockDim.x)
+        if (in_range(off + b, ntot, p.err)) same = same && p.mass[off + b] == m0;
+    *mu = m0;
+    return __syncthreads_and(same) != 0;
+}
+
+// A small system, owned by this CTA for all steps of the call.
+template <int T, int I, bool POT, int U, int JB>
+__device__ void run_small(float* sj, const BParams& p, int s, int64_t ntot) {
+    const int64_t off = p.offsets[s];
+    const int ns = (int)(p.offsets[s + 1] - off);
+    if (ns <= 0) return;
+    const float e = p.eps[s];
+    const float eps2s = e * e;
+    const f2 eps2 = pk(eps2s, eps2s);
+    const int npair = (ns + 1) >> 1;
+    float mu;
+    const bool uni = uniform_system(p, off, ns, ntot, &mu);
+    load_image(sj, p, off, ns, ntot);
+    __syncthreads();
+    for (int64_t ev = 0; ev <= p.steps; ++ev) {
+        const float kick = (p.steps == 0) ? 0.0f : ((ev == 0 || ev == p.steps) ? 0.5f * p.dt : p.dt);
+        const bool drift = ev < p.steps;
+        for (int base = 0; base < ns; base += T * I) {
+            // Each warp takes only as many i-bodies per thread as it has
+            // left in this pass (slot k of lane l is body base + k*T + l),
+            // and a warp with none skips the pass: padding costs less than
+            // one warp's row of bodies per system, not up to T*I - 1.
+            const int lw = ns - base - 32 * (int)(threadIdx.x >> 5);
+            const int left = lw <= 0 ? 0 : (lw + T - 1) / T;
+            if (left == 0) {
+            } else if (POT || eps2s == 0.0f) {  // the self pair must be excluded
+                if (uni)
+                    pass_dispatch<T, I, POT, true, true, U, JB>(left, sj, npair, ns, base, eps2, p, off, ntot, kick,
+                                                                drift, mu);
+                else
+                    pass_dispatch<T, I, POT, true, false, U, JB>(left, sj, npair, ns, base, eps2, p, off, ntot, kick,
+                                                                 drift, mu);
+            } else {
+                if (uni)
+                    pass_dispatch<T, I, POT, false, true, U, JB>(left, sj, npair, ns, base, eps2, p, off, ntot,
+                                                                 kick, drift, mu);
+                else
+                    pass_dispatch<T, I, POT, false, false, U, JB>(left, sj, npair, ns, base, eps2, p, off, ntot,
+                                                                  kick, drift, mu);
+            }
+        }
+        __syncthreads();
+        if (drift) {
+            load_image(sj, p, off, ns, ntot);  // the drifted positions of this step
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) atomicAdd(p.heartbeat, 1u);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Large systems: several CTAs per system, bodies streamed in tiles.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long load_acquire_u64(const unsigned long long* a) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned load_relaxed_u32(const unsigned* a) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+// The W workers of one large system meet here once per phase: each CTA adds 1
+// to the system's counter and waits until it reaches target = phase * W.  The
+// wait is bounded: if the counter is still short while no CTA of the grid has
+// bumped the heartbeat for kWaitLimitNs, the wait gives up, records a timeout
+// in the error word and returns false (the caller abandons the system).
+__device__ bool system_barrier(const BParams& p, unsigned long long* ctr, unsigned long long target) {
+    __shared__ int s_ok;
+    __syncthreads();  // every thread's writes of this phase are issued
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1ull);
+        int ok = 1;
+        unsigned hb = load_relaxed_u32(p.heartbeat);
+        uint64_t t0 = globaltimer_ns();
+        while (load_acquire_u64(ctr) < target) {
+            __nanosleep(256);
+            const uint64_t now = globaltimer_ns();
+            if (now - t0 > kWaitLimitNs) {
+                const unsigned h = load_relaxed_u32(p.heartbeat);
+                if (h == hb) {
+                    ok = 0;
+                    atomicExch(p.err, kErrTimeout);
+                    break;
+                }
+                hb = h;
+                t0 = now;
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ void kahan_fold(f2& sum, f2& comp, f2 part) {
+    const f2 y = sub2(part, comp);
+    const f2 t = add2(sum, y);
+    comp = sub2(sub2(t, sum), y);
+    sum = t;
+}
+
+// One chunk of 2T i-bodies [cb, cb + 2T) of a large system (bodies
+// [off, off + ns) of the batch) against all of its bodies, streamed through
+// the shared-memory image in tiles of tj bodies (a multiple of 128, so a
+// warp's 32 bodies of a slot lie in one tile and one 64-pair block).  Writes
+// the acceleration (and potential) or applies the kick; the drift of a large
+// system waits for its barrier.
+template <int T, bool POT, bool MASK, bool UNI, int U, int JB>
+__device__ void large_chunk(float* sj, const BParams& p, int64_t off, int ns, int cb, int tj, f2 eps2, float kick,
+                            float mu, int64_t ntot) {
+    constexpr int I = 2;
+    const int tid = threadIdx.x;
+    f2 xi[I], yi[I], zi[I];
+    int ib[I];
+#pragma unroll
+    for (int k = 0; k < I; ++k) {
+        ib[k] = cb + k * T + tid;
+        const int64_t g = off + (ib[k] < ns ? ib[k] : cb);  // past the end: repeat the chunk's first body
+        float x = 0.0f, y = 0.0f, z = 0.0f;
+        if (in_range(g, ntot, p.err)) {
+            x = ld_pos<true>(p.pos + 3 * g + 0);
+            y = ld_pos<true>(p.pos + 3 * g + 1);
+            z = ld_pos<true>(p.pos + 3 * g + 2);
+        }
+        xi[k] = pk(x, x);
+        yi[k] = pk(y, y);
+        zi[k] = pk(z, z);
+    }
+    f2 sx[I], sy[I], sz[I], sp[I], cx[I], cy[I], cz[I], cp[I];
+#pragma unroll
+    for (int k = 0; k < I; ++k) sx[k] = sy[k] = sz[k] = sp[k] = cx[k] = cy[k] = cz[k] = cp[k] = 0ull;
+    for (int j0 = 0; j0 < ns; j0 += tj) {
+        const int nb = min(tj, ns - j0);
+        __syncthreads();  // the previous tile is consumed
+        load_image<true>(sj, p, off + j0, nb, ntot);
+        __syncthreads();
+        int ibr[I], ws[I];
+#pragma unroll
+        for (int k = 0; k < I; ++k) {
+            ibr[k] = ib[k] - j0;
+            const int w0 = cb + k * T + 32 * (tid >> 5) - j0;
+            ws[k] = (w0 >= 0 && w0 < nb) ? w0 : -1;
+        }
+        f2 tx[I], ty[I], tz[I], tp[I];
+#pragma unroll
+        for (int k = 0; k < I; ++k) tx[k] = ty[k] = tz[k] = tp[k] = 0ull;
+        image_sum<I, POT, MASK, UNI, U, JB>(sj, (nb + 1) >> 1, xi, yi, zi, ibr, ws, eps2, tx, ty, tz, tp);
+#pragma unroll
+        for (int k = 0; k < I; ++k) {
+            kahan_fold(sx[k], cx[k], tx[k]);
+            kahan_fold(sy[k], cy[k], ty[k]);
+            kahan_fold(sz[k], cz[k], tz[k]);
+            if (POT) kahan_fold(sp[k], cp[k], tp[k]);
+        }
+        if (tid == 0) atomicAdd(p.heartbeat, 1u);
+    }
+#pragma unroll
+    for (int k = 0; k < I; ++k) {
+        if (ib[k] >= ns) continue;
+        const int64_t g = off + ib[k];
+        if (!in_range(g, ntot, p.err)) continue;
+        body_out<POT, UNI>(p, g, sub2(sx[k], cx[k]), sub2(sy[k], cy[k]), sub2(sz[k], cz[k]), sub2(sp[k], cp[k]), mu,
+                           kick, false);
+    }
+}
+
+// Worker w of the W workers of large system s: chunks w, w + W, ... of 2T
+// bodies, for every force evaluation of the call.
+template <int T, bool POT, int U, int JB>
+__device__ void run_large(float* sj, const BParams& p, int s, int w, int W, int64_t ntot) {
+    const int64_t off = p.offsets[s];
+    const int ns = (int)(p.offsets[s + 1] - off);
+    const float e = p.eps[s];
+    const float eps2s = e * e;
+    const f2 eps2 = pk(eps2s, eps2s);
+    float mu;
+    const bool uni = uniform_system(p, off, ns, ntot, &mu);
+    const int C = 2 * T;
+    const int nch = (ns + C - 1) / C;
+    const bool mask = POT || eps2s == 0.0f;
+    unsigned long long* bar = p.sysbar + s;
+    unsigned long long phase = 0;
+    for (int64_t ev = 0; ev <= p.steps; ++ev) {
+        const float kick = (p.steps == 0) ? 0.0f : ((ev == 0 || ev == p.steps) ? 0.5f * p.dt : p.dt);
+        for (int c = w; c < nch; c += W) {
+            if (mask) {
+                if (uni)
+                    large_chunk<T, POT, true, true, U, JB>(sj, p, off, ns, c * C, p.cap, eps2, kick, mu, ntot);
+                else
+                    large_chunk<T, POT, true, false, U, JB>(sj, p, off, ns, c * C, p.cap, eps2, kick, mu, ntot);
+            } else {
+                if (uni)
+                    large_chunk<T, POT, false, true, U, JB>(sj, p, off, ns, c * C, p.cap, eps2, kick, mu, ntot);
+                else
+                    large_chunk<T, POT, false, false, U, JB>(sj, p, off, ns, c * C, p.cap, eps2, kick, mu, ntot);
+            }
+        }
+        if (ev < p.steps) {
+            // every worker has read the positions of this evaluation ...
+            if (!system_barrier(p, bar, ++phase * (unsigned long long)W)) return;
+            for (int c = w; c < nch; c += W) {
+                const int hi = min(ns, (c + 1) * C);
+                for (int b = c * C + (int)threadIdx.x; b < hi; b += T) {
+                    const int64_t g = off + b;
+                    if (!in_range(g, ntot, p.err)) continue;
+                    p.pos[3 * g + 0] = fmaf(p.dt, p.vel[3 * g + 0], p.pos[3 * g + 0]);
+                    p.pos[3 * g + 1] = fmaf(p.dt, p.vel[3 * g + 1], p.pos[3 * g + 1]);
+                    p.pos[3 * g + 2] = fmaf(p.dt, p.vel[3 * g + 2], p.pos[3 * g + 2]);
+                }
+            }
+            // ... and has drifted its bodies before the next evaluation reads them
+            if (!system_barrier(p, bar, ++phase * (unsigned long long)W)) return;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The persistent kernel.
+// ---------------------------------------------------------------------------
 template <int T, int I, bool POT, int U, int JB>
 __global__ void __launch_bounds__(T) batched_kernel(const BParams p) {
     extern __shared__ __align__(16) float sj[];
-    __shared__ int s_next;
+    __shared__ unsigned long long s_item;
+    if (p.plan[kPlanInvalid] != 0) return;  // a bad batch: nothing is written
+    const int64_t L = p.plan[kPlanLarge];
+    const int64_t TL = p.plan[kPlanLargeItems];
+    const int64_t ntot = p.plan[kPlanBodies];
+    const unsigned long long nitems = (unsigned long long)(TL + (p.nsys - L));
     for (;;) {
-        if (threadIdx.x == 0) s_next = atomicAdd(p.queue, 1);
+        if (threadIdx.x == 0) s_item = atomicAdd(p.queue, 1ull);
         __syncthreads();
-        const int k = s_next;
+        const unsigned long long k = s_item;
         __syncthreads();
-        if (k >= p.nsys) break;
-        const int s = p.order[k];
-        if (!in_range(s, p.nsys, p.err)) continue;
-        const int64_t off = p.offsets[s];
-        const int ns = (int)(p.offsets[s + 1] - off);
-        if (ns <= 0) continue;
-        const float e = p.eps[s];
-        const float eps2s = e * e;
-        const f2 eps2 = pk(eps2s, eps2s);
-        const int npair = (ns + 1) >> 1;
-        // Equal masses throughout the system (the usual ensemble member)?
-        float mu = 0.0f;
-        if (in_range(off, p.ntot, p.err)) mu = p.mass[off];
-        bool same = true;
-        for (int b = threadIdx.x; b < ns; b += blockDim.x)
-            if (in_range(off + b, p.ntot, p.err)) same = same && p.mass[off + b] == mu;
-        const bool uni = __syncthreads_and(same) != 0;
-        load_system(sj, p, off, ns);
-        __syncthreads();
-        for (int64_t ev = 0; ev <= p.steps; ++ev) {
-            const float kick = (p.steps == 0) ? 0.0f : ((ev == 0 || ev == p.steps) ? 0.5f * p.dt : p.dt);
-            const bool drift = ev < p.steps;
-            for (int base = 0; base < ns; base += T * I) {
-                // Each warp takes only as many i-bodies per thread as it has
-                // left in this pass (slot k of lane l is body base + k*T + l),
-                // and a warp with none skips the pass: padding costs less than
-                // one warp's row of bodies per system, not up to T*I - 1.
-                const int lw = ns - base - 32 * (int)(threadIdx.x >> 5);
-                const int left = lw <= 0 ? 0 : (lw + T - 1) / T;
-                if (left == 0) {
-                } else if (POT || eps2s == 0.0f) {  // the self pair must be excluded
-                    if (uni)
-                        pass_dispatch<T, I, POT, true, true, U, JB>(left, sj, npair, ns, base, eps2, p, off, kick,
-                                                                    drift, mu);
-                    else
-                        pass_dispatch<T, I, POT, true, false, U, JB>(left, sj, npair, ns, base, eps2, p, off, kick,
-                                                                     drift, mu);
-                } else {
-                    if (uni)
-                        pass_dispatch<T, I, POT, false, true, U, JB>(left, sj, npair, ns, base, eps2, p, off, kick,
-                                                                     drift, mu);
-                    else
-                        pass_dispatch<T, I, POT, false, false, U, JB>(left, sj, npair, ns, base, eps2, p, off, kick,
-                                                                      drift, mu);
-                }
+        if (k >= nitems) break;
+        if ((int64_t)k < TL) {
+            // large system r of the order, lprefix[r] <= k < lprefix[r + 1]
+            int64_t lo = 0, hi = L;
+            while (hi - lo > 1) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (p.lprefix[mid] <= (int64_t)k)
+                    lo = mid;
+                else
+                    hi = mid;
             }
-            __syncthreads();
-            if (drift) {
-                load_system(sj, p, off, ns);  // the drifted positions of this step
-                __syncthreads();
-            }
+            const int s = p.order[lo];
+            if (!in_range(s, p.nsys, p.err)) continue;
+            run_large<T, POT, U, JB>(sj, p, s, (int)((int64_t)k - p.lprefix[lo]),
+                                     (int)(p.lprefix[lo + 1] - p.lprefix[lo]), ntot);
+        } else {
+            const int64_t r = L + ((int64_t)k - TL);
+            if (!in_range(r, p.nsys, p.err)) continue;
+            const int s = p.order[r];
+            if (!in_range(s, p.nsys, p.err)) continue;
+            run_small<T, I, POT, U, JB>(sj, p, s, ntot);
         }
+        __syncthreads();  // the shared image is reused by the next item
     }
+}
+
+// ---------------------------------------------------------------------------
+// Planning kernels.
+// ---------------------------------------------------------------------------
+// Sort key of a system: 255 - q, q = 128 + 4 e + (2 bits) for a large system
+// of 2^e * 1.xx bodies and q = 8 e + (3 bits) for a small one, so an ascending
+// sort puts the large systems first and then every system by size, descending,
+// in steps of 1/4 and 1/8 octave.  Empty and one-body systems go last.
+__device__ __forceinline__ unsigned size_key(int64_t ns, int cap) {
+    if (ns <= 1) return 255u;
+    const unsigned n = (unsigned)ns;
+    const int e = 31 - __clz(n);
+    const unsigned m = e >= 3 ? (n >> (e - 3)) & 7u : (n << (3 - e)) & 7u;
+    const unsigned q = ns > cap ? 128u + 4u * (unsigned)e + (m >> 1) : 8u * (unsigned)e + m;
+    return 255u - q;
+}
+
+// Checks the batch (offsets[0] == 0, sizes >= 0 and below 2^31, softenings
+// finite and >= 0), counts the large systems and writes every system's key.
+__global__ void __launch_bounds__(256) plan_keys_kernel(int64_t nsys, const int64_t* __restrict__ off,
+                                                        const float* __restrict__ eps, int cap,
+                                                        unsigned* __restrict__ key, int* __restrict__ val,
+                                                        int64_t* __restrict__ plan, int* err) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = off[s], b = off[s + 1];
+        const int64_t ns = b - a;
+        const float e = eps[s];
+        const bool bad = ns < 0 || ns > INT_MAX || !(isfinite(e) && e >= 0.0f) || (s == 0 && a != 0);
+        if (bad) {
+            atomicExch(reinterpret_cast<unsigned long long*>(plan + kPlanInvalid), 1ull);
+            atomicCAS(err, 0, kErrInvalid);
+        }
+        key[s] = size_key(bad ? 0 : ns, cap);
+        val[s] = (int)s;
+        if (!bad && ns > cap) atomicAdd(reinterpret_cast<unsigned long long*>(plan + kPlanLarge), 1ull);
+        if (s == nsys - 1) plan[kPlanBodies] = b;
+    }
+}
+
+// Workers of each large system (min(grid, its 2T-body chunks)) and their
+// prefix sums over the order; one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) plan_workers_kernel(const int* __restrict__ order,
+                                                            const int64_t* __restrict__ off, int64_t* plan,
+                                                            int64_t* __restrict__ lprefix, int grid, int chunk) {
+    __shared__ int64_t part[1024];
+    __shared__ int64_t carry;
+    if (plan[kPlanInvalid] != 0) return;
+    const int64_t L = plan[kPlanLarge];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        carry = 0;
+        lprefix[0] = 0;
+    }
+    __syncthreads();
+    for (int64_t base = 0; base < L; base += 1024) {
+        const int64_t r = base + tid;
+        int64_t wk = 0;
+        if (r < L) {
+            const int s = order[r];
+            const int64_t ns = off[s + 1] - off[s];
+            wk = min((int64_t)grid, (ns + chunk - 1) / chunk);
+        }
+        part[tid] = wk;
+        __syncthreads();
+        for (int d = 1; d < 1024; d <<= 1) {  // inclusive scan
+            const int64_t v = tid >= d ? part[tid - d] : 0;
+            __syncthreads();
+            part[tid] += v;
+            __syncthreads();
+        }
+        if (r < L) lprefix[r + 1] = carry + part[tid];
+        __syncthreads();
+        if (tid == 0) carry += part[1023];
+        __syncthreads();
+    }
+    if (tid == 0) plan[kPlanLargeItems] = carry;
 }
 
 typedef void (*BFn)(const BParams);
@@ -323,43 +668,144 @@ const BShapeEntry* bshapes() {
 }
 constexpr int kNumBShapes = 4;
 
+// Scratch layout (each area 256-byte aligned).
+struct BScratch {
+    int64_t* plan;               // kPlanWords
+    unsigned long long* queue;
+    unsigned* heartbeat;
+    unsigned* key_a;
+    unsigned* key_b;
+    int* val_a;
+    int* order;
+    int* hist;
+    int64_t* lprefix;
+    unsigned long long* sysbar;
+    size_t words_bytes;          // plan + queue + heartbeat, zeroed per call
+    size_t total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+BScratch carve(void* base, int64_t nsys) {
+    BScratch b;
+    const uintptr_t c = reinterpret_cast<uintptr_t>(base);
+    size_t o = 0;
+    b.plan = reinterpret_cast<int64_t*>(c + o);
+    b.queue = reinterpret_cast<unsigned long long*>(c + o + kPlanWords * 8);
+    b.heartbeat = reinterpret_cast<unsigned*>(c + o + kPlanWords * 8 + 8);
+    b.words_bytes = kPlanWords * 8 + 16;
+    o += align256(b.words_bytes);
+    b.key_a = reinterpret_cast<unsigned*>(c + o);
+    o += align256((size_t)nsys * 4);
+    b.key_b = reinterpret_cast<unsigned*>(c + o);
+    o += align256((size_t)nsys * 4);
+    b.val_a = reinterpret_cast<int*>(c + o);
+    o += align256((size_t)nsys * 4);
+    b.order = reinterpret_cast<int*>(c + o);
+    o += align256((size_t)nsys * 4);
+    b.hist = reinterpret_cast<int*>(c + o);
+    o += align256(sort_pass_hist_ints(nsys) * 4);
+    b.lprefix = reinterpret_cast<int64_t*>(c + o);
+    o += align256((size_t)(nsys + 1) * 8);
+    b.sysbar = reinterpret_cast<unsigned long long*>(c + o);
+    o += align256((size_t)nsys * 8);
+    b.total = o;
+    return b;
+}
+
 }  // namespace
 
 int batched_num_shapes() { return kNumBShapes; }
 BatchShape batched_shape(int k) { return bshapes()[k].shape; }
 
-size_t batched_smem_bytes(int max_ns) { return (size_t)((max_ns + 1) / 2) * 8 * sizeof(float); }
+size_t batched_smem_bytes(int cap) { return (size_t)((cap + 1) / 2) * 8 * sizeof(float); }
 
-cudaError_t batched_launch(int k, const BatchArgs& a, int num_sms, cudaStream_t st) {
+size_t batched_scratch_bytes(int64_t nsys) { return carve(nullptr, nsys).total; }
+
+int batched_max_cap() {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        optin = 48 * 1024;
+    }
+    const int bodies = (optin - 1024) / 16;  // leave room for the kernel's static shared memory
+    return bodies / 128 * 128;
+}
+
+cudaError_t batched_launch(int k, const BatchArgs& a, int num_sms, cudaStream_t st, int* launched) {
+    *launched = 0;
     const BShapeEntry& e = bshapes()[k];
     const int pot = a.pot != nullptr ? 1 : 0;
-    const size_t smem = std::max<size_t>(batched_smem_bytes(a.max_ns), 16);
+    const size_t smem = std::max<size_t>(batched_smem_bytes(a.cap), 16);
     cudaError_t err = cudaFuncSetAttribute(e.fn[pot], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int occ = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, e.fn[pot], e.shape.threads, smem);
     if (err != cudaSuccess) return err;
     if (occ < 1) return cudaErrorInvalidConfiguration;
+    // With large systems possible the grid is the full resident set (the
+    // launch is cooperative); otherwise at most one CTA per system.
+    const int64_t resident = (int64_t)num_sms * occ;
+    const int grid = (int)(a.coop ? resident : std::min<int64_t>(resident, std::max<int64_t>(a.nsys, 1)));
+    const BScratch sc = carve(a.scratch, a.nsys);
+
+    err = cudaMemsetAsync(sc.plan, 0, sc.words_bytes, st);
+    if (err != cudaSuccess) return err;
+    if (a.coop) {
+        err = cudaMemsetAsync(sc.sysbar, 0, (size_t)a.nsys * 8, st);
+        if (err != cudaSuccess) return err;
+    }
+    const int64_t kb = std::min<int64_t>((a.nsys + 255) / 256, (int64_t)num_sms * 8);
+    plan_keys_kernel<<<(unsigned)std::max<int64_t>(kb, 1), 256, 0, st>>>(a.nsys, a.offsets, a.eps, a.cap, sc.key_a,
+                                                                        sc.val_a, sc.plan, a.err);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    *launched += 1;
+    err = sort_pass(a.nsys, sc.key_a, sc.val_a, 0, sc.key_b, sc.order, sc.hist, st);
+    if (err != cudaSuccess) return err;
+    *launched += 3;
+    if (a.coop) {
+        plan_workers_kernel<<<1, 1024, 0, st>>>(sc.order, a.offsets, sc.plan, sc.lprefix, grid, 2 * e.shape.threads);
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+        *launched += 1;
+    }
+
     BParams p;
     p.nsys = a.nsys;
     p.offsets = a.offsets;
-    p.order = a.order;
-    p.queue = a.queue;
+    p.eps = a.eps;
+    p.order = sc.order;
+    p.plan = sc.plan;
+    p.lprefix = sc.lprefix;
+    p.queue = sc.queue;
+    p.sysbar = sc.sysbar;
+    p.heartbeat = sc.heartbeat;
     p.pos = a.pos;
     p.vel = a.vel;
     p.mass = a.mass;
-    p.eps = a.eps;
     p.acc = a.acc;
     p.pot = a.pot;
     p.dt = a.dt;
     p.steps = a.steps;
-    p.ntot = a.ntot;
+    p.cap = a.cap;
+    p.grid = grid;
     p.err = a.err;
-    const int64_t grid = std::min<int64_t>((int64_t)num_sms * occ, std::max<int64_t>(a.nsys, 1));
-    err = cudaMemsetAsync(a.queue, 0, sizeof(int), st);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)e.shape.threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = a.coop ? 1 : 0;
+    err = cudaLaunchKernelEx(&cfg, e.fn[pot], p);
     if (err != cudaSuccess) return err;
-    e.fn[pot]<<<(unsigned)grid, e.shape.threads, smem, st>>>(p);
-    return cudaGetLastError();
+    *launched += 1;
+    return cudaSuccess;
 }
 
 }  // namespace nbk

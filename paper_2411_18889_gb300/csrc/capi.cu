@@ -55,12 +55,17 @@ bool fault(const char* what) {
 std::atomic<int64_t> g_launches{0};
 std::atomic<bool> g_prof_on{false};
 std::mutex g_prof_mu;
+// Kernels timed by event pairs while profiling is on.
+enum ProfKind { PROF_FORCE = 0, PROF_PACK = 1, PROF_KICK = 2, PROF_KINDS = 3 };
 struct ProfPair {
     cudaEvent_t a, b;
+    int kind;
 };
 std::vector<ProfPair> g_prof_used, g_prof_free;
+double g_prof_ms[PROF_KINDS] = {};
+int64_t g_prof_n[PROF_KINDS] = {};
 
-bool prof_pair(ProfPair* out) {
+bool prof_pair(ProfPair* out, int kind = PROF_FORCE) {
     if (!g_prof_on.load()) return false;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     ProfPair p;
@@ -74,9 +79,37 @@ bool prof_pair(ProfPair* out) {
             return false;
         }
     }
+    p.kind = kind;
     g_prof_used.push_back(p);
     *out = p;
     return true;
+}
+
+// Wait for every recorded pair and add its time to its kind (caller holds g_prof_mu).
+cudaError_t prof_drain() {
+    for (auto& p : g_prof_used) {
+        cudaError_t e = cudaEventSynchronize(p.b);
+        if (e != cudaSuccess) return e;
+        float t = 0.0f;
+        e = cudaEventElapsedTime(&t, p.a, p.b);
+        if (e != cudaSuccess) return e;
+        g_prof_ms[p.kind] += t;
+        g_prof_n[p.kind] += 1;
+        g_prof_free.push_back(p);
+    }
+    g_prof_used.clear();
+    return cudaSuccess;
+}
+
+// A launch bracketed by an event pair of `kind` while profiling is on.
+template <typename F>
+cudaError_t timed(int kind, cudaStream_t st, F launch) {
+    ProfPair pp;
+    const bool on = prof_pair(&pp, kind);
+    if (on) (void)cudaEventRecord(pp.a, st);
+    const cudaError_t e = launch();
+    if (on) (void)cudaEventRecord(pp.b, st);
+    return e;
 }
 
 // Queue `launches` kernels' worth of accounting after a successful launch
@@ -136,8 +169,11 @@ enum BufId {
     B_RED,
     B_OUT9,
     B_ERR,
-    B_ORDER,
-    B_QUEUE,
+    B_BATCH,
+    B_VJX,
+    B_VJV,
+    B_VJM,
+    B_VJTAPE,
     B_VJ,
     B_VCENTRES,
     B_VPARTIAL,
@@ -698,27 +734,26 @@ static int leapfrog_issue(int64_t n, V* x, V* v, const float* m, double eps, dou
     if (f64 && fp.perm != nullptr) NB_CHECK(issue_order(fp, n, (const double*)x, st));  // order of the call
     NB_CHECK(issue_uniform(fp, n, m, st));
     count(1);
-    if (f64)
-        NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, (double*)x, nullptr, nullptr, m, 0.0, 0.0, plain, fp.jdup,
-                              fp.centres, st, fp.perm, fp.err));
-    else
-        NB_CUDA(nbk::pack_f32(n, fp.npad, (float*)x, nullptr, nullptr, m, 0.0f, 0.0f, fp.jdup, st));
+    NB_CUDA(timed(PROF_PACK, st, [&] {
+        return f64 ? nbk::pack_f64(n, fp.npad, fp.block, (double*)x, nullptr, nullptr, m, 0.0, 0.0, plain, fp.jdup,
+                                   fp.centres, st, fp.perm, fp.err)
+                   : nbk::pack_f32(n, fp.npad, (float*)x, nullptr, nullptr, m, 0.0f, 0.0f, fp.jdup, st);
+    }));
     NB_CHECK(run_force(fp, n, eps2, f64 && !plain, comp, a, nullptr, st));
     for (int64_t s = 0; s < steps; ++s) {
         const double kick = (s == 0) ? 0.5 * dt : dt;  // merged closing + opening half kicks
         count(1);
-        if (f64)
-            NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, (double*)x, (double*)v, a, m, kick, dt, plain, fp.jdup,
-                                  fp.centres, st, fp.perm, fp.err));
-        else
-            NB_CUDA(nbk::pack_f32(n, fp.npad, (float*)x, (float*)v, a, m, (float)kick, (float)dt, fp.jdup, st));
+        NB_CUDA(timed(PROF_PACK, st, [&] {
+            return f64 ? nbk::pack_f64(n, fp.npad, fp.block, (double*)x, (double*)v, a, m, kick, dt, plain, fp.jdup,
+                                       fp.centres, st, fp.perm, fp.err)
+                       : nbk::pack_f32(n, fp.npad, (float*)x, (float*)v, a, m, (float)kick, (float)dt, fp.jdup, st);
+        }));
         NB_CHECK(run_force(fp, n, eps2, f64 && !plain, comp, a, nullptr, st));
     }
     count(1);
-    if (f64)
-        NB_CUDA(nbk::kick_f64(n, (double*)v, a, 0.5 * dt, st));
-    else
-        NB_CUDA(nbk::kick_f32(n, (float*)v, a, 0.5f * (float)dt, st));
+    NB_CUDA(timed(PROF_KICK, st, [&] {
+        return f64 ? nbk::kick_f64(n, (double*)v, a, 0.5 * dt, st) : nbk::kick_f32(n, (float*)v, a, 0.5f * (float)dt, st);
+    }));
     return NBODY_OK;
 }
 
@@ -1094,10 +1129,10 @@ int nbody_leapfrog_record(int64_t n, double* pos, double* vel, const float* mass
     return NBODY_OK;
 }
 
-int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, double dt, int64_t steps, int64_t ckpt_every,
-                       const void* tape, const double* g_posT, const double* g_velT, double* g_pos0, double* g_vel0,
-                       double* g_mass, const nbody_opts* opts) {
-    NB_RANGE("nbody_leapfrog_vjp");
+int nbody_leapfrog_vjp_tape(int64_t n, const float* mass, double eps, double dt, int64_t steps, int64_t ckpt_every,
+                            const void* tape, const double* g_posT, const double* g_velT, double* g_pos0,
+                            double* g_vel0, double* g_mass, const nbody_opts* opts) {
+    NB_RANGE("nbody_leapfrog_vjp_tape");
     if (n < 0 || steps < 0 || ckpt_every < 1 || !finite_nonneg(eps) || !isfinite(dt)) return NBODY_EINVAL;
     if (n > 0 && (mass == nullptr || tape == nullptr || g_posT == nullptr || g_velT == nullptr ||
                   g_pos0 == nullptr || g_vel0 == nullptr || g_mass == nullptr))
@@ -1213,10 +1248,49 @@ int nbody_leapfrog_vjp(int64_t n, const float* mass, double eps, double dt, int6
     return sg.finish();
 }
 
-// Ragged batches: validate offsets and softenings on the host, order the
-// systems largest first, stage host arrays, one persistent launch.
+// The adjoint in one call from x(0), v(0): the forward run is recorded into
+// workspace copies of the state and a workspace tape, then swept.  Buffers of
+// its own (B_VJ*) hold those, so the staging inside the two calls it makes
+// cannot overwrite them.
+int nbody_leapfrog_vjp(int64_t n, const double* pos0, const double* vel0, const float* mass, double eps, double dt,
+                       int64_t steps, int64_t ckpt_every, const double* g_posT, const double* g_velT, double* g_pos0,
+                       double* g_vel0, double* g_mass, const nbody_opts* opts) {
+    NB_RANGE("nbody_leapfrog_vjp");
+    if (n < 0 || steps < 0 || ckpt_every < 1 || !finite_nonneg(eps) || !isfinite(dt)) return NBODY_EINVAL;
+    if (n > 0 && (pos0 == nullptr || vel0 == nullptr || mass == nullptr || g_posT == nullptr || g_velT == nullptr ||
+                  g_pos0 == nullptr || g_vel0 == nullptr || g_mass == nullptr))
+        return NBODY_EINVAL;
+    NB_CHECK(check_opts_only(opts));
+    if (n == 0) return NBODY_OK;
+    Ctx c;
+    NB_CHECK(begin(opts, &c));
+    cudaStream_t st = c.o.stream;
+    const size_t n3b = (size_t)n * 3 * sizeof(double);
+    const int64_t tb = nbody_tape_bytes(n, steps, ckpt_every);
+    void *px, *pv, *pm, *pt;
+    NB_CHECK(ensure(c.ws, B_VJX, n3b, &px));
+    NB_CHECK(ensure(c.ws, B_VJV, n3b, &pv));
+    NB_CHECK(ensure(c.ws, B_VJM, (size_t)n * sizeof(float), &pm));
+    NB_CHECK(ensure(c.ws, B_VJTAPE, (size_t)tb, &pt));
+    // cudaMemcpyDefault: the sources may be host (pageable or pinned) or device memory
+    NB_CUDA(cudaMemcpyAsync(px, pos0, n3b, cudaMemcpyDefault, st));
+    NB_CUDA(cudaMemcpyAsync(pv, vel0, n3b, cudaMemcpyDefault, st));
+    NB_CUDA(cudaMemcpyAsync(pm, mass, (size_t)n * sizeof(float), cudaMemcpyDefault, st));
+    NB_CHECK(nbody_leapfrog_record(n, (double*)px, (double*)pv, (const float*)pm, eps, dt, steps, ckpt_every, pt,
+                                   opts));
+    return nbody_leapfrog_vjp_tape(n, (const float*)pm, eps, dt, steps, ckpt_every, pt, g_posT, g_velT, g_pos0,
+                                   g_vel0, g_mass, opts);
+}
+
+// Ragged batches.  With the offsets in host memory the batch is checked on
+// the host (errors return before any work is queued) and its largest system
+// picks the kernel shape; with device offsets the checks run on the device
+// (a bad batch is skipped and nbody_last_device_error reports NBODY_EINVAL)
+// and shape 0 serves unless opts->config names another.  The order of the
+// systems and the split of the large ones are planned on the device in
+// either case, so a call on device arrays never waits for the GPU.
 static int batched_common(int64_t nsys, const int64_t* offsets, float* pos, float* vel, const float* mass,
-                          const float* eps, float* acc, float* pot, float dt, int64_t steps, const nbody_opts* opts,
+                          const float* eps, float* acc, float* pot, double dt, int64_t steps, const nbody_opts* opts,
                           bool leapfrog) {
     if (nsys < 0 || steps < 0 || !isfinite(dt)) return NBODY_EINVAL;
     if (nsys > 0 && (offsets == nullptr || pos == nullptr || mass == nullptr || eps == nullptr)) return NBODY_EINVAL;
@@ -1229,94 +1303,91 @@ static int batched_common(int64_t nsys, const int64_t* offsets, float* pos, floa
     Ctx c;
     NB_CHECK(begin(opts, &c));
     cudaStream_t st = c.o.stream;
-    // host copies of the offsets and softenings
-    std::vector<int64_t> off((size_t)nsys + 1);
-    std::vector<float> ep((size_t)nsys);
-    const bool off_host = is_host_ptr(offsets), eps_host = is_host_ptr(eps);
-    if (off_host) {
-        memcpy(off.data(), offsets, off.size() * sizeof(int64_t));
-    } else {
-        NB_CUDA(cudaMemcpyAsync(off.data(), offsets, off.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    int64_t max_ns = -1, ntot = -1;  // -1: not known on the host
+    if (is_host_ptr(offsets)) {
+        if (offsets[0] != 0) return NBODY_EINVAL;
+        max_ns = 0;
+        for (int64_t s = 0; s < nsys; ++s) {
+            const int64_t ns = offsets[s + 1] - offsets[s];
+            if (ns < 0 || ns > INT32_MAX) return NBODY_EINVAL;
+            max_ns = ns > max_ns ? ns : max_ns;
+        }
+        ntot = offsets[nsys];
+        if (is_host_ptr(eps))
+            for (int64_t s = 0; s < nsys; ++s)
+                if (!(isfinite(eps[s]) && eps[s] >= 0.0f)) return NBODY_EINVAL;
+        if (ntot == 0) return NBODY_OK;
     }
-    if (eps_host) {
-        memcpy(ep.data(), eps, ep.size() * sizeof(float));
-    } else {
-        NB_CUDA(cudaMemcpyAsync(ep.data(), eps, ep.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
+    const bool host_data = is_host_ptr(pos) || (leapfrog && is_host_ptr(vel)) || is_host_ptr(mass) ||
+                           (!leapfrog && is_host_ptr(acc)) || (!leapfrog && pot != nullptr && is_host_ptr(pot));
+    if (host_data && ntot < 0) {
+        // host arrays are copied in and out, so their size must be known: read
+        // the batch's body count back (the call is synchronous anyway)
+        NB_CUDA(cudaMemcpyAsync(&ntot, offsets + nsys, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        NB_CUDA(cudaStreamSynchronize(st));
+        if (ntot < 0) return NBODY_EINVAL;
+        if (ntot == 0) return NBODY_OK;
     }
-    if (!off_host || !eps_host) NB_CUDA(cudaStreamSynchronize(st));
-    if (off[0] != 0) return NBODY_EINVAL;
-    int64_t max_ns = 0;
-    for (int64_t s = 0; s < nsys; ++s) {
-        const int64_t ns = off[s + 1] - off[s];
-        if (ns < 0 || ns > NBODY_BATCH_MAX_N) return NBODY_EINVAL;
-        if (!(isfinite(ep[s]) && ep[s] >= 0.0f)) return NBODY_EINVAL;
-        max_ns = ns > max_ns ? ns : max_ns;
-    }
-    const int64_t ntot = off[nsys];
-    if (ntot == 0) return NBODY_OK;
-    std::vector<int> order((size_t)nsys);
-    for (int64_t s = 0; s < nsys; ++s) order[s] = (int)s;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
-
+    const size_t nb = ntot > 0 ? (size_t)ntot : 0;
     Staging sg(c.ws);
-    sg.add(offsets, off.size() * sizeof(int64_t), true, false);
-    sg.add(pos, (size_t)ntot * 3 * sizeof(float), true, leapfrog);
-    sg.add(vel, leapfrog ? (size_t)ntot * 3 * sizeof(float) : 0, leapfrog, leapfrog);
-    sg.add(mass, (size_t)ntot * sizeof(float), true, false);
-    sg.add(eps, ep.size() * sizeof(float), true, false);
-    sg.add(acc, leapfrog ? 0 : (size_t)ntot * 3 * sizeof(float), false, !leapfrog);
-    sg.add(pot, (leapfrog || pot == nullptr) ? 0 : (size_t)ntot * sizeof(float), false, !leapfrog);
+    sg.add(offsets, (size_t)(nsys + 1) * sizeof(int64_t), true, false);
+    sg.add(pos, nb * 3 * sizeof(float), true, leapfrog);
+    sg.add(vel, leapfrog ? nb * 3 * sizeof(float) : 0, leapfrog, leapfrog);
+    sg.add(mass, nb * sizeof(float), true, false);
+    sg.add(eps, (size_t)nsys * sizeof(float), true, false);
+    sg.add(acc, leapfrog ? 0 : nb * 3 * sizeof(float), false, !leapfrog);
+    sg.add(pot, (leapfrog || pot == nullptr) ? 0 : nb * sizeof(float), false, !leapfrog);
     NB_CHECK(sg.prepare());
-    void *po, *pq, *pe;
-    NB_CHECK(ensure(c.ws, B_ORDER, order.size() * sizeof(int), &po));
-    NB_CHECK(ensure(c.ws, B_QUEUE, sizeof(int), &pq));
-    NB_CUDA(cudaMemcpyAsync(po, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-    if (fault("launch")) return NBODY_ECUDA;
+    const int shape = c.o.config >= 0 ? c.o.config : (max_ns >= 0 ? tuned_shape(2, max_ns, 0) : 0);
+    const int maxcap = nbk::batched_max_cap();
     nbk::BatchArgs a;
+    if (max_ns >= 0 && max_ns <= maxcap) {  // every system fits one CTA's image
+        a.cap = max_ns > 2 ? (int)max_ns : 2;
+        a.coop = false;
+    } else {  // sizes unknown here, or some system too large for one image
+        a.cap = shape == 0 ? maxcap : std::min(maxcap, 4096);
+        a.coop = true;
+    }
+    void *pb, *pe;
+    NB_CHECK(ensure(c.ws, B_BATCH, nbk::batched_scratch_bytes(nsys), &pb));
+    NB_CHECK(ensure(c.ws, B_ERR, sizeof(int), &pe));
+    if (fault("launch")) return NBODY_ECUDA;
     a.nsys = nsys;
     a.offsets = (const int64_t*)sg.dev(0);
-    a.order = (const int*)po;
-    a.queue = (int*)pq;
     a.pos = (float*)sg.dev(1);
     a.vel = leapfrog ? (float*)sg.dev(2) : nullptr;
     a.mass = (const float*)sg.dev(3);
     a.eps = (const float*)sg.dev(4);
     a.acc = leapfrog ? nullptr : (float*)sg.dev(5);
     a.pot = (leapfrog || pot == nullptr) ? nullptr : (float*)sg.dev(6);
-    a.dt = dt;
+    a.dt = (float)dt;
     a.steps = leapfrog ? steps : 0;
-    a.max_ns = (int)max_ns;
-    a.ntot = ntot;
-    NB_CHECK(ensure(c.ws, B_ERR, sizeof(int), &pe));
+    a.scratch = pb;
     a.err = (int*)pe;
-    const int shape = c.o.config >= 0 ? c.o.config : tuned_shape(2, max_ns, 0);
-    // The order array is uploaded on every call (above); the graph holds the
-    // queue reset and the persistent launch.
     const std::vector<uint64_t> key = {2, (uint64_t)nsys, (uint64_t)(uintptr_t)a.offsets,
-                                       (uint64_t)(uintptr_t)a.order, (uint64_t)(uintptr_t)a.queue,
                                        (uint64_t)(uintptr_t)a.pos, (uint64_t)(uintptr_t)a.vel,
                                        (uint64_t)(uintptr_t)a.mass, (uint64_t)(uintptr_t)a.eps,
                                        (uint64_t)(uintptr_t)a.acc, (uint64_t)(uintptr_t)a.pot, bits_of(dt),
-                                       (uint64_t)a.steps, (uint64_t)max_ns, (uint64_t)ntot, (uint64_t)shape};
+                                       (uint64_t)a.steps, (uint64_t)shape, (uint64_t)a.cap, (uint64_t)a.coop,
+                                       (uint64_t)(uintptr_t)pb, (uint64_t)(uintptr_t)pe};
     NB_CHECK(run_graphed(c, key, true, [&](cudaStream_t s) {
-        count(1);
-        NB_CUDA(nbk::batched_launch(shape, a, c.sms, s));
+        int launched = 0;
+        const cudaError_t e = nbk::batched_launch(shape, a, c.sms, s, &launched);
+        count(launched);
+        NB_CUDA(e);
         return NBODY_OK;
     }));
-    // (a pageable-to-device copy has read `order` before cudaMemcpyAsync returns)
     return sg.finish();
 }
 
 int nbody_accel_batched(int64_t nsys, const int64_t* offsets, const float* pos, const float* mass, const float* eps,
                         float* acc, float* pot, const nbody_opts* opts) {
     NB_RANGE("nbody_accel_batched");
-    return batched_common(nsys, offsets, const_cast<float*>(pos), nullptr, mass, eps, acc, pot, 0.0f, 0, opts,
-                          false);
+    return batched_common(nsys, offsets, const_cast<float*>(pos), nullptr, mass, eps, acc, pot, 0.0, 0, opts, false);
 }
 
 int nbody_leapfrog_batched(int64_t nsys, const int64_t* offsets, float* pos, float* vel, const float* mass,
-                           const float* eps, float dt, int64_t steps, const nbody_opts* opts) {
+                           const float* eps, double dt, int64_t steps, const nbody_opts* opts) {
     NB_RANGE("nbody_leapfrog_batched");
     return batched_common(nsys, offsets, pos, vel, mass, eps, nullptr, nullptr, dt, steps, opts, true);
 }
@@ -1384,7 +1455,9 @@ int nbody_last_device_error(void) {
         int flag = 0;
         NB_CUDA(cudaMemcpy(&flag, w->buf[B_ERR].p, sizeof(int), cudaMemcpyDeviceToHost));
         if (flag != 0) {
-            result = flag == 2 ? NBODY_EBOUNDS : NBODY_ETIMEOUT;
+            result = flag == nbk::kErrBounds ? NBODY_EBOUNDS
+                     : flag == nbk::kErrInvalid ? NBODY_EINVAL
+                                                : NBODY_ETIMEOUT;
             NB_CUDA(cudaMemset(w->buf[B_ERR].p, 0, sizeof(int)));
         }
     }
@@ -1438,20 +1511,23 @@ void nbody_profile_enable(int on) { g_prof_on.store(on != 0); }
 
 int nbody_profile_read(double* force_ms, int64_t* force_launches, int64_t* all_launches) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    double ms = 0.0;
-    int64_t k = 0;
-    for (auto& p : g_prof_used) {
-        NB_CUDA(cudaEventSynchronize(p.b));
-        float t = 0.0f;
-        NB_CUDA(cudaEventElapsedTime(&t, p.a, p.b));
-        ms += t;
-        ++k;
-        g_prof_free.push_back(p);
-    }
-    g_prof_used.clear();
-    if (force_ms) *force_ms = ms;
-    if (force_launches) *force_launches = k;
+    NB_CUDA(prof_drain());
+    if (force_ms) *force_ms = g_prof_ms[PROF_FORCE];
+    if (force_launches) *force_launches = g_prof_n[PROF_FORCE];
+    g_prof_ms[PROF_FORCE] = 0.0;
+    g_prof_n[PROF_FORCE] = 0;
     if (all_launches) *all_launches = g_launches.exchange(0);
+    return NBODY_OK;
+}
+
+int nbody_profile_read_kind(int kind, double* ms, int64_t* launches) {
+    if (kind < 0 || kind >= PROF_KINDS) return NBODY_EINVAL;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    NB_CUDA(prof_drain());
+    if (ms) *ms = g_prof_ms[kind];
+    if (launches) *launches = g_prof_n[kind];
+    g_prof_ms[kind] = 0.0;
+    g_prof_n[kind] = 0;
     return NBODY_OK;
 }
 

@@ -140,6 +140,7 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 constexpr uint64_t kWaitLimitNs = 4000000000ull;
 constexpr int kErrTimeout = 1;
 constexpr int kErrBounds = 2;
+constexpr int kErrInvalid = 3;  // a batch's offsets or softenings, checked on the device
 
 // Checked builds (-DNBODY_CHECKS, the stand-in for a memory sanitizer): every
 // computed global index is tested before use; an index out of range records
@@ -273,24 +274,29 @@ struct BatchShape {
 struct BatchArgs {
     int64_t nsys;
     const int64_t* offsets;  // device [nsys+1]
-    const int* order;        // device [nsys], largest system first
-    int* queue;              // device counter (zeroed by the launch)
+    const float* eps;        // device [nsys]
     float* pos;
     float* vel;
     const float* mass;
-    const float* eps;
     float* acc;
     float* pot;
     float dt;
     int64_t steps;  // 0: force only (acc, pot); > 0: leapfrog in place
-    int max_ns;     // largest system (sizes the shared-memory image)
-    int64_t ntot;   // bodies over all systems
+    int cap;        // bodies of the shared-memory image; larger systems take the multi-CTA path
+    bool coop;      // a system may exceed cap: cooperative launch, full resident grid
+    void* scratch;  // batched_scratch_bytes(nsys) bytes (plan, order, barriers)
     int* err;       // error word
 };
 int batched_num_shapes();
 BatchShape batched_shape(int k);
-size_t batched_smem_bytes(int max_ns);
-cudaError_t batched_launch(int k, const BatchArgs& a, int num_sms, cudaStream_t st);
+size_t batched_smem_bytes(int cap);
+size_t batched_scratch_bytes(int64_t nsys);
+// Largest shared-memory image (bodies, a multiple of 128) a CTA of the
+// current device can hold.
+int batched_max_cap();
+// Queues the planning kernels and the persistent kernel; *launched gets the
+// number of kernels queued.
+cudaError_t batched_launch(int k, const BatchArgs& a, int num_sms, cudaStream_t st, int* launched);
 
 // ---- reverse mode (vjp.cu) ----
 struct VjpShape {

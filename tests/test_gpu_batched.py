@@ -128,30 +128,66 @@ def test_leapfrog_batched_matches_oracle(nb, oracle_mod):
             assert abs(eg - er) <= 1e-5 * abs(e0), s
 
 
+# Systems larger than one CTA's shared-memory image (about 14,000 bodies for
+# shape 0, 4096 for the others when the sizes are not known on the host) are
+# split over several CTAs that stream the bodies in tiles.
+LARGE = {0: 20011, 1: 6000, 2: 9001, 3: 5000}
+
+
+@pytest.mark.parametrize("device_offsets", [False, True])
 @pytest.mark.parametrize("shape", range(4))
-def test_largest_system_every_shape(nb, oracle_mod, shape):
-    """A system of NBODY_BATCH_MAX_N (12288) bodies, the largest a batch may
-    hold (192 KiB of shared memory), beside small ones, with every kernel shape;
-    one more body is rejected."""
+def test_large_member_every_shape(nb, oracle_mod, shape, device_offsets):
+    """A batch with a member too large for one CTA's image beside small ones
+    (and, with eps = 0 on the large one, its masked self pairs), every kernel
+    shape, offsets in host and in device memory; sampled bodies of the large
+    member and every body of the small ones against the oracle."""
     import torch
-    nmax = 12288
-    off, pos, vel, mass, eps = make_batch([5, nmax, 70], 61 + shape)
-    acc, pot = gpu_accel_batched(nb, off, pos, mass, eps, config=shape)
+    big = LARGE[shape] if device_offsets or shape == 0 else 20011
+    sizes = [5, big, 70, 1, 2049]
+    off, pos, vel, mass, eps = make_batch(sizes, 61 + shape)
+    eps[1] = 0.0 if shape % 2 else eps[1]
+    n = pos.shape[0]
+    acc = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    pot = torch.empty((n,), dtype=torch.float32, device="cuda")
+    O = t(off, np.int64) if device_offsets else off
+    nb.nbody_accel_batched(O, t(pos, np.float32), t(mass, np.float32), t(eps, np.float32), acc, pot, config=shape)
+    torch.cuda.synchronize()
     assert nb.nbody_last_device_error() == 0
-    for s, pick in ((0, None), (1, ni.subsample(nmax, 512, 62)), (2, None)):
+    acc, pot = acc.cpu().numpy(), pot.cpu().numpy()
+    for s in range(len(sizes)):
         a, b = off[s], off[s + 1]
-        idx = np.arange(b - a) if pick is None else pick
+        idx = ni.subsample(b - a, 512, 62) if b - a > 4096 else np.arange(b - a)
         ra, rp = oracle_mod.accel_subset(pos[a:b], mass[a:b], eps[s], idx)
+        if b - a == 1:
+            assert np.all(acc[a:b] == 0) and np.all(pot[a:b] == 0)
+            continue
         e = rel(acc[a:b][idx], ra)
-        assert np.median(e) <= ACC_MED and e.max() <= ACC_MAX, (shape, s, np.median(e), e.max())
-        assert rel(pot[a:b][idx], rp).max() <= POT_MAX, (shape, s)
-    o = np.asarray([0, 10, 10 + nmax + 1], dtype=np.int64)
-    n = int(o[-1])
-    z = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
-    with pytest.raises(nb.NbodyError) as ei:
-        nb.nbody_accel_batched(o, z, torch.ones(n, dtype=torch.float32, device="cuda"),
-                               torch.full((2,), 0.1, dtype=torch.float32, device="cuda"), torch.empty_like(z))
-    assert ei.value.code == nb.NBODY_EINVAL
+        tol = (ACC_MED, ACC_MAX, POT_MAX) if eps[s] > 0 else (1e-5, 1e-3, 1e-4)
+        assert np.median(e) <= tol[0] and e.max() <= tol[1], (shape, s, np.median(e), e.max())
+        assert rel(pot[a:b][idx], rp).max() <= tol[2], (shape, s)
+
+
+def test_large_member_leapfrog(nb, oracle_mod):
+    """The leapfrog of a batch whose first member (20011 bodies) is split over
+    several CTAs meeting at barriers between the phases of each step."""
+    import torch
+    sizes = [20011, 300, 1500]
+    off, pos, vel, mass, eps = make_batch(sizes, 81)
+    P, V = t(pos, np.float32), t(vel, np.float32)
+    dt, steps = 2.0 ** -8, 3
+    nb.nbody_leapfrog_batched(t(off, np.int64), P, V, t(mass, np.float32), t(eps, np.float32), dt, steps)
+    torch.cuda.synchronize()
+    assert nb.nbody_last_device_error() == 0
+    pg, vg = P.cpu().numpy().astype(np.float64), V.cpu().numpy().astype(np.float64)
+    for s in range(len(sizes)):
+        a, b = off[s], off[s + 1]
+        pr, vr, _ = oracle_mod.leapfrog(pos[a:b], vel[a:b], mass[a:b], eps[s], dt, steps)
+        assert np.abs(pg[a:b] - pr).max() <= 2e-5, s
+        assert np.abs(vg[a:b] - vr).max() <= 2e-4, s
+        e0 = oracle_mod.energy(pos[a:b], vel[a:b], mass[a:b], eps[s])["E"]
+        er = oracle_mod.energy(pr, vr, mass[a:b], eps[s])["E"]
+        eg = oracle_mod.energy(pg[a:b], vg[a:b], mass[a:b], eps[s])["E"]
+        assert abs(eg - er) <= 1e-5 * abs(e0), s
 
 
 def test_batched_deterministic_and_host_arrays(nb):
@@ -165,19 +201,56 @@ def test_batched_deterministic_and_host_arrays(nb):
     assert np.array_equal(acc_h, a1) and np.array_equal(pot_h, p1)
 
 
-def test_batched_rejects_bad_offsets(nb):
+BAD_BATCHES = ([1, 5, 10], [0, 6, 5], [0, 10])
+
+
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_batched_rejects_bad_offsets(nb, where):
+    """Offsets and softenings in host memory are checked before any work is
+    queued (NBODY_EINVAL); in device memory on the device: the call returns,
+    the batch is skipped (nothing written) and nbody_last_device_error reports
+    NBODY_EINVAL."""
     import torch
     pos = torch.zeros((10, 3), dtype=torch.float32, device="cuda")
     m = torch.ones(10, dtype=torch.float32, device="cuda")
-    acc = torch.empty((10, 3), dtype=torch.float32, device="cuda")
-    for off in ([1, 5, 10], [0, 6, 5], [0, 10]):
+    for off in BAD_BATCHES:
+        acc = torch.full((10, 3), 7.0, dtype=torch.float32, device="cuda")
         o = np.asarray(off, dtype=np.int64)
-        e = torch.full((len(off) - 1,), 0.1, dtype=torch.float32, device="cuda")
-        if off == [0, 10]:
-            e = torch.full((1,), -0.1, dtype=torch.float32, device="cuda")  # negative softening
-        with pytest.raises(nb.NbodyError) as ei:
-            nb.nbody_accel_batched(o, pos, m, e, acc)
-        assert ei.value.code == nb.NBODY_EINVAL
+        e = np.full(len(off) - 1, -0.1 if off == [0, 10] else 0.1, dtype=np.float32)  # [0, 10]: negative softening
+        if where == "device":
+            e = t(e, np.float32)
+        if where == "host":
+            with pytest.raises(nb.NbodyError) as ei:
+                nb.nbody_accel_batched(o, pos, m, e, acc)
+            assert ei.value.code == nb.NBODY_EINVAL
+        else:
+            nb.nbody_accel_batched(t(o, np.int64), pos, m, e, acc)
+            assert nb.nbody_last_device_error() == nb.NBODY_EINVAL
+            assert bool((acc == 7.0).all())
+    assert nb.nbody_last_device_error() == 0  # the flag was cleared
+
+
+def test_batched_call_is_asynchronous(nb):
+    """With device arrays a batched call queues its work and returns: an event
+    recorded right after a long call (the ragged workload, 64 steps, about
+    0.2 s of GPU time) is not complete when the call returns.  Its results
+    equal those of the same call with the offsets in host memory."""
+    import torch
+    off, pos, vel, mass, eps = ni.ragged_batch()
+    O, M, E = t(off, np.int64), t(mass, np.float32), t(eps, np.float32)
+    P1, V1 = t(pos, np.float32), t(vel, np.float32)
+    P2, V2 = P1.clone(), V1.clone()
+    torch.cuda.synchronize()
+    nb.nbody_leapfrog_batched(O, P1, V1, M, E, 2.0 ** -8, 64)
+    ev = torch.cuda.Event()
+    ev.record()
+    pending = not ev.query()
+    torch.cuda.synchronize()
+    assert pending
+    nb.nbody_leapfrog_batched(off, P2, V2, M, E, 2.0 ** -8, 64)  # host offsets
+    torch.cuda.synchronize()
+    assert nb.nbody_last_device_error() == 0
+    assert torch.equal(P1, P2) and torch.equal(V1, V2)
 
 
 def test_ragged_workload_sampled_systems(nb, oracle_mod):

@@ -149,7 +149,8 @@ def test_leapfrog_in_bounds(nb, checked_lib, precision):
 @pytest.mark.parametrize("shape", range(4))
 def test_batched_in_bounds(nb, checked_lib, shape):
     import torch
-    sizes = [1, 2, 3, 0, 63, 64, 65, 127, 511, 513, 1000, 2049, 5, 0, 777]
+    # 15001 bodies: more than one CTA's image, so split over several CTAs
+    sizes = [1, 2, 3, 0, 63, 64, 65, 127, 511, 513, 1000, 2049, 5, 0, 777, 15001]
     P, V, M = [], [], []
     for s, n in enumerate(sizes):
         p, v, m = ni.plummer(n, 920 + s)
@@ -210,7 +211,7 @@ def test_adjoint_in_bounds(nb, checked_lib):
         g0 = torch.empty((n, 3), dtype=torch.float64, device="cuda")
         h0 = torch.empty((n, 3), dtype=torch.float64, device="cuda")
         gm = torch.empty((n,), dtype=torch.float64, device="cuda")
-        nb.nbody_leapfrog_vjp(M, 2.0 ** -7, 2.0 ** -8, K, ck, tape, t(gx, np.float64), t(gv, np.float64), g0, h0, gm)
+        nb.nbody_leapfrog_vjp_tape(M, 2.0 ** -7, 2.0 ** -8, K, ck, tape, t(gx, np.float64), t(gv, np.float64), g0, h0, gm)
         return P.cpu().numpy(), g0.cpu().numpy(), h0.cpu().numpy(), gm.cpu().numpy()
 
     both(nb, checked_lib, run)

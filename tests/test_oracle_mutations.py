@@ -17,9 +17,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 MUTANTS = {
     "force_exponent_1": ("w = mass[j] * rinv * rinv * rinv", "w = mass[j] * rinv * rinv"),
-    "self_term_kept_with_softening": ("if (j == i) continue;", "if (j == i && eps2 == 0.0) continue;"),
+    "self_term_kept_with_softening": ("if (j == i) continue;\n        const double dx",
+                                      "if (j == i && eps2 == 0.0) continue;\n        const double dx"),
     "potential_sign": ("p -= mass[j] * rinv;", "p += mass[j] * rinv;"),
-    "transposed_coordinate": ("pos[3 * j + 1] - yi", "pos[3 * j + 0] - yi"),
+    "transposed_coordinate": ("const double dy = pos[3 * j + 1] - yi", "const double dy = pos[3 * j + 0] - yi"),
     "softening_dropped": ("const double s = dx * dx + dy * dy + dz * dz + eps2;\n        const double rinv = 1.0 / sqrt(s);\n        const double w = mass[j]",
                           "const double s = dx * dx + dy * dy + dz * dz;\n        const double rinv = 1.0 / sqrt(s);\n        const double w = mass[j]"),
     "full_kick_instead_of_half": ("oracle_accel(n, pos, mass, eps, a, NULL);\n    const double h = 0.5 * dt;",
