@@ -300,3 +300,30 @@ def test_equal_mass_loop_matches_general_loop(nb, precision):
     assert np.median(eg / np.linalg.norm(g1, axis=1)) <= 1e-5, np.median(eg / np.linalg.norm(g1, axis=1))
     assert np.median(np.abs(h0 - h1) / np.abs(h1)) <= 1e-5
     assert nb.nbody_last_device_error() == 0
+
+
+@pytest.mark.parametrize("accumulate", ["compensated", "fp32"])
+@pytest.mark.parametrize("n,masses,eps", [(1000, "equal", 2.0 ** -7), (4096, "loguniform", 2.0 ** -7),
+                                          (20011, "equal", 2.0 ** -8)])
+def test_fp32_path_at_least_as_accurate_as_listing(nb, oracle_mod, n, masses, eps, accumulate):
+    """The plain FP32 path (nbody_accel_f32) against the oracle's correctly
+    rounded FP32 restatement of Listing 4: per body, both are compared with the
+    FP64 oracle on the same FP32 inputs, and the GPU's error must be no larger
+    than the listing's own (median) and at most 1.5 times its largest (max).
+    The kernel replaces the listing's exact 1/sqrt by the MUFU approximation
+    but sums in shorter FP32 runs (per j-tile, folded by Kahan summation, or
+    split across the stream-K slices), so it is expected to be more accurate,
+    not only within a loose bound; a slip in its per-pair arithmetic would show
+    as an error well above the listing's."""
+    p, _, m = ni.plummer(n, 300 + n, masses=masses)
+    p = p.astype(np.float32).astype(np.float64)
+    m = m.astype(np.float32).astype(np.float64)
+    eps = float(np.float32(eps))
+    idx = np.arange(n) if n <= 4096 else ni.subsample(n, 2048, 5)
+    ra, _ = oracle_mod.accel_subset(p, m, eps, idx)
+    la, _ = oracle_mod.accel_listing_f32(p, m, eps, idx=idx)
+    kw = {} if accumulate == "compensated" else {"accumulate": nb.NBODY_ACC_FP32}
+    acc, _ = gpu_accel(nb, "f32", p, m.astype(np.float32), eps, with_pot=False, **kw)
+    eg, el = rel_err(acc[idx], ra), rel_err(la, ra)
+    assert np.median(eg) <= np.median(el), (np.median(eg), np.median(el))
+    assert eg.max() <= 1.5 * el.max(), (eg.max(), el.max())
