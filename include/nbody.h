@@ -316,7 +316,7 @@ NBODY_API int nbody_selftest_wait(double limit_seconds, const nbody_opts* opts);
  * anything (no cudaMalloc, cudaFree or allocating library routine).
  *
  * Its scratch is one fixed array in the library's device module,
- * 24,449,280 bytes (23.3 MiB), which every GPU that loads the library holds
+ * 24,453,376 bytes (23.3 MiB), which every GPU that loads the library holds
  * until the process exits.  Limits: n <= NBODY_NOALLOC_MAX_N (65536); larger n returns
  * NBODY_EINVAL without queuing work.  If the device needs more partial-sum
  * scratch than the array holds (a GPU with more SMs than it was sized for),
@@ -351,8 +351,8 @@ NBODY_API int nbody_accel_noalloc(int64_t n, const double* pos, const float* mas
  * The leapfrog's integrator kernels are timed the same way:
  * nbody_profile_read_kind(kind, &ms, &launches) returns and resets the summed
  * device time and launch count of kind 0 (force kernel), 1 (pack kernel:
- * kick, drift and the packed j-array) or 2 (closing kick kernel);
- * NBODY_EINVAL for another kind. */
+ * kick, drift and the packed j-array), 2 (closing kick kernel) or 3 (force
+ * VJP kernel); NBODY_EINVAL for another kind. */
 NBODY_API void nbody_profile_enable(int on);
 NBODY_API int nbody_profile_read(double* force_ms, int64_t* force_launches, int64_t* all_launches);
 NBODY_API int nbody_profile_read_kind(int kind, double* ms, int64_t* launches);

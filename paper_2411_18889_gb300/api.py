@@ -278,12 +278,13 @@ def nbody_profile_read():
     return ms.value, k.value, allk.value
 
 
-PROFILE_KINDS = {"force": 0, "pack": 1, "kick": 2}
+PROFILE_KINDS = {"force": 0, "pack": 1, "kick": 2, "vjp": 3}
 
 
 def nbody_profile_read_kind(kind):
     """(ms, launches) of one timed kernel kind since its last read: "force", "pack" (kick, drift
-    and packed j-array of a leapfrog step) or "kick" (the closing half kick)."""
+    and packed j-array of a leapfrog step), "kick" (the closing half kick) or "vjp" (the force
+    VJP kernel)."""
     ms, k = ctypes.c_double(), ctypes.c_int64()
     check(load().nbody_profile_read_kind(PROFILE_KINDS[kind], ctypes.byref(ms), ctypes.byref(k)),
           "nbody_profile_read_kind")

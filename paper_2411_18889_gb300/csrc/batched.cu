@@ -722,15 +722,20 @@ size_t batched_smem_bytes(int cap) { return (size_t)((cap + 1) / 2) * 8 * sizeof
 
 size_t batched_scratch_bytes(int64_t nsys) { return carve(nullptr, nsys).total; }
 
-int batched_max_cap() {
-    int dev = 0, optin = 0;
+int batched_max_cap(int k) {
+    // The image of shape k may take as much shared memory as still lets the
+    // CTAs its registers allow share an SM; never more than one CTA may hold.
+    const BShapeEntry& e = bshapes()[k];
+    int dev = 0, optin = 48 * 1024, per_sm = 48 * 1024, occ = 1;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, e.fn[0], e.shape.threads, 0) != cudaSuccess) {
         (void)cudaGetLastError();
-        optin = 48 * 1024;
     }
-    const int bodies = (optin - 1024) / 16;  // leave room for the kernel's static shared memory
-    return bodies / 128 * 128;
+    occ = std::max(occ, 1);
+    const int per_cta = std::min(optin, per_sm / occ) - 1024;  // room for static shared memory and the runtime's share
+    return std::max(128, per_cta / 16 / 128 * 128);
 }
 
 cudaError_t batched_launch(int k, const BatchArgs& a, int num_sms, cudaStream_t st, int* launched) {

@@ -56,7 +56,7 @@ std::atomic<int64_t> g_launches{0};
 std::atomic<bool> g_prof_on{false};
 std::mutex g_prof_mu;
 // Kernels timed by event pairs while profiling is on.
-enum ProfKind { PROF_FORCE = 0, PROF_PACK = 1, PROF_KICK = 2, PROF_KINDS = 3 };
+enum ProfKind { PROF_FORCE = 0, PROF_PACK = 1, PROF_KICK = 2, PROF_VJP = 3, PROF_KINDS = 4 };
 struct ProfPair {
     cudaEvent_t a, b;
     int kind;
@@ -559,7 +559,7 @@ int plan_force(Workspace* ws, int64_t n, int shape, int num_sms, ForcePlan* fp) 
     void* p;
     NB_CHECK(ensure(ws, B_JDUP, (size_t)fp->npad * nbk::kJdupFloats * sizeof(float), &p));
     fp->jdup = (float*)p;
-    NB_CHECK(ensure(ws, B_CENTRES, (size_t)nblk * 3 * sizeof(double), &p));
+    NB_CHECK(ensure(ws, B_CENTRES, nbk::pack_centre_doubles(fp->npad, fp->block) * sizeof(double), &p));
     fp->centres = (double*)p;
     NB_CHECK(ensure(ws, B_PARTIAL, nbk::force_partial_doubles(shape, num_sms) * sizeof(double), &p));
     fp->partial = (double*)p;
@@ -568,8 +568,10 @@ int plan_force(Workspace* ws, int64_t n, int shape, int num_sms, ForcePlan* fp) 
     return NBODY_OK;
 }
 
+// defer (optional): leave the split i-blocks' partial sums to the pack kernel
+// that consumes this evaluation (no fixup launch); see nbk::SplitSums.
 int run_force(const ForcePlan& fp, int64_t n, float eps2, bool mixed, int summation, float* acc, float* pot,
-              cudaStream_t st) {
+              cudaStream_t st, nbk::SplitSums* defer = nullptr) {
     if (fault("launch")) return NBODY_ECUDA;
     nbk::ForceArgs a;
     a.jdup = fp.jdup;
@@ -588,7 +590,7 @@ int run_force(const ForcePlan& fp, int64_t n, float eps2, bool mixed, int summat
     const bool timed = prof_pair(&pp);
     int launched = 0;
     cudaError_t e = nbk::force_launch(fp.shape, a, fp.num_sms, st, &launched, timed ? pp.a : nullptr,
-                                      timed ? pp.b : nullptr);
+                                      timed ? pp.b : nullptr, defer);
     count(launched);
     NB_CUDA(e);
     return NBODY_OK;
@@ -625,7 +627,7 @@ int accel_f64_dev(Ctx& c, int64_t n, const double* pos, const float* mass, doubl
     }
     NB_CHECK(plan_uniform(c.ws, &fp));
     NB_CHECK(issue_uniform(fp, n, mass, c.o.stream));
-    count(1);
+    count(nbk::pack_f64_launches(plain));
     NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, const_cast<double*>(pos), nullptr, nullptr, mass, 0.0, 0.0, plain,
                           fp.jdup, fp.centres, c.o.stream, fp.perm, fp.err));
     return run_force(fp, n, (float)(eps * eps), !plain, summation_mode(c.o.accumulate), acc, pot,
@@ -733,22 +735,26 @@ static int leapfrog_issue(int64_t n, V* x, V* v, const float* m, double eps, dou
     const float eps2 = f64 ? (float)(eps * eps) : (float)eps * (float)eps;
     if (f64 && fp.perm != nullptr) NB_CHECK(issue_order(fp, n, (const double*)x, st));  // order of the call
     NB_CHECK(issue_uniform(fp, n, m, st));
-    count(1);
+    count(f64 ? nbk::pack_f64_launches(plain) : 1);
     NB_CUDA(timed(PROF_PACK, st, [&] {
         return f64 ? nbk::pack_f64(n, fp.npad, fp.block, (double*)x, nullptr, nullptr, m, 0.0, 0.0, plain, fp.jdup,
                                    fp.centres, st, fp.perm, fp.err)
                    : nbk::pack_f32(n, fp.npad, (float*)x, nullptr, nullptr, m, 0.0f, 0.0f, fp.jdup, st);
     }));
-    NB_CHECK(run_force(fp, n, eps2, f64 && !plain, comp, a, nullptr, st));
+    // Every evaluation but the last is consumed by the next step's pack
+    // kernel, which adds the split i-blocks' partial sums itself.
+    nbk::SplitSums ss;
+    NB_CHECK(run_force(fp, n, eps2, f64 && !plain, comp, a, nullptr, st, steps > 0 ? &ss : nullptr));
     for (int64_t s = 0; s < steps; ++s) {
         const double kick = (s == 0) ? 0.5 * dt : dt;  // merged closing + opening half kicks
-        count(1);
+        count(f64 ? nbk::pack_f64_launches(plain) : 1);
         NB_CUDA(timed(PROF_PACK, st, [&] {
             return f64 ? nbk::pack_f64(n, fp.npad, fp.block, (double*)x, (double*)v, a, m, kick, dt, plain, fp.jdup,
-                                       fp.centres, st, fp.perm, fp.err)
-                       : nbk::pack_f32(n, fp.npad, (float*)x, (float*)v, a, m, (float)kick, (float)dt, fp.jdup, st);
+                                       fp.centres, st, fp.perm, fp.err, &ss)
+                       : nbk::pack_f32(n, fp.npad, (float*)x, (float*)v, a, m, (float)kick, (float)dt, fp.jdup, st,
+                                       &ss);
         }));
-        NB_CHECK(run_force(fp, n, eps2, f64 && !plain, comp, a, nullptr, st));
+        NB_CHECK(run_force(fp, n, eps2, f64 && !plain, comp, a, nullptr, st, s + 1 < steps ? &ss : nullptr));
     }
     count(1);
     NB_CUDA(timed(PROF_KICK, st, [&] {
@@ -920,11 +926,11 @@ static int accel_ij_common(int64_t ni, const void* ipos, int64_t nj, const void*
     const int64_t nipad = niblk * fp.block;
     void *pi, *pc;
     NB_CHECK(ensure(c.ws, B_IPACK, (size_t)nipad * nbk::kJdupFloats * sizeof(float), &pi));
-    NB_CHECK(ensure(c.ws, B_ICENTRES, (size_t)niblk * 3 * sizeof(double), &pc));
+    NB_CHECK(ensure(c.ws, B_ICENTRES, nbk::pack_centre_doubles(nipad, fp.block) * sizeof(double), &pc));
     const bool plain = !f64 || c.o.precision == NBODY_PREC_PLAIN;
     // sinks need no mass: pack them with the sources' first mass pointer unused
     if (f64) {
-        count(2);
+        count(2 * nbk::pack_f64_launches(plain));
         NB_CUDA(nbk::pack_f64(ni, nipad, fp.block, (double*)sg.dev(0), nullptr, nullptr, nullptr, 0.0, 0.0, plain,
                               (float*)pi, (double*)pc, st));
         NB_CUDA(nbk::pack_f64(nj, fp.npad, fp.block, (double*)sg.dev(1), nullptr, nullptr, (const float*)sg.dev(2),
@@ -995,7 +1001,7 @@ static int plan_vjp(Workspace* ws, int64_t n, int shape, int num_sms, VjpPlan* v
     void* p;
     NB_CHECK(ensure(ws, B_VJ, (size_t)vp->npad * nbk::vjp_floats_per_body() * sizeof(float), &p));
     vp->jv = (float*)p;
-    NB_CHECK(ensure(ws, B_VCENTRES, (size_t)nblk * 3 * sizeof(double), &p));
+    NB_CHECK(ensure(ws, B_VCENTRES, nbk::pack_centre_doubles(vp->npad, vp->block) * sizeof(double), &p));
     vp->centres = (double*)p;
     NB_CHECK(ensure(ws, B_VPARTIAL, nbk::vjp_partial_doubles(shape, num_sms) * sizeof(double), &p));
     vp->partial = (double*)p;
@@ -1004,8 +1010,9 @@ static int plan_vjp(Workspace* ws, int64_t n, int shape, int num_sms, VjpPlan* v
     return NBODY_OK;
 }
 
+// defer (optional): leave the split blocks' partials to the next pack_vjp.
 static int run_vjp(const VjpPlan& vp, int64_t n, float eps2, bool mixed, bool has_mu, float* g_pos, float* g_mass,
-            int num_sms, cudaStream_t st) {
+            int num_sms, cudaStream_t st, nbk::SplitSums* defer = nullptr) {
     if (fault("launch")) return NBODY_ECUDA;
     nbk::VjpArgs a;
     a.jv = vp.jv;
@@ -1020,7 +1027,10 @@ static int run_vjp(const VjpPlan& vp, int64_t n, float eps2, bool mixed, bool ha
     a.err = vp.err;
     a.uni = vp.uni;
     int launched = 0;
-    cudaError_t e = nbk::vjp_launch(vp.shape, a, num_sms, st, &launched);
+    ProfPair pp;
+    const bool timed_vjp = prof_pair(&pp, PROF_VJP);
+    cudaError_t e = nbk::vjp_launch(vp.shape, a, num_sms, st, &launched, timed_vjp ? pp.a : nullptr,
+                                    timed_vjp ? pp.b : nullptr, defer);
     count(launched);
     NB_CUDA(e);
     return NBODY_OK;
@@ -1055,7 +1065,7 @@ int nbody_accel_vjp(int64_t n, const double* pos, const float* mass, double eps,
         count(1);
         NB_CUDA(nbk::uniform_mass_flag(n, (const float*)sg.dev(1), vp.uni, c.o.stream));
     }
-    count(1);
+    count(2);
     NB_CUDA(nbk::pack_vjp(n, vp.npad, vp.block, (const double*)sg.dev(0), (const float*)sg.dev(1),
                           (const float*)sg.dev(2), nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, 1.0,
                           g_pot ? (const float*)sg.dev(3) : nullptr, plain, vp.jv, vp.centres, c.o.stream));
@@ -1108,20 +1118,21 @@ int nbody_leapfrog_record(int64_t n, double* pos, double* vel, const float* mass
     }
     NB_CHECK(plan_uniform(c.ws, &fp));
     NB_CHECK(issue_uniform(fp, n, mass, st));
-    count(1);
+    count(nbk::pack_f64_launches(plain));
     NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, pos, nullptr, nullptr, mass, 0.0, 0.0, plain, fp.jdup, fp.centres,
                           st, fp.perm, fp.err));
-    NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, st));
+    nbk::SplitSums ss;  // as nbody_leapfrog: the next pack adds the split blocks' partials
+    NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, st, &ss));
     for (int64_t s = 0; s < steps; ++s) {
         const bool ck = (s % ckpt_every) == 0;
         double* slot = tp + (size_t)(s / ckpt_every) * 2 * n * 3;
         if (ck) NB_CUDA(cudaMemcpyAsync(slot, pos, n3b, cudaMemcpyDeviceToDevice, st));
         const double kick = (s == 0) ? 0.5 * dt : dt;
-        count(1);
+        count(nbk::pack_f64_launches(plain));
         NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, pos, vel, a, mass, kick, dt, plain, fp.jdup, fp.centres, st,
-                              fp.perm, fp.err));
+                              fp.perm, fp.err, &ss));
         if (ck) NB_CUDA(cudaMemcpyAsync(slot + (size_t)n * 3, vel, n3b, cudaMemcpyDeviceToDevice, st));
-        NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, st));
+        NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, st, s + 1 < steps ? &ss : nullptr));
     }
     count(1);
     NB_CUDA(nbk::kick_f64(n, vel, a, 0.5 * dt, st));
@@ -1199,14 +1210,15 @@ int nbody_leapfrog_vjp_tape(int64_t n, const float* mass, double eps, double dt,
         double* Xs = X + (size_t)(seg & 1) * segd;
         NB_CUDA(cudaMemcpyAsync(Xs, slot, n3b, cudaMemcpyDeviceToDevice, aux));
         if (c1 - c0 > 1) NB_CUDA(cudaMemcpyAsync(v, slot + (size_t)n * 3, n3b, cudaMemcpyDeviceToDevice, aux));
+        nbk::SplitSums ss;  // each replayed force is consumed by the next pack, as in the recorded run
         for (int64_t k = c0 + 1; k < c1; ++k) {
             double* xk = Xs + (size_t)(k - c0) * n * 3;
             NB_CUDA(cudaMemcpyAsync(xk, xk - (size_t)n * 3, n3b, cudaMemcpyDeviceToDevice, aux));
             // x_k = x_{k-1} + dt v_{k-1/2}; v_{k-1/2} = v_{k-3/2} + dt a(x_{k-1}) for k > c0 + 1
-            count(1);
+            count(nbk::pack_f64_launches(plain));
             NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, xk, v, k > c0 + 1 ? a : nullptr, mass,
-                                  k > c0 + 1 ? dt : 0.0, dt, plain, fp.jdup, fp.centres, aux, fp.perm, fp.err));
-            if (k + 1 < c1) NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, aux));
+                                  k > c0 + 1 ? dt : 0.0, dt, plain, fp.jdup, fp.centres, aux, fp.perm, fp.err, &ss));
+            if (k + 1 < c1) NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, aux, &ss));
         }
         NB_CUDA(cudaEventRecord(ev_rep[seg & 1], aux));
         return NBODY_OK;
@@ -1219,11 +1231,13 @@ int nbody_leapfrog_vjp_tape(int64_t n, const float* mass, double eps, double dt,
     NB_CHECK(replay(nck - 1));
     if (nck >= 2) NB_CHECK(replay(nck - 2));
 
-    // v_K = v_{K-1/2} + h a(x_K)
-    count(1);
+    // v_K = v_{K-1/2} + h a(x_K).  Every VJP but the last is consumed by the
+    // next pack_vjp, which adds the split blocks' partial sums itself.
+    nbk::SplitSums ss;
+    count(2);
     NB_CUDA(nbk::pack_vjp(n, vp.npad, vp.block, xK, mass, nullptr, lamv, lamx, nullptr, nullptr, gm_acc, 0.0, h,
                           nullptr, plain, vp.jv, vp.centres, st));
-    NB_CHECK(run_vjp(vp, n, eps2, !plain, false, g, gm, c.sms, st));
+    NB_CHECK(run_vjp(vp, n, eps2, !plain, false, g, gm, c.sms, st, &ss));
     for (int64_t seg = nck - 1; seg >= 0; --seg) {
         const int64_t c0 = seg * ckpt_every;
         const int64_t c1 = (c0 + ckpt_every < steps) ? c0 + ckpt_every : steps;
@@ -1232,10 +1246,10 @@ int nbody_leapfrog_vjp_tape(int64_t n, const float* mass, double eps, double dt,
         // reverse over the segment
         for (int64_t s = c1 - 1; s >= c0; --s) {
             const double kappa = (s == 0) ? h : dt;
-            count(1);
+            count(2);
             NB_CUDA(nbk::pack_vjp(n, vp.npad, vp.block, Xs + (size_t)(s - c0) * n * 3, mass, nullptr, lamv, lamx,
-                                  g, gm, gm_acc, dt, kappa, nullptr, plain, vp.jv, vp.centres, st));
-            NB_CHECK(run_vjp(vp, n, eps2, !plain, false, g, gm, c.sms, st));
+                                  g, gm, gm_acc, dt, kappa, nullptr, plain, vp.jv, vp.centres, st, &ss));
+            NB_CHECK(run_vjp(vp, n, eps2, !plain, false, g, gm, c.sms, st, s > 0 ? &ss : nullptr));
         }
         NB_CUDA(cudaEventRecord(ev_sw[seg & 1], st));
         if (seg >= 2) {
@@ -1339,13 +1353,13 @@ static int batched_common(int64_t nsys, const int64_t* offsets, float* pos, floa
     sg.add(pot, (leapfrog || pot == nullptr) ? 0 : nb * sizeof(float), false, !leapfrog);
     NB_CHECK(sg.prepare());
     const int shape = c.o.config >= 0 ? c.o.config : (max_ns >= 0 ? tuned_shape(2, max_ns, 0) : 0);
-    const int maxcap = nbk::batched_max_cap();
+    const int maxcap = nbk::batched_max_cap(shape);
     nbk::BatchArgs a;
     if (max_ns >= 0 && max_ns <= maxcap) {  // every system fits one CTA's image
         a.cap = max_ns > 2 ? (int)max_ns : 2;
         a.coop = false;
     } else {  // sizes unknown here, or some system too large for one image
-        a.cap = shape == 0 ? maxcap : std::min(maxcap, 4096);
+        a.cap = maxcap;
         a.coop = true;
     }
     void *pb, *pe;

@@ -8,14 +8,17 @@
 // of FP32 peak with three CTAs per SM and 66 % with two.
 //
 // Decomposition.  Bodies are grouped in i-blocks ("cells") of
-// block = 2 * IP * T bodies; the j-range is cut into tiles of J bodies.  The
-// work is the grid of units (i-block, j-tile), flattened i-block-major, and a
-// persistent grid of P CTAs takes equal contiguous slices of it ("stream-K"):
-// CTA c owns units [c*U/P, (c+1)*U/P).  Every SM therefore gets the same
-// number of pair interactions whatever n is, with no tail wave.  A CTA that
-// covers a whole i-block writes the result; the i-blocks cut by a slice
-// boundary get per-CTA partial sums that a small fixup kernel adds in CTA
-// order (deterministic, no atomics).
+// block = 2 * IP * T bodies; the j-range is cut into tiles of J bodies, and
+// each tile into granules of 32 j-bodies.  The work is the grid of granules
+// (i-block, 32 j-bodies), flattened i-block-major, and a persistent grid of P
+// CTAs takes equal contiguous slices of it ("stream-K"): CTA c owns granules
+// [c*U/P, (c+1)*U/P), so every CTA gets the same number of pair interactions
+// to within one granule whatever n is, with no tail wave (with whole tiles as
+// the unit, N = 16384 gave CTAs 6 or 7 tiles each: a 14 % spread).  The first
+// and last tile of a slice may be used in part.  A CTA that covers a whole
+// i-block writes the result; the i-blocks cut by a slice boundary get per-CTA
+// partial sums that a small fixup kernel adds in CTA order (deterministic, no
+// atomics).
 //
 // Inside a CTA.  Each thread holds IP packed pairs of i-bodies in registers:
 // pair q holds bodies 2q*T + t and (2q+1)*T + t of the i-block.  j-tiles
@@ -35,7 +38,9 @@
 //
 // Self term.  The diagonal tiles (j-tile inside the thread's own i-block) run
 // a masked variant that zeroes the pair whose j equals i, so j = i is excluded
-// exactly (Eq. 1) and eps = 0 is valid for distinct positions.
+// exactly (Eq. 1) and eps = 0 is valid for distinct positions.  Without the
+// potential and with eps > 0 the mask is not needed (the pair's difference
+// vector is exactly zero) and every tile takes the unmasked loop.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -55,8 +60,8 @@ struct KParams {
     float eps2;
     int64_t n;              // sinks
     int64_t nblk;
-    int64_t ntile;  // j-tiles over the padded array
-    int64_t units;  // nblk * ntile
+    int64_t gpb;    // granules per i-block row (npad / kGranule)
+    int64_t units;  // granules in all: nblk * gpb
     int64_t nctas;
     float* acc;
     float* pot;
@@ -79,14 +84,18 @@ __device__ __forceinline__ void kahan_add(f2& sum, f2& comp, f2 term) {
 // UNI: every source has the same mass; the pair weight leaves m_j out (11
 // instead of 12 FP32 operations per interaction) and the caller scales the
 // sums by that mass.
-template <int T, int IP, int J, int UNROLL, bool POT, bool DIAG, int MODE, int WF, bool UNI>
+// FULL: the whole tile (compile-time bounds); else j-bodies [jlo, jhi) of it
+// (multiples of the granule).
+template <int T, int IP, int J, int UNROLL, bool POT, bool DIAG, int MODE, int WF, bool UNI, bool FULL>
 __device__ __forceinline__ void tile_pass(const unsigned char* tile, const f2 (&xi)[IP], const f2 (&yi)[IP],
                                           const f2 (&zi)[IP], f2 eps2, f2 (&ax)[IP], f2 (&ay)[IP], f2 (&az)[IP],
                                           f2 (&ap)[IP], f2 (&kx)[IP], f2 (&ky)[IP], f2 (&kz)[IP], f2 (&kp)[IP],
-                                          int jl0, int tid) {
+                                          int jl0, int tid, int jlo, int jhi) {
     const ulonglong2* tj = reinterpret_cast<const ulonglong2*>(tile);
+    const int lo = FULL ? 0 : jlo;
+    const int hi = FULL ? J : jhi;
 #pragma unroll UNROLL
-    for (int j = 0; j < J; ++j) {
+    for (int j = lo; j < hi; ++j) {
         const ulonglong2 A = tj[2 * j];
         const ulonglong2 B = tj[2 * j + 1];
         const f2 xj = A.x, yj = A.y, zj = B.x, mj = B.y;
@@ -157,8 +166,12 @@ __device__ __forceinline__ void force_body(const KParams& p) {
 
     const int tid = threadIdx.x;
     const int64_t cta = blockIdx.x;
-    const int64_t u_begin = cta * p.units / p.nctas;
+    constexpr int64_t GPT = J / kGranule;  // granules per j-tile
+    static_assert(J % kGranule == 0, "a j-tile is a whole number of granules");
+    const int64_t u_begin = cta * p.units / p.nctas;  // this CTA's granules [u_begin, u_end)
     const int64_t u_end = (cta + 1) * p.units / p.nctas;
+    // end of the segment (the part of one j-tile inside the slice) starting at granule g
+    auto seg_end = [&](int64_t g) { return min(u_end, (g / GPT + 1) * GPT); };
     unsigned char* tiles = smem;
     f2* xsave = reinterpret_cast<f2*>(smem + 2 * TILE_BYTES);  // MIXED: [IP][3][T]
 
@@ -169,15 +182,23 @@ __device__ __forceinline__ void force_body(const KParams& p) {
     }
     __syncthreads();
 
-    auto issue = [&](int s, int64_t unit) {
-        int64_t tile = unit % p.ntile;
-        if (!in_range(tile, p.ntile, p.err)) tile = 0;
+    // the j-tile of the segment starting at granule g (the whole tile is copied)
+    auto issue = [&](int s, int64_t g) {
+        int64_t tile = (g % p.gpb) / GPT;
+        if (!in_range(tile, p.gpb / GPT, p.err)) tile = 0;
         mbar_expect_tx(&bar[s], TILE_BYTES);
         bulk_g2s(tiles + s * TILE_BYTES, p.jdup + tile * (int64_t)J * kJdupFloats, TILE_BYTES, &bar[s]);
     };
-    if (tid == 0) {
-        if (u_begin < u_end) issue(0, u_begin);
-        if (u_begin + 1 < u_end) issue(1, u_begin + 1);
+    int64_t g_issued = u_begin;  // start of the last segment issued (thread 0's view)
+    int in_flight = 0;           // segments issued and not yet consumed (thread 0's view)
+    if (tid == 0 && u_begin < u_end) {
+        issue(0, u_begin);
+        in_flight = 1;
+        if (seg_end(u_begin) < u_end) {
+            g_issued = seg_end(u_begin);
+            issue(1, g_issued);
+            in_flight = 2;
+        }
     }
 
     const f2 eps2 = pk(p.eps2, p.eps2);
@@ -190,9 +211,9 @@ __device__ __forceinline__ void force_body(const KParams& p) {
     bool failed = false;
 
     while (u < u_end) {
-        const int64_t b = u / p.ntile;
-        const int64_t t0 = u - b * p.ntile;
-        const int64_t t1 = min(p.ntile, t0 + (u_end - u));
+        const int64_t b = u / p.gpb;
+        const int64_t ub0 = u;                              // this CTA's first granule of block b
+        const int64_t ub1 = min(u_end, (b + 1) * p.gpb);  // and its end
         const int64_t base = b * C;
 
         f2 xi[IP], yi[IP], zi[IP];
@@ -222,7 +243,11 @@ __device__ __forceinline__ void force_body(const KParams& p) {
         }
         int64_t cur_cell = p.self ? b : -1;  // i-offsets start relative to cell b's own centre
 
-        for (int64_t tt = t0; tt < t1; ++tt, ++u) {
+        while (u < ub1) {
+            const int64_t ue = seg_end(u);  // tiles never straddle i-block rows (gpb is a multiple of GPT)
+            const int64_t tt = (u % p.gpb) / GPT;
+            const int jlo = (int)(u % GPT) * kGranule, jhi = jlo + (int)(ue - u) * kGranule;
+            const bool whole = jlo == 0 && jhi == J;
             const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u, kWaitLimitNs);
             if (__syncthreads_or(!ok)) {
                 failed = true;
@@ -248,21 +273,30 @@ __device__ __forceinline__ void force_body(const KParams& p) {
                 }
             }
             const unsigned char* tile = tiles + s * TILE_BYTES;
-            if (p.self && cell == b) {
-                if (UNIMODE == 1 || (UNIMODE == 2 && uni))
-                    tile_pass<T, IP, J, UNROLL, POT, true, KAHAN, WF, true>(tile, xi, yi, zi, eps2, ax, ay, az, ap, cx,
-                                                                        cy, cz, cp, (int)(tt * J - base), tid);
-                else
-                    tile_pass<T, IP, J, UNROLL, POT, true, KAHAN, WF, false>(tile, xi, yi, zi, eps2, ax, ay, az, ap,
-                                                                         cx, cy, cz, cp, (int)(tt * J - base), tid);
+            // The self pair needs the mask only for the potential (it would
+            // add m_i/eps) or eps == 0 (0 * inf); otherwise its difference
+            // vector is exactly zero (both sides are the same packed entry
+            // relative to the same centre) and it adds exactly 0.
+            const bool diag = p.self && cell == b && (POT || p.eps2 == 0.0f);
+            const bool unil = UNIMODE == 1 || (UNIMODE == 2 && uni);
+            const int jl0 = diag ? (int)(tt * J - base) : 0;
+#define NBK_TILE(DG, UN, FL)                                                                                       \
+    tile_pass<T, IP, J, UNROLL, POT, DG, KAHAN, WF, UN, FL>(tile, xi, yi, zi, eps2, ax, ay, az, ap, cx, cy, cz, cp, \
+                                                            jl0, tid, jlo, jhi)
+            if (whole) {
+                if (diag) {
+                    if (unil) NBK_TILE(true, true, true); else NBK_TILE(true, false, true);
+                } else {
+                    if (unil) NBK_TILE(false, true, true); else NBK_TILE(false, false, true);
+                }
             } else {
-                if (UNIMODE == 1 || (UNIMODE == 2 && uni))
-                    tile_pass<T, IP, J, UNROLL, POT, false, KAHAN, WF, true>(tile, xi, yi, zi, eps2, ax, ay, az, ap,
-                                                                         cx, cy, cz, cp, 0, tid);
-                else
-                    tile_pass<T, IP, J, UNROLL, POT, false, KAHAN, WF, false>(tile, xi, yi, zi, eps2, ax, ay, az, ap,
-                                                                          cx, cy, cz, cp, 0, tid);
+                if (diag) {
+                    if (unil) NBK_TILE(true, true, false); else NBK_TILE(true, false, false);
+                } else {
+                    if (unil) NBK_TILE(false, true, false); else NBK_TILE(false, false, false);
+                }
             }
+#undef NBK_TILE
             if (KAHAN == 1) {
 #pragma unroll
                 for (int q = 0; q < IP; ++q) {
@@ -273,14 +307,23 @@ __device__ __forceinline__ void force_body(const KParams& p) {
                 }
             }
             __syncthreads();  // every thread is done with stage s
-            if (tid == 0 && u + 2 < u_end) issue(s, u + 2);
+            if (tid == 0) {
+                --in_flight;
+                const int64_t gn = seg_end(g_issued);  // the segment after the last one issued
+                if (gn < u_end) {
+                    g_issued = gn;
+                    issue(s, gn);
+                    ++in_flight;
+                }
+            }
             s ^= 1;
+            u = ue;
         }
         if (failed) break;
 
         // ---- results of i-block b from this CTA's slice ----
-        const bool full = (t0 == 0 && t1 == p.ntile);
-        const int slot = (b == u_begin / p.ntile) ? 0 : 1;
+        const bool full = (ub0 == b * p.gpb && ub1 == (b + 1) * p.gpb);
+        const int slot = (b == u_begin / p.gpb) ? 0 : 1;
 #pragma unroll
         for (int q = 0; q < IP; ++q) {
             float v[2][4];
@@ -340,8 +383,7 @@ __device__ __forceinline__ void force_body(const KParams& p) {
         if (tid == 0) {
             atomicExch(p.err, kErrTimeout);
             // Let copies still in flight land before shared memory goes away.
-            const int64_t inflight = (u_end - u) < 2 ? (u_end - u) : 2;
-            for (int k = 0; k < inflight; ++k) {
+            for (int k = 0; k < in_flight; ++k) {
                 const int st = (s + k) & 1;
                 (void)mbar_wait_bounded(&bar[st], (parity >> st) & 1u, kWaitLimitNs / 4);
             }
@@ -371,33 +413,22 @@ __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
 // return at once.
 __global__ void fixup_kernel(const KParams p, int C, int pot_on) {
     const int64_t b = blockIdx.x;
-    const int64_t u0 = b * p.ntile, u1 = u0 + p.ntile - 1;
-    const int64_t c_lo = ((u0 + 1) * p.nctas - 1) / p.units;
-    const int64_t c_hi = ((u1 + 1) * p.nctas - 1) / p.units;
+    int64_t c_lo, c_hi;
+    int slot_lo;
+    split_ctas(b, p.gpb, p.units, p.nctas, &c_lo, &c_hi, &slot_lo);
     if (c_lo == c_hi) return;
-    // Every CTA after c_lo starts its slice inside block b (partial slot 0);
-    // c_lo does only if its slice starts exactly at the block's first unit.
-    const int slot_lo = (c_lo * p.units / p.nctas == u0) ? 0 : 1;
     for (int lb = blockIdx.y * blockDim.x + threadIdx.x; lb < C; lb += gridDim.y * blockDim.x) {
         const int64_t g = b * C + lb;
         if (g >= p.n) break;
-        double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0;
-        for (int64_t c = c_lo; c <= c_hi; ++c) {
-            const int slot = c == c_lo ? slot_lo : 0;
-            const int64_t pi = (c * 2 + slot) * C + lb;
-            if (!in_range(pi, p.nctas * 2 * C, p.err)) continue;
-            const double4_16a v = reinterpret_cast<const double4_16a*>(p.partial)[pi];
-            sx += v.x;
-            sy += v.y;
-            sz += v.z;
-            sp += v.w;
-        }
+        if (!in_range((c_hi * 2) * C + lb, p.nctas * 2 * C, p.err)) continue;
+        double s4[4];
+        split_sum(p.partial, C, b, c_lo, c_hi, slot_lo, lb, s4);
         const int64_t o = p.perm != nullptr ? (int64_t)p.perm[g] : g;
         if (!in_range(o, p.n, p.err)) continue;
-        p.acc[3 * o + 0] = (float)sx;
-        p.acc[3 * o + 1] = (float)sy;
-        p.acc[3 * o + 2] = (float)sz;
-        if (pot_on) p.pot[o] = -(float)sp;
+        p.acc[3 * o + 0] = (float)s4[0];
+        p.acc[3 * o + 1] = (float)s4[1];
+        p.acc[3 * o + 2] = (float)s4[2];
+        if (pot_on) p.pot[o] = -(float)s4[3];
     }
 }
 
@@ -536,7 +567,7 @@ size_t force_partial_doubles(int k, int num_sms) {
     return (size_t)num_sms * 8u * 2u * (size_t)s.block * 4u;
 }
 
-cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t ntile, int64_t nctas, int block, const double* partial,
+cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t gpb, int64_t nctas, int block, const double* partial,
                         float* out3, float* out1, cudaStream_t st, const int* perm, int* err) {
     KParams p;
     p.jdup = nullptr;
@@ -548,8 +579,8 @@ cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t ntile, int64_t nctas, i
     p.eps2 = 0.0f;
     p.n = n;
     p.nblk = nblk;
-    p.ntile = ntile;
-    p.units = nblk * ntile;
+    p.gpb = gpb;
+    p.units = nblk * gpb;
     p.nctas = nctas;
     p.acc = out3;
     p.pot = out1;
@@ -564,13 +595,13 @@ cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t ntile, int64_t nctas, i
 size_t force_partial_doubles_for(int k, bool pot, bool mixed, bool compensated, int64_t npad, int num_sms) {
     const ShapeEntry& e = shapes()[k];
     const int occ = std::min(occupancy(k, pot ? 1 : 0, mixed ? 1 : 0, compensated ? 1 : 0), e.cap);  // mode 0 or 1
-    const int64_t units = (npad / e.shape.block) * (npad / e.jt[mixed ? 1 : 0]);
+    const int64_t units = (npad / e.shape.block) * (npad / kGranule);
     const int64_t nctas = std::min<int64_t>((int64_t)num_sms * occ, units);
     return (size_t)nctas * 2u * (size_t)e.shape.block * 4u;
 }
 
 cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st, int* launched, cudaEvent_t ev0,
-                         cudaEvent_t ev1) {
+                         cudaEvent_t ev1, SplitSums* defer) {
     const ShapeEntry& e = shapes()[k];
     const int C = e.shape.block;
     const int pot = a.pot != nullptr, mixed = a.centres != nullptr, kahan = a.summation;
@@ -584,8 +615,8 @@ cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st
     p.eps2 = a.eps2;
     p.n = a.n;
     p.nblk = (a.ipack != nullptr ? a.nipad : a.npad) / C;
-    p.ntile = a.npad / e.jt[mixed];
-    p.units = p.nblk * p.ntile;
+    p.gpb = a.npad / kGranule;
+    p.units = p.nblk * p.gpb;
     int occ = occupancy(k, pot, mixed, kahan);
     occ = std::min(occ, e.cap);
     p.nctas = std::min<int64_t>((int64_t)num_sms * occ, p.units);
@@ -602,6 +633,14 @@ cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st
     if (err != cudaSuccess) return err;
     *launched = 1;
     if (ev1 != nullptr) cudaEventRecord(ev1, st);
+    if (defer != nullptr) {  // the pack kernel that consumes these accelerations adds the partials
+        defer->partial = p.nctas > 1 ? p.partial : nullptr;
+        defer->units = p.units;
+        defer->nctas = p.nctas;
+        defer->gpb = p.gpb;
+        defer->block = C;
+        return cudaSuccess;
+    }
     if (p.nctas > 1) {  // a single CTA covers every i-block whole
         fixup_kernel<<<dim3((unsigned)p.nblk, (unsigned)((C + 255) / 256)), 256, 0, st>>>(p, C, pot);
         err = cudaGetLastError();

@@ -23,6 +23,14 @@ namespace nbk {
 constexpr float kPadPos = 1.0e15f;
 constexpr int kJdupFloats = 8;
 
+// Work split of the all-pairs kernels: the (i-block, j) plane is cut into
+// granules of kGranule consecutive j-bodies of one i-block row, and CTA c of
+// a persistent grid of P takes granules [c*U/P, (c+1)*U/P) of the U in all
+// (i-block-major): every CTA gets the same number of pair interactions to
+// within one granule, whatever n and P are.  j-tiles are whole multiples of
+// a granule, so a CTA's first and last tiles may be used in part.
+constexpr int kGranule = 32;
+
 // ---------------------------------------------------------------------------
 // Packed FP32 pairs (PTX f32x2 arithmetic, sm_100 and later).  A pair is a
 // 64-bit register holding (lo, hi); every op is round-to-nearest with
@@ -225,11 +233,24 @@ struct ForceArgs {
 // Scratch doubles needed for the split i-block partial sums of shape k.
 size_t force_partial_doubles(int k, int num_sms);
 // Adds the per-CTA partial sums (double4 per body: three vector components and
-// one scalar) of every i-block a stream-K slice boundary cut, in CTA order, and
+// one scalar) of every i-block a stream-K slice boundary cut (gpb = granules
+// per i-block row, npad / kGranule), in CTA order, and
 // writes out3[3g..3g+2] and out1[g] = -(scalar) for those blocks.
-cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t ntile, int64_t nctas, int block, const double* partial,
+cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t gpb, int64_t nctas, int block, const double* partial,
                         float* out3, float* out1, cudaStream_t st, const int* perm = nullptr,
                         int* err = nullptr);
+
+// The partial sums of a force launch whose fixup was left to the next pack
+// kernel: for the i-blocks a stream-K slice boundary cut, the pack adds the
+// per-CTA partials itself (in CTA order, rounded to FP32 as the fixup does, so
+// the result is the same bits) instead of reading the acceleration array.
+struct SplitSums {
+    const double* partial = nullptr;  // nullptr: every acceleration is in the acceleration array
+    int64_t units = 0;                // granules of the launch
+    int64_t nctas = 0;                // its CTAs
+    int64_t gpb = 0;                  // granules per i-block row
+    int block = 0;                    // bodies per i-block
+};
 
 // Exact scratch doubles force_launch needs for this variant and padded size
 // (its grid: resident CTAs on num_sms SMs, capped by the work units).
@@ -238,8 +259,10 @@ size_t force_partial_doubles_for(int k, bool pot, bool mixed, bool compensated, 
 // that combines split i-blocks; *launched gets the number of kernels queued.
 // ev0/ev1 (optional) are recorded on `st` just before and after the force
 // kernel itself.  Returns a cudaError_t.
+// With defer != nullptr the fixup is not launched and *defer describes the
+// partial sums for the pack kernel that consumes them (sinks = sources only).
 cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st, int* launched,
-                         cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
+                         cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, SplitSums* defer = nullptr);
 
 // Pack kernels: build jdup (and cell centres) from the state, optionally
 // applying a kick (vel += kick * acc) and a drift (pos += drift * vel) first.
@@ -249,11 +272,23 @@ int pack_threads(int block);
 // *flag = 1 if mass[0..n) all compare equal, else 0.  Queues a memset
 // and one kernel on st.
 cudaError_t uniform_mass_flag(int64_t n, const float* mass, int* flag, cudaStream_t st);
+// ss (optional): the accelerations of split i-blocks are in these deferred
+// partial sums (see SplitSums) rather than in acc.  pack_f64 needs block to be
+// a multiple of 256, and a centres buffer of pack_centre_doubles(npad, block)
+// doubles (the cell centres, then the 256-body chunk sums); it queues
+// pack_f64_launches(plain) kernels.
+size_t pack_centre_doubles(int64_t npad, int block);
+int pack_f64_launches(bool plain);
 cudaError_t pack_f64(int64_t n, int64_t npad, int block, double* pos, double* vel, const float* acc,
                      const float* mass, double kick, double drift, bool plain, float* jdup,
-                     double* centres, cudaStream_t st, const int* perm = nullptr, int* err = nullptr);
+                     double* centres, cudaStream_t st, const int* perm = nullptr, int* err = nullptr,
+                     const SplitSums* ss = nullptr);
 cudaError_t pack_f32(int64_t n, int64_t npad, float* pos, float* vel, const float* acc,
-                     const float* mass, float kick, float drift, float* jdup, cudaStream_t st);
+                     const float* mass, float kick, float drift, float* jdup, cudaStream_t st,
+                     const SplitSums* ss = nullptr);
+// Device side of SplitSums: the acceleration of the body in slot k (body g)
+// from the deferred partials when its i-block was split, else from acc.
+__device__ __forceinline__ void split_acc(const SplitSums& ss, int64_t k, int64_t g, const float* acc, float* out);
 // vel += kick * acc (the closing half kick of a leapfrog call).
 cudaError_t kick_f64(int64_t n, double* vel, const float* acc, double kick, cudaStream_t st);
 cudaError_t kick_f32(int64_t n, float* vel, const float* acc, float kick, cudaStream_t st);
@@ -291,9 +326,10 @@ int batched_num_shapes();
 BatchShape batched_shape(int k);
 size_t batched_smem_bytes(int cap);
 size_t batched_scratch_bytes(int64_t nsys);
-// Largest shared-memory image (bodies, a multiple of 128) a CTA of the
-// current device can hold.
-int batched_max_cap();
+// Shared-memory image (bodies, a multiple of 128) a CTA of shape k gets when
+// the batch's sizes are not known on the host: as large as the resident CTAs
+// its registers allow per SM can each have.
+int batched_max_cap(int k);
 // Queues the planning kernels and the persistent kernel; *launched gets the
 // number of kernels queued.
 cudaError_t batched_launch(int k, const BatchArgs& a, int num_sms, cudaStream_t st, int* launched);
@@ -327,13 +363,19 @@ size_t vjp_partial_doubles(int k, int num_sms);
 // Pack the VJP j-array.  With lam_f64/lamx given (adjoint sweep) it first does
 // lamx += gprev, gm_acc += gmprev, lam_f64 += drift * lamx; the cotangent
 // packed is kappa * lam.
+// Two kernels; centres holds pack_centre_doubles(npad, block) doubles (block a
+// multiple of 256).  ss (optional): g_prev/gm_prev of split i-blocks are in the
+// previous VJP's deferred partial sums.
 cudaError_t pack_vjp(int64_t n, int64_t npad, int block, const double* pos, const float* mass, const float* lam_f32,
                      double* lam_f64, double* lamx, const float* gprev, const float* gmprev, double* gm_acc,
                      double drift, double kappa, const float* mu, bool plain, float* jv, double* centres,
-                     cudaStream_t st);
+                     cudaStream_t st, const SplitSums* ss = nullptr);
 cudaError_t adjoint_accumulate(int64_t n, double* lamx, const float* g, double* gm_acc, const float* gm,
                                cudaStream_t st);
-cudaError_t vjp_launch(int k, const VjpArgs& a, int num_sms, cudaStream_t st, int* launched);
+// ev0/ev1 (optional) are recorded on `st` just before and after the VJP kernel.
+// defer (optional): skip the fixup; the next pack_vjp adds the partials.
+cudaError_t vjp_launch(int k, const VjpArgs& a, int num_sms, cudaStream_t st, int* launched,
+                       cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, SplitSums* defer = nullptr);
 
 // ---- spatial order (order.cu) ----
 // perm[k] = index of the body at position k of the Morton order (stable, by
@@ -349,5 +391,66 @@ cudaError_t sort_pass(int64_t n, const unsigned* key_in, const int* val_in, int 
 
 // One CTA waits on an mbarrier nothing completes, for limit_ns, then sets *err.
 cudaError_t selftest_wait(uint64_t limit_ns, int* err, cudaStream_t st);
+
+// The CTAs of a stream-K launch whose slices touch i-block b: [*c_lo, *c_hi],
+// and the partial slot c_lo wrote (0 if its slice starts at the block, else 1;
+// every later CTA starts inside the block, slot 0).
+__host__ __device__ __forceinline__ void split_ctas(int64_t b, int64_t gpb, int64_t units, int64_t nctas,
+                                                    int64_t* c_lo, int64_t* c_hi, int* slot_lo) {
+    const int64_t u0 = b * gpb, u1 = u0 + gpb - 1;
+    *c_lo = ((u0 + 1) * nctas - 1) / units;
+    *c_hi = ((u1 + 1) * nctas - 1) / units;
+    *slot_lo = (*c_lo * units / nctas == u0) ? 0 : 1;
+}
+
+// Sum in CTA order of the partial double4 (x, y, z, w) of slot lb of block b,
+// loads issued four at a time.
+__device__ __forceinline__ void split_sum(const double* partial, int C, int64_t b, int64_t c_lo, int64_t c_hi,
+                                          int slot_lo, int lb, double* s4) {
+    const double4_16a* P = reinterpret_cast<const double4_16a*>(partial);
+    double sx = 0.0, sy = 0.0, sz = 0.0, sw = 0.0;
+    for (int64_t c0 = c_lo; c0 <= c_hi; c0 += 4) {
+        double4_16a v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t c = c0 + q;
+            if (c <= c_hi) v[q] = P[(c * 2 + (c == c_lo ? slot_lo : 0)) * C + lb];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (c0 + q <= c_hi) {
+                sx += v[q].x;
+                sy += v[q].y;
+                sz += v[q].z;
+                sw += v[q].w;
+            }
+        }
+    }
+    s4[0] = sx;
+    s4[1] = sy;
+    s4[2] = sz;
+    s4[3] = sw;
+    (void)b;
+}
+
+__device__ __forceinline__ void split_acc(const SplitSums& ss, int64_t k, int64_t g, const float* acc, float* out) {
+    if (ss.partial != nullptr) {
+        const int64_t b = k / ss.block;
+        int64_t c_lo, c_hi;
+        int slot_lo;
+        split_ctas(b, ss.gpb, ss.units, ss.nctas, &c_lo, &c_hi, &slot_lo);
+        if (c_lo < c_hi) {
+            double s4[4];
+            split_sum(ss.partial, ss.block, b, c_lo, c_hi, slot_lo, (int)(k - b * ss.block), s4);
+            out[0] = (float)s4[0];
+            out[1] = (float)s4[1];
+            out[2] = (float)s4[2];
+            return;
+        }
+    }
+    out[0] = acc[3 * g + 0];
+    out[1] = acc[3 * g + 1];
+    out[2] = acc[3 * g + 2];
+}
 
 }  // namespace nbk

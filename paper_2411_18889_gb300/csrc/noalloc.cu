@@ -32,7 +32,7 @@ constexpr int64_t kMaxN = NBODY_NOALLOC_MAX_N;      // 65536 bodies
 constexpr int kShape = 1;                           // 1024-body i-blocks, 256-body j-tiles
 constexpr int kBlock = 1024;
 constexpr size_t kJdupBytes = (size_t)kMaxN * nbk::kJdupFloats * sizeof(float);  // 2 MiB
-constexpr size_t kCentreBytes = 4096;               // >= (kMaxN / kBlock) cells x 3 doubles
+constexpr size_t kCentreBytes = 8192;               // cell centres and 256-body chunk sums (pack_centre_doubles)
 constexpr size_t kWordBytes = 256;                  // error word (when the caller passes none), equal-mass flag
 constexpr size_t kPermBytes = (size_t)kMaxN * sizeof(int);                       // Morton permutation
 constexpr size_t kOrderBytes = (size_t)kMaxN * 16 + ((size_t)64 << 10);         // radix-sort scratch
@@ -43,7 +43,7 @@ constexpr size_t kOffPerm = kOffWords + kWordBytes;
 constexpr size_t kOffOrder = kOffPerm + kPermBytes;
 constexpr size_t kOffPartial = kOffOrder + kOrderBytes;
 constexpr size_t kScratchBytes = kOffPartial + kPartialBytes;
-static_assert((kMaxN / kBlock) * 3 * sizeof(double) <= kCentreBytes, "centre area too small");
+static_assert((3 * (kMaxN / kBlock) + 3 * (kMaxN / 256)) * sizeof(double) <= kCentreBytes, "centre area too small");
 static_assert(kOffPerm % 256 == 0 && kOffOrder % 256 == 0 && kOffPartial % 256 == 0, "areas stay 256-byte aligned");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];

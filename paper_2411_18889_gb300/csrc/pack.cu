@@ -25,32 +25,44 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// One CTA per cell.  Kick (vel += kick*acc), drift (pos += drift*vel), cell
-// centre, packed offsets.  kick/drift == 0 or vel/acc == nullptr skip them;
-// mass == nullptr packs zero masses (sinks that exert nothing).
-__global__ void __launch_bounds__(1024) pack_f64_kernel(int64_t n, int block, double* __restrict__ pos,
-                                                       double* __restrict__ vel, const float* __restrict__ acc,
-                                                       const float* __restrict__ mass, double kick, double drift,
-                                                       int plain, float* __restrict__ jdup,
-                                                       double* __restrict__ centres, const int* __restrict__ perm,
-                                                       int* __restrict__ err) {
-    __shared__ double red[3][32];
-    __shared__ double cen[3];
-    const int64_t base = (int64_t)blockIdx.x * block;
+// The FP64 pack runs as two body-parallel kernels (one thread per slot of the
+// packed array, 256-slot chunks), so at mid sizes it is not bound by a few
+// CTAs walking whole cells (one CTA per cell took 23 to 61 us at N = 16384
+// against 2 to 3 us now):
+//  1. kick (vel += kick * acc, the acceleration from acc or from the force
+//     launch's deferred partial sums), drift (pos += drift * vel), and each
+//     chunk's FP64 position sum; plain precision writes the packed entry here;
+//  2. (mixed) each cell's FP64 centre, the mean of its bodies' positions from
+//     its chunk sums in chunk order, and the packed FP32 offsets from it.
+// kick/drift == 0 or vel/acc == nullptr skip them; mass == nullptr packs zero
+// masses (sinks that exert nothing).  The chunk sums live after the cell
+// centres (pack_centre_doubles).
+constexpr int kChunk = 256;
+
+__global__ void __launch_bounds__(kChunk) pack_step_kernel(int64_t n, double* __restrict__ pos,
+                                                           double* __restrict__ vel, const float* __restrict__ acc,
+                                                           const float* __restrict__ mass, double kick, double drift,
+                                                           int plain, float* __restrict__ jdup,
+                                                           double* __restrict__ chunks, const int* __restrict__ perm,
+                                                           int* __restrict__ err, const SplitSums ss) {
+    __shared__ double red[3][kChunk / 32];
     const int tid = threadIdx.x;
-    double sx = 0.0, sy = 0.0, sz = 0.0;
-    for (int lb = tid; lb < block; lb += blockDim.x) {
-        const int64_t k = base + lb;
-        if (k >= n) break;
+    const int64_t k = (int64_t)blockIdx.x * kChunk + tid;
+    double x = 0.0, y = 0.0, z = 0.0;
+    if (k < n) {
         int64_t g = perm != nullptr ? perm[k] : k;  // body in slot k
         if (!in_range(g, n, err)) g = k;
-        double x = pos[3 * g + 0], y = pos[3 * g + 1], z = pos[3 * g + 2];
+        x = pos[3 * g + 0];
+        y = pos[3 * g + 1];
+        z = pos[3 * g + 2];
         if (vel != nullptr && (kick != 0.0 || drift != 0.0)) {
             double vx = vel[3 * g + 0], vy = vel[3 * g + 1], vz = vel[3 * g + 2];
             if (acc != nullptr && kick != 0.0) {
-                vx += kick * (double)acc[3 * g + 0];
-                vy += kick * (double)acc[3 * g + 1];
-                vz += kick * (double)acc[3 * g + 2];
+                float a3[3];
+                split_acc(ss, k, g, acc, a3);
+                vx += kick * (double)a3[0];
+                vy += kick * (double)a3[1];
+                vz += kick * (double)a3[2];
                 vel[3 * g + 0] = vx;
                 vel[3 * g + 1] = vy;
                 vel[3 * g + 2] = vz;
@@ -64,51 +76,61 @@ __global__ void __launch_bounds__(1024) pack_f64_kernel(int64_t n, int block, do
                 pos[3 * g + 2] = z;
             }
         }
-        sx += x;
-        sy += y;
-        sz += z;
+        if (plain) store_jdup(jdup, k, (float)x, (float)y, (float)z, mass != nullptr ? mass[g] : 0.0f);
+    } else if (plain) {
+        store_jdup(jdup, k, kPadPos, kPadPos, kPadPos, 0.0f);
     }
-    if (!plain) {
-        sx = warp_sum(sx);
-        sy = warp_sum(sy);
-        sz = warp_sum(sz);
-        const int w = tid >> 5, l = tid & 31;
-        if (l == 0) {
-            red[0][w] = sx;
-            red[1][w] = sy;
-            red[2][w] = sz;
-        }
-        __syncthreads();
-        if (tid < 3) {
-            double t = 0.0;
-            const int nw = (blockDim.x + 31) >> 5;
-            for (int k = 0; k < nw; ++k) t += red[tid][k];
-            const int64_t cnt = (n - base) < block ? (n - base) : (int64_t)block;
-            cen[tid] = t / (double)cnt;
-            centres[3 * blockIdx.x + tid] = cen[tid];
-        }
-        __syncthreads();
+    if (plain) return;
+    x = warp_sum(x);
+    y = warp_sum(y);
+    z = warp_sum(z);
+    const int w = tid >> 5, l = tid & 31;
+    if (l == 0) {
+        red[0][w] = x;
+        red[1][w] = y;
+        red[2][w] = z;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        double t = 0.0;
+        for (int q = 0; q < kChunk / 32; ++q) t += red[tid][q];
+        chunks[3 * (int64_t)blockIdx.x + tid] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kChunk) pack_offsets_kernel(int64_t n, int block, const double* __restrict__ pos,
+                                                              const float* __restrict__ mass,
+                                                              float* __restrict__ jdup, double* __restrict__ centres,
+                                                              const double* __restrict__ chunks,
+                                                              const int* __restrict__ perm, int* __restrict__ err) {
+    __shared__ double cen[3];
+    const int tid = threadIdx.x;
+    const int64_t ch = blockIdx.x;
+    const int per_cell = block / kChunk;
+    const int64_t cell = ch / per_cell;
+    if (tid < 3) {
+        double t = 0.0;
+        for (int q = 0; q < per_cell; ++q) t += chunks[3 * (cell * per_cell + q) + tid];
+        const int64_t base = cell * block;
+        const int64_t cnt = (n - base) < block ? (n - base) : (int64_t)block;
+        cen[tid] = t / (double)cnt;
+        if (ch % per_cell == 0) centres[3 * cell + tid] = cen[tid];
+    }
+    __syncthreads();
+    const int64_t k = ch * kChunk + tid;
+    if (k < n) {
+        int64_t g = perm != nullptr ? perm[k] : k;
+        if (!in_range(g, n, err)) g = k;
+        store_jdup(jdup, k, (float)(pos[3 * g + 0] - cen[0]), (float)(pos[3 * g + 1] - cen[1]),
+                   (float)(pos[3 * g + 2] - cen[2]), mass != nullptr ? mass[g] : 0.0f);
     } else {
-        if (tid < 3) cen[tid] = 0.0;
-        __syncthreads();
-    }
-    const double cx = cen[0], cy = cen[1], cz = cen[2];
-    for (int lb = tid; lb < block; lb += blockDim.x) {
-        const int64_t k = base + lb;
-        if (k < n) {
-            int64_t g = perm != nullptr ? perm[k] : k;
-            if (!in_range(g, n, err)) g = k;
-            store_jdup(jdup, k, (float)(pos[3 * g + 0] - cx), (float)(pos[3 * g + 1] - cy),
-                       (float)(pos[3 * g + 2] - cz), mass != nullptr ? mass[g] : 0.0f);
-        } else {
-            store_jdup(jdup, k, kPadPos, kPadPos, kPadPos, 0.0f);
-        }
+        store_jdup(jdup, k, kPadPos, kPadPos, kPadPos, 0.0f);
     }
 }
 
 __global__ void pack_f32_kernel(int64_t n, int64_t npad, float* __restrict__ pos, float* __restrict__ vel,
                                 const float* __restrict__ acc, const float* __restrict__ mass, float kick,
-                                float drift, float* __restrict__ jdup) {
+                                float drift, float* __restrict__ jdup, const SplitSums ss) {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < npad;
          g += (int64_t)gridDim.x * blockDim.x) {
         if (g < n) {
@@ -116,9 +138,11 @@ __global__ void pack_f32_kernel(int64_t n, int64_t npad, float* __restrict__ pos
             if (vel != nullptr && (kick != 0.0f || drift != 0.0f)) {
                 float vx = vel[3 * g + 0], vy = vel[3 * g + 1], vz = vel[3 * g + 2];
                 if (acc != nullptr && kick != 0.0f) {
-                    vx = fmaf(kick, acc[3 * g + 0], vx);
-                    vy = fmaf(kick, acc[3 * g + 1], vy);
-                    vz = fmaf(kick, acc[3 * g + 2], vz);
+                    float a3[3];
+                    split_acc(ss, g, g, acc, a3);
+                    vx = fmaf(kick, a3[0], vx);
+                    vy = fmaf(kick, a3[1], vy);
+                    vz = fmaf(kick, a3[2], vz);
                     vel[3 * g + 0] = vx;
                     vel[3 * g + 1] = vy;
                     vel[3 * g + 2] = vz;
@@ -172,18 +196,28 @@ unsigned grid_for(int64_t work, int threads) {
 
 }  // namespace
 
+size_t pack_centre_doubles(int64_t npad, int block) { return 3 * (size_t)(npad / block) + 3 * (size_t)(npad / kChunk); }
+
+int pack_f64_launches(bool plain) { return plain ? 1 : 2; }
+
 cudaError_t pack_f64(int64_t n, int64_t npad, int block, double* pos, double* vel, const float* acc,
                      const float* mass, double kick, double drift, bool plain, float* jdup, double* centres,
-                     cudaStream_t st, const int* perm, int* err) {
-    const unsigned nblk = (unsigned)(npad / block);
-    pack_f64_kernel<<<nblk, pack_threads(block), 0, st>>>(n, block, pos, vel, acc, mass, kick, drift,
-                                                            plain ? 1 : 0, jdup, centres, perm, err);
+                     cudaStream_t st, const int* perm, int* err, const SplitSums* ss) {
+    if (block % kChunk != 0 || npad % block != 0) return cudaErrorInvalidValue;
+    const unsigned nch = (unsigned)(npad / kChunk);
+    double* chunks = centres + 3 * (npad / block);
+    pack_step_kernel<<<nch, kChunk, 0, st>>>(n, pos, vel, acc, mass, kick, drift, plain ? 1 : 0, jdup, chunks, perm,
+                                            err, ss != nullptr ? *ss : SplitSums());
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || plain) return e;
+    pack_offsets_kernel<<<nch, kChunk, 0, st>>>(n, block, pos, mass, jdup, centres, chunks, perm, err);
     return cudaGetLastError();
 }
 
 cudaError_t pack_f32(int64_t n, int64_t npad, float* pos, float* vel, const float* acc, const float* mass,
-                     float kick, float drift, float* jdup, cudaStream_t st) {
-    pack_f32_kernel<<<grid_for(npad, 256), 256, 0, st>>>(n, npad, pos, vel, acc, mass, kick, drift, jdup);
+                     float kick, float drift, float* jdup, cudaStream_t st, const SplitSums* ss) {
+    pack_f32_kernel<<<grid_for(npad, 256), 256, 0, st>>>(n, npad, pos, vel, acc, mass, kick, drift, jdup,
+                                                         ss != nullptr ? *ss : SplitSums());
     return cudaGetLastError();
 }
 

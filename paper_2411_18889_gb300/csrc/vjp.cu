@@ -14,7 +14,7 @@
 // the force.
 //
 // The kernel mirrors the force kernel: stream-K persistent grid over
-// (i-block, j-tile) units, i-bodies packed in f32x2 pairs in registers, j-tiles
+// (i-block, 32 j-body granule) units, i-bodies packed in f32x2 pairs in registers, j-tiles
 // of 64 bytes per body (x, y, z, m, lam, mu, each duplicated) staged by 1-D
 // bulk copies on a two-stage mbarrier ring with bounded waits, masked diagonal
 // tiles for j = k, FP64 cell centres for mixed precision, and per-tile FP32
@@ -37,8 +37,8 @@ struct VParams {
     float eps2;
     int64_t n;
     int64_t nblk;
-    int64_t ntile;
-    int64_t units;
+    int64_t gpb;    // granules per i-block row (npad / kGranule)
+    int64_t units;  // granules in all: nblk * gpb
     int64_t nctas;
     float* g_pos;
     float* g_mass;
@@ -50,16 +50,20 @@ struct VParams {
 // UNI: every body has the same mass mu; u = m_k lam_j - m_j lam_k becomes
 // mu (lam_j - lam_k), formed without the masses (27 instead of 30 packed
 // operations per pair), and the caller scales the position gradient by mu.
-template <int T, int IP, int J, int UNROLL, bool MU, bool DIAG, bool UNI>
+// FULL: the whole tile; else j-bodies [jlo, jhi) of it (granule multiples).
+template <int T, int IP, int J, int UNROLL, bool MU, bool DIAG, bool UNI, bool FULL>
 __device__ __forceinline__ void vjp_tile(const unsigned char* tile, const f2 (&xi)[IP], const f2 (&yi)[IP],
                                          const f2 (&zi)[IP], const f2 (&nlx)[IP], const f2 (&nly)[IP],
                                          const f2 (&nlz)[IP], const f2 (&mi)[IP], const f2 (&nmi)[IP],
                                          const f2 (&nmui)[IP], f2 eps2,
-                                         f2 (&gx)[IP], f2 (&gy)[IP], f2 (&gz)[IP], f2 (&gm)[IP], int jl0, int tid) {
+                                         f2 (&gx)[IP], f2 (&gy)[IP], f2 (&gz)[IP], f2 (&gm)[IP], int jl0, int tid,
+                                         int jlo, int jhi) {
     const ulonglong2* tj = reinterpret_cast<const ulonglong2*>(tile);
     const f2 m3 = pk(-3.0f, -3.0f);
+    const int lo = FULL ? 0 : jlo;
+    const int hi = FULL ? J : jhi;
 #pragma unroll UNROLL
-    for (int j = 0; j < J; ++j) {
+    for (int j = lo; j < hi; ++j) {
         const ulonglong2 A = tj[4 * j + 0];
         const ulonglong2 B = tj[4 * j + 1];
         const ulonglong2 Cc = tj[4 * j + 2];
@@ -124,8 +128,11 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
 
     const int tid = threadIdx.x;
     const int64_t cta = blockIdx.x;
-    const int64_t u_begin = cta * p.units / p.nctas;
+    constexpr int64_t GPT = J / kGranule;  // granules per j-tile
+    static_assert(J % kGranule == 0, "a j-tile is a whole number of granules");
+    const int64_t u_begin = cta * p.units / p.nctas;  // this CTA's granules [u_begin, u_end)
     const int64_t u_end = (cta + 1) * p.units / p.nctas;
+    auto seg_end = [&](int64_t g) { return min(u_end, (g / GPT + 1) * GPT); };
     unsigned char* tiles = smem;
     f2* xsave = reinterpret_cast<f2*>(smem + 2 * TILE_BYTES);  // MIXED: [IP][3][T]
 
@@ -135,15 +142,22 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
         fence_mbar_init();
     }
     __syncthreads();
-    auto issue = [&](int s, int64_t unit) {
-        int64_t tile = unit % p.ntile;
-        if (!in_range(tile, p.ntile, p.err)) tile = 0;
+    auto issue = [&](int s, int64_t g) {
+        int64_t tile = (g % p.gpb) / GPT;
+        if (!in_range(tile, p.gpb / GPT, p.err)) tile = 0;
         mbar_expect_tx(&bar[s], TILE_BYTES);
         bulk_g2s(tiles + s * TILE_BYTES, p.jv + tile * (int64_t)J * kVjpFloats, TILE_BYTES, &bar[s]);
     };
-    if (tid == 0) {
-        if (u_begin < u_end) issue(0, u_begin);
-        if (u_begin + 1 < u_end) issue(1, u_begin + 1);
+    int64_t g_issued = u_begin;
+    int in_flight = 0;
+    if (tid == 0 && u_begin < u_end) {
+        issue(0, u_begin);
+        in_flight = 1;
+        if (seg_end(u_begin) < u_end) {
+            g_issued = seg_end(u_begin);
+            issue(1, g_issued);
+            in_flight = 2;
+        }
     }
     const f2 eps2 = pk(p.eps2, p.eps2);
     // One mass for every body (j-slot 0 is always a real body): the pair loop
@@ -156,9 +170,9 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
     bool failed = false;
 
     while (u < u_end) {
-        const int64_t b = u / p.ntile;
-        const int64_t t0 = u - b * p.ntile;
-        const int64_t t1 = min(p.ntile, t0 + (u_end - u));
+        const int64_t b = u / p.gpb;
+        const int64_t ub0 = u;
+        const int64_t ub1 = min(u_end, (b + 1) * p.gpb);
         const int64_t base = b * C;
         f2 xi[IP], yi[IP], zi[IP], nlx[IP], nly[IP], nlz[IP], mi[IP], nmi[IP], nmui[IP];
 #pragma unroll
@@ -188,7 +202,11 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
         for (int q = 0; q < IP; ++q) gx[q] = gy[q] = gz[q] = gm[q] = tx[q] = ty[q] = tz[q] = tm[q] = 0ull;
         int64_t cur_cell = b;
 
-        for (int64_t tt = t0; tt < t1; ++tt, ++u) {
+        while (u < ub1) {
+            const int64_t ue = seg_end(u);
+            const int64_t tt = (u % p.gpb) / GPT;
+            const int jlo = (int)(u % GPT) * kGranule, jhi = jlo + (int)(ue - u) * kGranule;
+            const bool whole = jlo == 0 && jhi == J;
             const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u, kWaitLimitNs);
             if (__syncthreads_or(!ok)) {
                 failed = true;
@@ -212,21 +230,28 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
                 }
             }
             const unsigned char* tile = tiles + s * TILE_BYTES;
-            if (cell == b) {
-                if (uni)
-                    vjp_tile<T, IP, J, UNROLL, MU, true, true>(tile, xi, yi, zi, nlx, nly, nlz, mi, nmi, nmui, eps2, gx,
-                                                               gy, gz, gm, (int)(tt * J - base), tid);
-                else
-                    vjp_tile<T, IP, J, UNROLL, MU, true, false>(tile, xi, yi, zi, nlx, nly, nlz, mi, nmi, nmui, eps2,
-                                                                gx, gy, gz, gm, (int)(tt * J - base), tid);
+            // With one mass for all bodies, no potential cotangent and eps > 0
+            // the self pair adds exactly 0 (u = mu (lam_k - lam_k) = 0 and the
+            // difference vector is zero), so only the other cases mask it.
+            const bool diag = cell == b && (MU || !uni || p.eps2 == 0.0f);
+            const int jl0 = diag ? (int)(tt * J - base) : 0;
+#define NBK_VTILE(DG, UN, FL)                                                                              \
+    vjp_tile<T, IP, J, UNROLL, MU, DG, UN, FL>(tile, xi, yi, zi, nlx, nly, nlz, mi, nmi, nmui, eps2, gx, gy, gz, gm, \
+                                               jl0, tid, jlo, jhi)
+            if (whole) {
+                if (diag) {
+                    if (uni) NBK_VTILE(true, true, true); else NBK_VTILE(true, false, true);
+                } else {
+                    if (uni) NBK_VTILE(false, true, true); else NBK_VTILE(false, false, true);
+                }
             } else {
-                if (uni)
-                    vjp_tile<T, IP, J, UNROLL, MU, false, true>(tile, xi, yi, zi, nlx, nly, nlz, mi, nmi, nmui, eps2,
-                                                                gx, gy, gz, gm, 0, tid);
-                else
-                    vjp_tile<T, IP, J, UNROLL, MU, false, false>(tile, xi, yi, zi, nlx, nly, nlz, mi, nmi, nmui, eps2,
-                                                                 gx, gy, gz, gm, 0, tid);
+                if (diag) {
+                    if (uni) NBK_VTILE(true, true, false); else NBK_VTILE(true, false, false);
+                } else {
+                    if (uni) NBK_VTILE(false, true, false); else NBK_VTILE(false, false, false);
+                }
             }
+#undef NBK_VTILE
 #pragma unroll
             for (int q = 0; q < IP; ++q) {
                 tx[q] = add2(tx[q], gx[q]);
@@ -236,13 +261,22 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
                 gx[q] = gy[q] = gz[q] = gm[q] = 0ull;
             }
             __syncthreads();
-            if (tid == 0 && u + 2 < u_end) issue(s, u + 2);
+            if (tid == 0) {
+                --in_flight;
+                const int64_t gn = seg_end(g_issued);
+                if (gn < u_end) {
+                    g_issued = gn;
+                    issue(s, gn);
+                    ++in_flight;
+                }
+            }
             s ^= 1;
+            u = ue;
         }
         if (failed) break;
 
-        const bool full = (t0 == 0 && t1 == p.ntile);
-        const int slot = (b == u_begin / p.ntile) ? 0 : 1;
+        const bool full = (ub0 == b * p.gpb && ub1 == (b + 1) * p.gpb);
+        const int slot = (b == u_begin / p.gpb) ? 0 : 1;
 #pragma unroll
         for (int q = 0; q < IP; ++q) {
             float v[2][4];
@@ -282,8 +316,7 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
     if (failed) {
         if (tid == 0) {
             atomicExch(p.err, kErrTimeout);
-            const int64_t inflight = (u_end - u) < 2 ? (u_end - u) : 2;
-            for (int k = 0; k < inflight; ++k) {
+            for (int k = 0; k < in_flight; ++k) {
                 const int st = (s + k) & 1;
                 (void)mbar_wait_bounded(&bar[st], (parity >> st) & 1u, kWaitLimitNs / 4);
             }
@@ -307,73 +340,118 @@ __device__ __forceinline__ void store_jv(float* jv, int64_t k, float x, float y,
     d[3] = make_float4(lz, lz, mu, mu);
 }
 
-// One CTA per cell: the adjoint-sweep updates (when lamx != nullptr)
+// The VJP's j-array, built as the force's FP64 pack is: two body-parallel
+// kernels over 256-slot chunks.  The first does the adjoint-sweep updates
+// (when lamx != nullptr)
 //   lamx += g_prev, gm_acc += gm_prev, lam += drift * lamx
-// then the VJP's j-array with cotangent kappa * lam, relative to the FP64
-// cell centre (mixed) or absolute (plain).
+// (g_prev and gm_prev from the previous VJP, or from its deferred partial sums)
+// and each chunk's FP64 position sum; the second the cell centres (mixed) and
+// the entries with cotangent kappa * lam, relative to the centre (mixed) or
+// absolute (plain).
+constexpr int kVChunk = 256;
+
 template <typename L>
-__global__ void __launch_bounds__(1024) pack_vjp_kernel(int64_t n, int block, const double* __restrict__ pos,
-                                                       const float* __restrict__ mass, L* __restrict__ lam,
-                                                       double* __restrict__ lamx, const float* __restrict__ gprev,
-                                                       const float* __restrict__ gmprev, double* __restrict__ gm_acc,
-                                                       double drift, double kappa, const float* __restrict__ mu,
-                                                       int plain, float* __restrict__ jv, double* __restrict__ centres) {
-    __shared__ double red[3][32];
-    __shared__ double cen[3];
-    const int64_t base = (int64_t)blockIdx.x * block;
+__global__ void __launch_bounds__(kVChunk) vjp_step_kernel(int64_t n, const double* __restrict__ pos,
+                                                           L* __restrict__ lam, double* __restrict__ lamx,
+                                                           const float* __restrict__ gprev,
+                                                           const float* __restrict__ gmprev,
+                                                           double* __restrict__ gm_acc, double drift,
+                                                           double* __restrict__ chunks, const SplitSums ss) {
+    __shared__ double red[3][kVChunk / 32];
     const int tid = threadIdx.x;
-    double sx = 0.0, sy = 0.0, sz = 0.0;
-    for (int lb = tid; lb < block; lb += blockDim.x) {
-        const int64_t g = base + lb;
-        if (g >= n) break;
+    const int64_t g = (int64_t)blockIdx.x * kVChunk + tid;
+    double x = 0.0, y = 0.0, z = 0.0;
+    if (g < n) {
         if constexpr (!std::is_const<L>::value) {
             if (lamx != nullptr) {
+                float gp[3] = {0.0f, 0.0f, 0.0f};
+                float gmp = 0.0f;
+                if (gprev != nullptr) {
+                    bool split = false;
+                    if (ss.partial != nullptr) {  // the previous VJP's partials, summed as its fixup would
+                        const int64_t b = g / ss.block;
+                        int64_t c_lo, c_hi;
+                        int slot_lo;
+                        split_ctas(b, ss.gpb, ss.units, ss.nctas, &c_lo, &c_hi, &slot_lo);
+                        if (c_lo < c_hi) {
+                            double s4[4];
+                            split_sum(ss.partial, ss.block, b, c_lo, c_hi, slot_lo, (int)(g - b * ss.block), s4);
+                            gp[0] = (float)s4[0];
+                            gp[1] = (float)s4[1];
+                            gp[2] = (float)s4[2];
+                            gmp = -(float)s4[3];
+                            split = true;
+                        }
+                    }
+                    if (!split) {
+                        gp[0] = gprev[3 * g + 0];
+                        gp[1] = gprev[3 * g + 1];
+                        gp[2] = gprev[3 * g + 2];
+                        gmp = gmprev != nullptr ? gmprev[g] : 0.0f;
+                    }
+                }
                 for (int c = 0; c < 3; ++c) {
                     double lx = lamx[3 * g + c];
-                    if (gprev != nullptr) lx += (double)gprev[3 * g + c];
+                    if (gprev != nullptr) lx += (double)gp[c];
                     lamx[3 * g + c] = lx;
                     lam[3 * g + c] = (L)((double)lam[3 * g + c] + drift * lx);
                 }
-                if (gmprev != nullptr) gm_acc[g] += (double)gmprev[g];
+                if (gmprev != nullptr) gm_acc[g] += (double)gmp;
             }
         }
-        sx += pos[3 * g + 0];
-        sy += pos[3 * g + 1];
-        sz += pos[3 * g + 2];
+        x = pos[3 * g + 0];
+        y = pos[3 * g + 1];
+        z = pos[3 * g + 2];
     }
-    if (!plain) {
-        sx = warp_sum(sx);
-        sy = warp_sum(sy);
-        sz = warp_sum(sz);
-        const int w = tid >> 5, l = tid & 31;
-        if (l == 0) {
-            red[0][w] = sx;
-            red[1][w] = sy;
-            red[2][w] = sz;
-        }
-        __syncthreads();
-        if (tid < 3) {
+    x = warp_sum(x);
+    y = warp_sum(y);
+    z = warp_sum(z);
+    const int w = tid >> 5, l = tid & 31;
+    if (l == 0) {
+        red[0][w] = x;
+        red[1][w] = y;
+        red[2][w] = z;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        double t = 0.0;
+        for (int q = 0; q < kVChunk / 32; ++q) t += red[tid][q];
+        chunks[3 * (int64_t)blockIdx.x + tid] = t;
+    }
+}
+
+template <typename L>
+__global__ void __launch_bounds__(kVChunk) vjp_offsets_kernel(int64_t n, int block, const double* __restrict__ pos,
+                                                              const float* __restrict__ mass,
+                                                              const L* __restrict__ lam, double kappa,
+                                                              const float* __restrict__ mu, int plain,
+                                                              float* __restrict__ jv, double* __restrict__ centres,
+                                                              const double* __restrict__ chunks) {
+    __shared__ double cen[3];
+    const int tid = threadIdx.x;
+    const int64_t ch = blockIdx.x;
+    const int per_cell = block / kVChunk;
+    const int64_t cell = ch / per_cell;
+    if (tid < 3) {
+        double c = 0.0;
+        if (!plain) {
             double t = 0.0;
-            for (int k = 0; k < (int)((blockDim.x + 31) >> 5); ++k) t += red[tid][k];
+            for (int q = 0; q < per_cell; ++q) t += chunks[3 * (cell * per_cell + q) + tid];
+            const int64_t base = cell * block;
             const int64_t cnt = (n - base) < block ? (n - base) : (int64_t)block;
-            cen[tid] = t / (double)cnt;
-            centres[3 * blockIdx.x + tid] = cen[tid];
+            c = t / (double)cnt;
+            if (ch % per_cell == 0) centres[3 * cell + tid] = c;
         }
-        __syncthreads();
-    } else {
-        if (tid < 3) cen[tid] = 0.0;
-        __syncthreads();
+        cen[tid] = c;
     }
-    const double cx = cen[0], cy = cen[1], cz = cen[2];
-    for (int lb = tid; lb < block; lb += blockDim.x) {
-        const int64_t g = base + lb;
-        if (g < n) {
-            store_jv(jv, g, (float)(pos[3 * g + 0] - cx), (float)(pos[3 * g + 1] - cy), (float)(pos[3 * g + 2] - cz),
-                     mass[g], (float)(kappa * (double)lam[3 * g + 0]), (float)(kappa * (double)lam[3 * g + 1]),
-                     (float)(kappa * (double)lam[3 * g + 2]), mu ? mu[g] : 0.0f);
-        } else {
-            store_jv(jv, g, kPadPos, kPadPos, kPadPos, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f);
-        }
+    __syncthreads();
+    const int64_t g = ch * kVChunk + tid;
+    if (g < n) {
+        store_jv(jv, g, (float)(pos[3 * g + 0] - cen[0]), (float)(pos[3 * g + 1] - cen[1]),
+                 (float)(pos[3 * g + 2] - cen[2]), mass[g], (float)(kappa * (double)lam[3 * g + 0]),
+                 (float)(kappa * (double)lam[3 * g + 1]), (float)(kappa * (double)lam[3 * g + 2]), mu ? mu[g] : 0.0f);
+    } else {
+        store_jv(jv, g, kPadPos, kPadPos, kPadPos, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f);
     }
 }
 
@@ -461,16 +539,22 @@ size_t vjp_partial_doubles(int k, int num_sms) {
 cudaError_t pack_vjp(int64_t n, int64_t npad, int block, const double* pos, const float* mass, const float* lam_f32,
                      double* lam_f64, double* lamx, const float* gprev, const float* gmprev, double* gm_acc,
                      double drift, double kappa, const float* mu, bool plain, float* jv, double* centres,
-                     cudaStream_t st) {
-    const unsigned nblk = (unsigned)(npad / block);
-    if (lam_f64 != nullptr)
-        pack_vjp_kernel<double><<<nblk, pack_threads(block), 0, st>>>(n, block, pos, mass, lam_f64, lamx, gprev,
-                                                                      gmprev, gm_acc, drift, kappa, mu,
-                                                                      plain ? 1 : 0, jv, centres);
-    else
-        pack_vjp_kernel<const float><<<nblk, pack_threads(block), 0, st>>>(n, block, pos, mass, lam_f32, nullptr,
-                                                                           nullptr, nullptr, nullptr, 0.0, kappa, mu,
-                                                                           plain ? 1 : 0, jv, centres);
+                     cudaStream_t st, const SplitSums* ss) {
+    if (block % kVChunk != 0 || npad % block != 0) return cudaErrorInvalidValue;
+    const unsigned nch = (unsigned)(npad / kVChunk);
+    double* chunks = centres + 3 * (npad / block);
+    const SplitSums sv = ss != nullptr ? *ss : SplitSums();
+    if (lam_f64 != nullptr) {
+        vjp_step_kernel<double><<<nch, kVChunk, 0, st>>>(n, pos, lam_f64, lamx, gprev, gmprev, gm_acc, drift, chunks,
+                                                         sv);
+        vjp_offsets_kernel<double><<<nch, kVChunk, 0, st>>>(n, block, pos, mass, lam_f64, kappa, mu, plain ? 1 : 0,
+                                                            jv, centres, chunks);
+    } else {
+        vjp_step_kernel<const float><<<nch, kVChunk, 0, st>>>(n, pos, lam_f32, nullptr, nullptr, nullptr, nullptr, 0.0,
+                                                              chunks, sv);
+        vjp_offsets_kernel<const float><<<nch, kVChunk, 0, st>>>(n, block, pos, mass, lam_f32, kappa, mu,
+                                                                 plain ? 1 : 0, jv, centres, chunks);
+    }
     return cudaGetLastError();
 }
 
@@ -484,7 +568,8 @@ cudaError_t adjoint_accumulate(int64_t n, double* lamx, const float* g, double* 
     return cudaGetLastError();
 }
 
-cudaError_t vjp_launch(int k, const VjpArgs& a, int num_sms, cudaStream_t st, int* launched) {
+cudaError_t vjp_launch(int k, const VjpArgs& a, int num_sms, cudaStream_t st, int* launched, cudaEvent_t ev0,
+                       cudaEvent_t ev1, SplitSums* defer) {
     const VShapeEntry& e = vshapes()[k];
     const int C = e.shape.block;
     const int mu = a.has_mu ? 1 : 0, mixed = a.centres != nullptr ? 1 : 0;
@@ -494,8 +579,8 @@ cudaError_t vjp_launch(int k, const VjpArgs& a, int num_sms, cudaStream_t st, in
     p.eps2 = a.eps2;
     p.n = a.n;
     p.nblk = a.npad / C;
-    p.ntile = a.npad / e.shape.jtile;
-    p.units = p.nblk * p.ntile;
+    p.gpb = a.npad / kGranule;
+    p.units = p.nblk * p.gpb;
     p.nctas = std::min<int64_t>((int64_t)num_sms * vocc(k, mu, mixed), p.units);
     p.g_pos = a.g_pos;
     p.g_mass = a.g_mass;
@@ -503,12 +588,22 @@ cudaError_t vjp_launch(int k, const VjpArgs& a, int num_sms, cudaStream_t st, in
     p.err = a.err;
     p.uni = a.uni;
     *launched = 0;
+    if (ev0 != nullptr) cudaEventRecord(ev0, st);
     e.fn[mu][mixed]<<<(unsigned)p.nctas, e.shape.threads, e.smem(mixed), st>>>(p);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     *launched = 1;
+    if (ev1 != nullptr) cudaEventRecord(ev1, st);
+    if (defer != nullptr) {  // the next pack_vjp adds the split blocks' partials
+        defer->partial = p.nctas > 1 ? p.partial : nullptr;
+        defer->units = p.units;
+        defer->nctas = p.nctas;
+        defer->gpb = p.gpb;
+        defer->block = C;
+        return cudaSuccess;
+    }
     if (p.nctas > 1) {
-        err = split_fixup(p.n, p.nblk, p.ntile, p.nctas, C, p.partial, p.g_pos, p.g_mass, st, nullptr, p.err);
+        err = split_fixup(p.n, p.nblk, p.gpb, p.nctas, C, p.partial, p.g_pos, p.g_mass, st, nullptr, p.err);
         if (err == cudaSuccess) *launched = 2;
     }
     return err;
