@@ -354,8 +354,9 @@ def throughput_leg(nb, dev, peak_int_s, args):
 def adjoint_leg(nb, dev, args):
     """Adjoint workload: N = 16384 Plummer, eps = 2^-7, dt = 2^-8, K = 64 KDK
     steps, checkpoints every 8 steps.  Forward = nbody_leapfrog_record (the run
-    that produces x(T) and the tape); gradient = nbody_leapfrog_vjp_tape (replay of
-    each segment from its checkpoint + one force VJP per force evaluation)."""
+    that produces x(T) and the tape); gradient = nbody_leapfrog_vjp_tape (one
+    force VJP per force evaluation, at positions run backwards from the end and
+    reset at the checkpoints)."""
     import torch
     import nbody_inputs as ni
     w = ni.adjoint_case()
@@ -407,8 +408,9 @@ def adjoint_leg(nb, dev, args):
     return {"workload": "plummer_n16384_eps2^-7_kdk64_dt2^-8_ckpt8_loss_sum_m_x_minus_y_sq",
             "forward_ms": f * 1e3, "gradient_ms": g * 1e3, "adjoint_to_forward": g / f,
             "forward_gints": inter / f / 1e9, "forward_pct_fp32_peak": None,
-            "note": "gradient = replay of 48 force evaluations from 8 checkpoints (on a second stream, two "
-                    "segments ahead) + 65 force VJPs"}, check
+            "note": "gradient = 65 force VJPs at positions run backwards from the end of the run and reset "
+                    "to the recorded state at the 8 checkpoints; 55 of them also give the force there for "
+                    "the reverse step (no forward replay)"}, check
 
 
 def with_potential_leg(nb, dev, P0, M, w, peak_int_s, reps):

@@ -235,14 +235,17 @@ NBODY_API int nbody_accel_vjp(int64_t n, const double* pos, const float* mass, d
  * The same in two calls, for a caller that makes the forward run anyway:
  * nbody_leapfrog_record runs nbody_leapfrog (FP64 state, in place) and writes
  * a tape: for every checkpoint step k = 0, c, 2c, ... < steps (c = ckpt_every)
- * the positions x_k and half-step velocities v_{k+1/2}, then x_steps
- * (nbody_tape_bytes(n, steps, c) bytes of device memory, caller-owned).
- * nbody_leapfrog_vjp_tape is the reverse sweep from that tape: newest segment
- * first, it replays each segment's positions from its checkpoint (the same
- * kernels, so the same bits) and applies one force VJP per force evaluation
- * of the forward run.  The tape and mass must be device memory; the cotangent
- * and gradient arrays may be host or device.  nbody_tape_bytes returns -1
- * for invalid sizes.
+ * the positions x_k and half-step velocities v_{k+1/2}, then x_steps and
+ * v_{steps-1/2} (nbody_tape_bytes(n, steps, c) bytes of device memory,
+ * caller-owned).  nbody_leapfrog_vjp_tape is the reverse sweep from that
+ * tape: one force VJP per force evaluation of the forward run, newest first,
+ * at positions obtained by running the leapfrog backwards from the end
+ * (x_s = x_{s+1} - dt v_{s+1/2}, v_{s-1/2} = v_{s+1/2} - dt a(x_s), the
+ * force computed by the VJP kernel itself at x_s) and reset to the recorded
+ * state at every checkpoint -- so no forward replay, and a reversed state is
+ * at most c - 1 steps from a recorded one (they agree to rounding).  The tape
+ * and mass must be device memory; the cotangent and gradient arrays may be
+ * host or device.  nbody_tape_bytes returns -1 for invalid sizes.
  */
 NBODY_API int nbody_leapfrog_vjp(int64_t n, const double* pos0, const double* vel0, const float* mass, double eps,
                                  double dt, int64_t steps, int64_t ckpt_every, const double* g_posT,

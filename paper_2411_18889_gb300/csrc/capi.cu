@@ -346,16 +346,15 @@ bool g_tune_loaded = false;
 
 void tune_defaults(std::vector<TuneRule>& r) {
     r.clear();
-    r.push_back({0, 0, 0, 4});
-    r.push_back({0, 0, 10240, 3});
-    r.push_back({0, 0, 49152, 2});
+    r.push_back({0, 0, 0, 3});
+    r.push_back({0, 0, 2560, 4});
+    r.push_back({0, 0, 10240, 2});
     r.push_back({0, 1, 0, 4});
-    r.push_back({0, 1, 24576, 1});
-    r.push_back({0, 1, 49152, 0});
+    r.push_back({0, 1, 10240, 1});
+    r.push_back({0, 1, 49152, 2});
     r.push_back({1, 0, 0, 3});
     r.push_back({1, 0, 2560, 2});
-    r.push_back({1, 0, 10240, 1});
-    r.push_back({1, 0, 24576, 0});
+    r.push_back({1, 0, 49152, 0});
     r.push_back({2, 0, 0, 3});
     r.push_back({2, 0, 320, 2});
     r.push_back({2, 0, 763, 0});
@@ -1011,8 +1010,10 @@ static int plan_vjp(Workspace* ws, int64_t n, int shape, int num_sms, VjpPlan* v
 }
 
 // defer (optional): leave the split blocks' partials to the next pack_vjp.
+// acc (optional): also the force at the same positions (defer_acc: deferred).
 static int run_vjp(const VjpPlan& vp, int64_t n, float eps2, bool mixed, bool has_mu, float* g_pos, float* g_mass,
-            int num_sms, cudaStream_t st, nbk::SplitSums* defer = nullptr) {
+                   int num_sms, cudaStream_t st, nbk::SplitSums* defer = nullptr, float* acc = nullptr,
+                   nbk::SplitSums* defer_acc = nullptr) {
     if (fault("launch")) return NBODY_ECUDA;
     nbk::VjpArgs a;
     a.jv = vp.jv;
@@ -1026,11 +1027,12 @@ static int run_vjp(const VjpPlan& vp, int64_t n, float eps2, bool mixed, bool ha
     a.partial = vp.partial;
     a.err = vp.err;
     a.uni = vp.uni;
+    a.acc = acc;
     int launched = 0;
     ProfPair pp;
     const bool timed_vjp = prof_pair(&pp, PROF_VJP);
     cudaError_t e = nbk::vjp_launch(vp.shape, a, num_sms, st, &launched, timed_vjp ? pp.a : nullptr,
-                                    timed_vjp ? pp.b : nullptr, defer);
+                                    timed_vjp ? pp.b : nullptr, defer, defer_acc);
     count(launched);
     NB_CUDA(e);
     return NBODY_OK;
@@ -1076,11 +1078,11 @@ int nbody_accel_vjp(int64_t n, const double* pos, const float* mass, double eps,
 
 // Tape of a recorded leapfrog: for each checkpoint k = 0, c, 2c, ... < steps the
 // positions x_k and the half-step velocity v_{k+1/2} (FP64 [n][3] each), then
-// the final positions x_steps.
+// the final positions x_steps and the last half-step velocity v_{steps-1/2}.
 int64_t nbody_tape_bytes(int64_t n, int64_t steps, int64_t ckpt_every) {
     if (n < 0 || steps < 0 || ckpt_every < 1) return -1;
     const int64_t nck = (steps + ckpt_every - 1) / ckpt_every;
-    return (nck * 2 + 1) * n * 3 * (int64_t)sizeof(double);
+    return (nck * 2 + 2) * n * 3 * (int64_t)sizeof(double);
 }
 
 static bool device_only(const void* p) { return p != nullptr && !is_host_ptr(p); }
@@ -1134,6 +1136,7 @@ int nbody_leapfrog_record(int64_t n, double* pos, double* vel, const float* mass
         if (ck) NB_CUDA(cudaMemcpyAsync(slot + (size_t)n * 3, vel, n3b, cudaMemcpyDeviceToDevice, st));
         NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, st, s + 1 < steps ? &ss : nullptr));
     }
+    NB_CUDA(cudaMemcpyAsync(xK + (size_t)n * 3, vel, n3b, cudaMemcpyDeviceToDevice, st));  // v_{K-1/2}
     count(1);
     NB_CUDA(nbk::kick_f64(n, vel, a, 0.5 * dt, st));
     NB_CUDA(cudaMemcpyAsync(xK, pos, n3b, cudaMemcpyDeviceToDevice, st));
@@ -1171,91 +1174,71 @@ int nbody_leapfrog_vjp_tape(int64_t n, const float* mass, double eps, double dt,
     if (steps == 0) return sg.finish();
 
     const bool plain = c.o.precision == NBODY_PREC_PLAIN;
-    const int comp = summation_mode(c.o.accumulate);
     const float eps2 = (float)(eps * eps);
     const double h = 0.5 * dt;
     const double* tp = (const double*)tape;
     const int64_t nck = (steps + ckpt_every - 1) / ckpt_every;
     const double* xK = tp + (size_t)nck * 2 * n * 3;
+    const double* vK = xK + (size_t)n * 3;  // v_{K-1/2}
     VjpPlan vp;
     NB_CHECK(plan_vjp(c.ws, n, choose_vjp_shape(n), c.sms, &vp));
-    ForcePlan fp;
-    NB_CHECK(plan_force(c.ws, n, shape_for(c, n, false), c.sms, &fp));
-    if (sorted_mixed(c.o.precision)) NB_CHECK(plan_order(c.ws, n, &fp));
-    NB_CHECK(plan_uniform(c.ws, &fp));
-    void *pg, *pgm, *pa, *px, *pv;
+    void *pg, *pgm, *pa, *px, *pv, *pu;
     NB_CHECK(ensure(c.ws, B_VG, (size_t)n * 3 * sizeof(float), &pg));
     NB_CHECK(ensure(c.ws, B_VGM, (size_t)n * sizeof(float), &pgm));
     NB_CHECK(ensure(c.ws, B_ACC, (size_t)n * 3 * sizeof(float), &pa));
-    NB_CHECK(ensure(c.ws, B_SEGX, 2 * (size_t)ckpt_every * n3b, &px));
+    NB_CHECK(ensure(c.ws, B_SEGX, n3b, &px));
     NB_CHECK(ensure(c.ws, B_SEGV, n3b, &pv));
+    NB_CHECK(ensure(c.ws, B_UNI, sizeof(int), &pu));
     float* g = (float*)pg;
     float* gm = (float*)pgm;
     float* a = (float*)pa;
-    double* X = (double*)px;  // two segment buffers, [2][ckpt_every][n][3]
-    double* v = (double*)pv;
-    NB_CHECK(ensure_aux(c.ws));
-    cudaStream_t aux = c.ws->aux;
-    cudaEvent_t ev_start = c.ws->ev[0], ev_rep[2] = {c.ws->ev[1], c.ws->ev[2]}, ev_sw[2] = {c.ws->ev[3], c.ws->ev[4]};
-    const size_t segd = (size_t)ckpt_every * n * 3;
+    double* X = (double*)px;  // x_s, run backwards from x_K
+    double* VH = (double*)pv; // v_{s+1/2}
+    vp.uni = (int*)pu;
+    count(1);
+    NB_CUDA(nbk::uniform_mass_flag(n, mass, vp.uni, st));
+    NB_CUDA(cudaMemcpyAsync(X, xK, n3b, cudaMemcpyDeviceToDevice, st));
+    NB_CUDA(cudaMemcpyAsync(VH, vK, n3b, cudaMemcpyDeviceToDevice, st));
 
-    // Segment replays run on the auxiliary stream, two segments ahead of the
-    // reverse sweep on the caller's stream: the replay (force kernels) of
-    // segment s-2 overlaps the VJPs of segment s.  Buffer s % 2 holds segment
-    // s; ev_rep[p] says it is filled, ev_sw[p] that the sweep has read it.
-    auto replay = [&](int64_t seg) -> int {
-        const int64_t c0 = seg * ckpt_every;
-        const int64_t c1 = (c0 + ckpt_every < steps) ? c0 + ckpt_every : steps;
-        const double* slot = tp + (size_t)seg * 2 * n * 3;
-        double* Xs = X + (size_t)(seg & 1) * segd;
-        NB_CUDA(cudaMemcpyAsync(Xs, slot, n3b, cudaMemcpyDeviceToDevice, aux));
-        if (c1 - c0 > 1) NB_CUDA(cudaMemcpyAsync(v, slot + (size_t)n * 3, n3b, cudaMemcpyDeviceToDevice, aux));
-        nbk::SplitSums ss;  // each replayed force is consumed by the next pack, as in the recorded run
-        for (int64_t k = c0 + 1; k < c1; ++k) {
-            double* xk = Xs + (size_t)(k - c0) * n * 3;
-            NB_CUDA(cudaMemcpyAsync(xk, xk - (size_t)n * 3, n3b, cudaMemcpyDeviceToDevice, aux));
-            // x_k = x_{k-1} + dt v_{k-1/2}; v_{k-1/2} = v_{k-3/2} + dt a(x_{k-1}) for k > c0 + 1
-            count(nbk::pack_f64_launches(plain));
-            NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, xk, v, k > c0 + 1 ? a : nullptr, mass,
-                                  k > c0 + 1 ? dt : 0.0, dt, plain, fp.jdup, fp.centres, aux, fp.perm, fp.err, &ss));
-            if (k + 1 < c1) NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, aux, &ss));
-        }
-        NB_CUDA(cudaEventRecord(ev_rep[seg & 1], aux));
-        return NBODY_OK;
-    };
-    NB_CHECK(issue_uniform(fp, n, mass, st));  // the replays take the recorded run's pair loop
-    vp.uni = fp.uni;                           // and the VJPs the equal-mass loop when it applies
-    NB_CUDA(cudaEventRecord(ev_start, st));  // the tape and inputs are ready on the caller's stream
-    NB_CUDA(cudaStreamWaitEvent(aux, ev_start, 0));
-    if (sorted_mixed(c.o.precision)) NB_CHECK(issue_order(fp, n, tp, aux));  // x_0's order, as recorded
-    NB_CHECK(replay(nck - 1));
-    if (nck >= 2) NB_CHECK(replay(nck - 2));
-
-    // v_K = v_{K-1/2} + h a(x_K).  Every VJP but the last is consumed by the
-    // next pack_vjp, which adds the split blocks' partial sums itself.
-    nbk::SplitSums ss;
+    // The sweep needs the positions x_s of every step, newest first.  It runs
+    // the leapfrog backwards from (x_K, v_{K-1/2}):
+    //   x_s = x_{s+1} - dt v_{s+1/2},   v_{s-1/2} = v_{s+1/2} - dt a(x_s),
+    // with a(x_s) from the VJP kernel at x_s itself (its FORCE variant: the
+    // same pair terms, 3 or 4 more FMAs per pair), and takes (x_c, v_{c+1/2})
+    // from the tape at every checkpoint c, so a reversed state is never more
+    // than ckpt_every - 1 steps from a recorded one.  No forward replay.
+    // Every VJP but the last is consumed by the next pack_vjp, which adds the
+    // split blocks' partial sums itself (and those of the force).
+    nbk::SplitSums ss, ss_acc;
+    // v_K = v_{K-1/2} + h a(x_K): the closing kick's VJP at x_K
     count(2);
-    NB_CUDA(nbk::pack_vjp(n, vp.npad, vp.block, xK, mass, nullptr, lamv, lamx, nullptr, nullptr, gm_acc, 0.0, h,
+    NB_CUDA(nbk::pack_vjp(n, vp.npad, vp.block, X, mass, nullptr, lamv, lamx, nullptr, nullptr, gm_acc, 0.0, h,
                           nullptr, plain, vp.jv, vp.centres, st));
     NB_CHECK(run_vjp(vp, n, eps2, !plain, false, g, gm, c.sms, st, &ss));
-    for (int64_t seg = nck - 1; seg >= 0; --seg) {
-        const int64_t c0 = seg * ckpt_every;
-        const int64_t c1 = (c0 + ckpt_every < steps) ? c0 + ckpt_every : steps;
-        const double* Xs = X + (size_t)(seg & 1) * segd;
-        NB_CUDA(cudaStreamWaitEvent(st, ev_rep[seg & 1], 0));
-        // reverse over the segment
-        for (int64_t s = c1 - 1; s >= c0; --s) {
-            const double kappa = (s == 0) ? h : dt;
-            count(2);
-            NB_CUDA(nbk::pack_vjp(n, vp.npad, vp.block, Xs + (size_t)(s - c0) * n * 3, mass, nullptr, lamv, lamx,
-                                  g, gm, gm_acc, dt, kappa, nullptr, plain, vp.jv, vp.centres, st, &ss));
-            NB_CHECK(run_vjp(vp, n, eps2, !plain, false, g, gm, c.sms, st, s > 0 ? &ss : nullptr));
+    bool have_a = false;  // a holds (or defers) the force at x_{s+1}
+    for (int64_t s = steps - 1; s >= 0; --s) {
+        nbk::ReverseStep rev;
+        rev.x = X;
+        rev.vh = VH;
+        if (s % ckpt_every == 0) {  // a checkpoint: the recorded state
+            const double* slot = tp + (size_t)(s / ckpt_every) * 2 * n * 3;
+            rev.anchor_x = slot;
+            rev.anchor_v = slot + (size_t)n * 3;
+        } else {
+            rev.a = have_a ? a : nullptr;  // s = steps - 1 starts from v_{K-1/2} itself
+            rev.ss_acc = ss_acc;
+            rev.kick = have_a ? dt : 0.0;
+            rev.drift = dt;
         }
-        NB_CUDA(cudaEventRecord(ev_sw[seg & 1], st));
-        if (seg >= 2) {
-            NB_CUDA(cudaStreamWaitEvent(aux, ev_sw[seg & 1], 0));
-            NB_CHECK(replay(seg - 2));
-        }
+        const double kappa = (s == 0) ? h : dt;
+        count(2);
+        NB_CUDA(nbk::pack_vjp(n, vp.npad, vp.block, X, mass, nullptr, lamv, lamx, g, gm, gm_acc, dt, kappa, nullptr,
+                              plain, vp.jv, vp.centres, st, &ss, &rev));
+        // the force at x_s is needed to step back to x_{s-1} unless that is a checkpoint
+        const bool want_a = s > 0 && (s - 1) % ckpt_every != 0;
+        NB_CHECK(run_vjp(vp, n, eps2, !plain, false, g, gm, c.sms, st, s > 0 ? &ss : nullptr, want_a ? a : nullptr,
+                         want_a ? &ss_acc : nullptr));
+        have_a = want_a;
     }
     count(1);
     NB_CUDA(nbk::adjoint_accumulate(n, lamx, g, gm_acc, gm, st));

@@ -286,9 +286,7 @@ cudaError_t pack_f64(int64_t n, int64_t npad, int block, double* pos, double* ve
 cudaError_t pack_f32(int64_t n, int64_t npad, float* pos, float* vel, const float* acc,
                      const float* mass, float kick, float drift, float* jdup, cudaStream_t st,
                      const SplitSums* ss = nullptr);
-// Device side of SplitSums: the acceleration of the body in slot k (body g)
-// from the deferred partials when its i-block was split, else from acc.
-__device__ __forceinline__ void split_acc(const SplitSums& ss, int64_t k, int64_t g, const float* acc, float* out);
+
 // vel += kick * acc (the closing half kick of a leapfrog call).
 cudaError_t kick_f64(int64_t n, double* vel, const float* acc, double kick, cudaStream_t st);
 cudaError_t kick_f32(int64_t n, float* vel, const float* acc, float kick, cudaStream_t st);
@@ -350,6 +348,7 @@ struct VjpArgs {
     bool has_mu;            // potential cotangent present
     float* g_pos;           // [n][3]
     float* g_mass;          // [n]
+    float* acc = nullptr;   // [n][3]: also the force at the same positions (no potential cotangent)
     double* partial;
     int* err;
     // Device word, nonzero when every body has the same mass (the pair loop
@@ -363,19 +362,38 @@ size_t vjp_partial_doubles(int k, int num_sms);
 // Pack the VJP j-array.  With lam_f64/lamx given (adjoint sweep) it first does
 // lamx += gprev, gm_acc += gmprev, lam_f64 += drift * lamx; the cotangent
 // packed is kappa * lam.
+// One step of the leapfrog run backwards, done by pack_vjp before it packs
+// (the adjoint sweep's positions without a forward replay):
+//   vh -= kick * a;  x -= drift * vh
+// with a the force at the previous positions (from acc, or from its deferred
+// partial sums ss_acc); or, at a checkpoint, x and vh taken from the tape.
+struct ReverseStep {
+    double* x = nullptr;              // positions [n][3], updated in place; nullptr: no reverse step
+    double* vh = nullptr;             // half-step velocities [n][3], updated in place
+    const double* anchor_x = nullptr; // checkpoint: x and vh are copied from here (kick, drift ignored)
+    const double* anchor_v = nullptr;
+    const float* a = nullptr;         // force at the previous positions, [n][3]; nullptr: no kick
+    SplitSums ss_acc;                 // its deferred partial sums
+    double kick = 0.0;
+    double drift = 0.0;
+};
+
 // Two kernels; centres holds pack_centre_doubles(npad, block) doubles (block a
 // multiple of 256).  ss (optional): g_prev/gm_prev of split i-blocks are in the
-// previous VJP's deferred partial sums.
+// previous VJP's deferred partial sums.  rev (optional): the reverse step,
+// after which pos is rev->x.
 cudaError_t pack_vjp(int64_t n, int64_t npad, int block, const double* pos, const float* mass, const float* lam_f32,
                      double* lam_f64, double* lamx, const float* gprev, const float* gmprev, double* gm_acc,
                      double drift, double kappa, const float* mu, bool plain, float* jv, double* centres,
-                     cudaStream_t st, const SplitSums* ss = nullptr);
+                     cudaStream_t st, const SplitSums* ss = nullptr, const ReverseStep* rev = nullptr);
 cudaError_t adjoint_accumulate(int64_t n, double* lamx, const float* g, double* gm_acc, const float* gm,
                                cudaStream_t st);
 // ev0/ev1 (optional) are recorded on `st` just before and after the VJP kernel.
 // defer (optional): skip the fixup; the next pack_vjp adds the partials.
+// defer_acc (optional, with a.acc): the same for the force.
 cudaError_t vjp_launch(int k, const VjpArgs& a, int num_sms, cudaStream_t st, int* launched,
-                       cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, SplitSums* defer = nullptr);
+                       cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, SplitSums* defer = nullptr,
+                       SplitSums* defer_acc = nullptr);
 
 // ---- spatial order (order.cu) ----
 // perm[k] = index of the body at position k of the Morton order (stable, by
@@ -404,20 +422,21 @@ __host__ __device__ __forceinline__ void split_ctas(int64_t b, int64_t gpb, int6
 }
 
 // Sum in CTA order of the partial double4 (x, y, z, w) of slot lb of block b,
-// loads issued four at a time.
+// loads issued eight at a time (a block of a mid-size launch has ~20 CTAs'
+// partials: three rounds of L2 latency instead of twenty).
 __device__ __forceinline__ void split_sum(const double* partial, int C, int64_t b, int64_t c_lo, int64_t c_hi,
                                           int slot_lo, int lb, double* s4) {
     const double4_16a* P = reinterpret_cast<const double4_16a*>(partial);
     double sx = 0.0, sy = 0.0, sz = 0.0, sw = 0.0;
-    for (int64_t c0 = c_lo; c0 <= c_hi; c0 += 4) {
-        double4_16a v[4];
+    for (int64_t c0 = c_lo; c0 <= c_hi; c0 += 8) {
+        double4_16a v[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 8; ++q) {
             const int64_t c = c0 + q;
             if (c <= c_hi) v[q] = P[(c * 2 + (c == c_lo ? slot_lo : 0)) * C + lb];
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 8; ++q) {
             if (c0 + q <= c_hi) {
                 sx += v[q].x;
                 sy += v[q].y;
@@ -433,20 +452,37 @@ __device__ __forceinline__ void split_sum(const double* partial, int C, int64_t 
     (void)b;
 }
 
-__device__ __forceinline__ void split_acc(const SplitSums& ss, int64_t k, int64_t g, const float* acc, float* out) {
-    if (ss.partial != nullptr) {
-        const int64_t b = k / ss.block;
-        int64_t c_lo, c_hi;
-        int slot_lo;
-        split_ctas(b, ss.gpb, ss.units, ss.nctas, &c_lo, &c_hi, &slot_lo);
-        if (c_lo < c_hi) {
-            double s4[4];
-            split_sum(ss.partial, ss.block, b, c_lo, c_hi, slot_lo, (int)(k - b * ss.block), s4);
-            out[0] = (float)s4[0];
-            out[1] = (float)s4[1];
-            out[2] = (float)s4[2];
-            return;
+// The split of the i-block holding slots [k0, k0 + 256) (one block: blocks are
+// multiples of 256), computed by thread 0 and shared through shared memory
+// (64-bit divisions are slow on the GPU; once per CTA, not per body).
+// Every thread of the CTA must call it.
+struct BlockSplit {
+    int64_t b, c_lo, c_hi;
+    int slot_lo;
+};
+__device__ __forceinline__ BlockSplit block_split(const SplitSums& ss, int64_t k0) {
+    __shared__ BlockSplit sh;
+    if (threadIdx.x == 0) {
+        BlockSplit r{0, 0, 0, 0};
+        if (ss.partial != nullptr) {
+            r.b = k0 / ss.block;
+            split_ctas(r.b, ss.gpb, ss.units, ss.nctas, &r.c_lo, &r.c_hi, &r.slot_lo);
         }
+        sh = r;
+    }
+    __syncthreads();
+    return sh;
+}
+
+__device__ __forceinline__ void split_acc(const SplitSums& ss, const BlockSplit& bs, int64_t k, int64_t g,
+                                          const float* acc, float* out) {
+    if (ss.partial != nullptr && bs.c_lo < bs.c_hi) {
+        double s4[4];
+        split_sum(ss.partial, ss.block, bs.b, bs.c_lo, bs.c_hi, bs.slot_lo, (int)(k - bs.b * ss.block), s4);
+        out[0] = (float)s4[0];
+        out[1] = (float)s4[1];
+        out[2] = (float)s4[2];
+        return;
     }
     out[0] = acc[3 * g + 0];
     out[1] = acc[3 * g + 1];

@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(kChunk) pack_step_kernel(int64_t n, double* __
     __shared__ double red[3][kChunk / 32];
     const int tid = threadIdx.x;
     const int64_t k = (int64_t)blockIdx.x * kChunk + tid;
+    const BlockSplit bs = block_split(ss, (int64_t)blockIdx.x * kChunk);
     double x = 0.0, y = 0.0, z = 0.0;
     if (k < n) {
         int64_t g = perm != nullptr ? perm[k] : k;  // body in slot k
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(kChunk) pack_step_kernel(int64_t n, double* __
             double vx = vel[3 * g + 0], vy = vel[3 * g + 1], vz = vel[3 * g + 2];
             if (acc != nullptr && kick != 0.0) {
                 float a3[3];
-                split_acc(ss, k, g, acc, a3);
+                split_acc(ss, bs, k, g, acc, a3);
                 vx += kick * (double)a3[0];
                 vy += kick * (double)a3[1];
                 vz += kick * (double)a3[2];
@@ -128,38 +129,39 @@ __global__ void __launch_bounds__(kChunk) pack_offsets_kernel(int64_t n, int blo
     }
 }
 
-__global__ void pack_f32_kernel(int64_t n, int64_t npad, float* __restrict__ pos, float* __restrict__ vel,
-                                const float* __restrict__ acc, const float* __restrict__ mass, float kick,
-                                float drift, float* __restrict__ jdup, const SplitSums ss) {
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < npad;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        if (g < n) {
-            float x = pos[3 * g + 0], y = pos[3 * g + 1], z = pos[3 * g + 2];
-            if (vel != nullptr && (kick != 0.0f || drift != 0.0f)) {
-                float vx = vel[3 * g + 0], vy = vel[3 * g + 1], vz = vel[3 * g + 2];
-                if (acc != nullptr && kick != 0.0f) {
-                    float a3[3];
-                    split_acc(ss, g, g, acc, a3);
-                    vx = fmaf(kick, a3[0], vx);
-                    vy = fmaf(kick, a3[1], vy);
-                    vz = fmaf(kick, a3[2], vz);
-                    vel[3 * g + 0] = vx;
-                    vel[3 * g + 1] = vy;
-                    vel[3 * g + 2] = vz;
-                }
-                if (drift != 0.0f) {
-                    x = fmaf(drift, vx, x);
-                    y = fmaf(drift, vy, y);
-                    z = fmaf(drift, vz, z);
-                    pos[3 * g + 0] = x;
-                    pos[3 * g + 1] = y;
-                    pos[3 * g + 2] = z;
-                }
+// FP32 state, absolute coordinates: one thread per slot (256-slot chunks).
+__global__ void __launch_bounds__(kChunk) pack_f32_kernel(int64_t n, float* __restrict__ pos,
+                                                          float* __restrict__ vel, const float* __restrict__ acc,
+                                                          const float* __restrict__ mass, float kick, float drift,
+                                                          float* __restrict__ jdup, const SplitSums ss) {
+    const int64_t g = (int64_t)blockIdx.x * kChunk + threadIdx.x;
+    const BlockSplit bs = block_split(ss, (int64_t)blockIdx.x * kChunk);
+    if (g < n) {
+        float x = pos[3 * g + 0], y = pos[3 * g + 1], z = pos[3 * g + 2];
+        if (vel != nullptr && (kick != 0.0f || drift != 0.0f)) {
+            float vx = vel[3 * g + 0], vy = vel[3 * g + 1], vz = vel[3 * g + 2];
+            if (acc != nullptr && kick != 0.0f) {
+                float a3[3];
+                split_acc(ss, bs, g, g, acc, a3);
+                vx = fmaf(kick, a3[0], vx);
+                vy = fmaf(kick, a3[1], vy);
+                vz = fmaf(kick, a3[2], vz);
+                vel[3 * g + 0] = vx;
+                vel[3 * g + 1] = vy;
+                vel[3 * g + 2] = vz;
             }
-            store_jdup(jdup, g, x, y, z, mass != nullptr ? mass[g] : 0.0f);
-        } else {
-            store_jdup(jdup, g, kPadPos, kPadPos, kPadPos, 0.0f);
+            if (drift != 0.0f) {
+                x = fmaf(drift, vx, x);
+                y = fmaf(drift, vy, y);
+                z = fmaf(drift, vz, z);
+                pos[3 * g + 0] = x;
+                pos[3 * g + 1] = y;
+                pos[3 * g + 2] = z;
+            }
         }
+        store_jdup(jdup, g, x, y, z, mass != nullptr ? mass[g] : 0.0f);
+    } else {
+        store_jdup(jdup, g, kPadPos, kPadPos, kPadPos, 0.0f);
     }
 }
 
@@ -216,8 +218,9 @@ cudaError_t pack_f64(int64_t n, int64_t npad, int block, double* pos, double* ve
 
 cudaError_t pack_f32(int64_t n, int64_t npad, float* pos, float* vel, const float* acc, const float* mass,
                      float kick, float drift, float* jdup, cudaStream_t st, const SplitSums* ss) {
-    pack_f32_kernel<<<grid_for(npad, 256), 256, 0, st>>>(n, npad, pos, vel, acc, mass, kick, drift, jdup,
-                                                         ss != nullptr ? *ss : SplitSums());
+    if (npad % kChunk != 0) return cudaErrorInvalidValue;
+    pack_f32_kernel<<<(unsigned)(npad / kChunk), kChunk, 0, st>>>(n, pos, vel, acc, mass, kick, drift, jdup,
+                                                                 ss != nullptr ? *ss : SplitSums());
     return cudaGetLastError();
 }
 

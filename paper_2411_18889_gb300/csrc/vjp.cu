@@ -42,7 +42,9 @@ struct VParams {
     int64_t nctas;
     float* g_pos;
     float* g_mass;
-    double* partial;
+    float* acc;           // FORCE kernels: the force at the same positions, [n][3]
+    double* partial;      // [nctas][2][block] double4: (g_pos, -g_mass) of split blocks
+    double* partial_acc;  // FORCE kernels: [nctas][2][block] double4 (acc, 0), after the VJP's
     int* err;
     const int* uni;  // nonzero word: every body has one mass (or nullptr)
 };
@@ -51,13 +53,15 @@ struct VParams {
 // mu (lam_j - lam_k), formed without the masses (27 instead of 30 packed
 // operations per pair), and the caller scales the position gradient by mu.
 // FULL: the whole tile; else j-bodies [jlo, jhi) of it (granule multiples).
-template <int T, int IP, int J, int UNROLL, bool MU, bool DIAG, bool UNI, bool FULL>
+// FORCE: also the force a_k = sum_j m_j s^{-3/2} d at the same positions (3
+// more FMAs per pair; 4 with distinct masses), into (fx, fy, fz).
+template <int T, int IP, int J, int UNROLL, bool MU, bool DIAG, bool UNI, bool FULL, bool FORCE>
 __device__ __forceinline__ void vjp_tile(const unsigned char* tile, const f2 (&xi)[IP], const f2 (&yi)[IP],
                                          const f2 (&zi)[IP], const f2 (&nlx)[IP], const f2 (&nly)[IP],
                                          const f2 (&nlz)[IP], const f2 (&mi)[IP], const f2 (&nmi)[IP],
                                          const f2 (&nmui)[IP], f2 eps2,
-                                         f2 (&gx)[IP], f2 (&gy)[IP], f2 (&gz)[IP], f2 (&gm)[IP], int jl0, int tid,
-                                         int jlo, int jhi) {
+                                         f2 (&gx)[IP], f2 (&gy)[IP], f2 (&gz)[IP], f2 (&gm)[IP], f2 (&fx)[IP],
+                                         f2 (&fy)[IP], f2 (&fz)[IP], int jl0, int tid, int jlo, int jhi) {
     const ulonglong2* tj = reinterpret_cast<const ulonglong2*>(tile);
     const f2 m3 = pk(-3.0f, -3.0f);
     const int lo = FULL ? 0 : jlo;
@@ -105,6 +109,12 @@ __device__ __forceinline__ void vjp_tile(const unsigned char* tile, const f2 (&x
             dl = fma2(dy, lyj, dl);
             dl = fma2(dz, lzj, dl);
             gm[q] = fma2(r3, dl, gm[q]);
+            if (FORCE) {
+                const f2 w = UNI ? r3 : mul2(r3, mj);
+                fx[q] = fma2(dx, w, fx[q]);
+                fy[q] = fma2(dy, w, fy[q]);
+                fz[q] = fma2(dz, w, fz[q]);
+            }
             if (MU) {
                 // -s^{-3/2} d (mu_j m_k + mu_k m_j) with d = r_j - r_k, and mu_j s^{-1/2};
                 // nmi, nmui hold -m_k, -mu_k
@@ -118,7 +128,7 @@ __device__ __forceinline__ void vjp_tile(const unsigned char* tile, const f2 (&x
     }
 }
 
-template <int T, int IP, int J, int UNROLL, bool MU, bool MIXED>
+template <int T, int IP, int J, int UNROLL, bool MU, bool MIXED, bool FORCE>
 __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
     constexpr int C = 2 * IP * T;
     constexpr uint32_t TILE_BYTES = J * kVjpFloats * 4u;
@@ -198,8 +208,12 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
             }
         }
         f2 gx[IP], gy[IP], gz[IP], gm[IP], tx[IP], ty[IP], tz[IP], tm[IP];
+        f2 fx[IP], fy[IP], fz[IP], ux[IP], uy[IP], uz[IP];  // FORCE: per tile, and totals
 #pragma unroll
-        for (int q = 0; q < IP; ++q) gx[q] = gy[q] = gz[q] = gm[q] = tx[q] = ty[q] = tz[q] = tm[q] = 0ull;
+        for (int q = 0; q < IP; ++q) {
+            gx[q] = gy[q] = gz[q] = gm[q] = tx[q] = ty[q] = tz[q] = tm[q] = 0ull;
+            fx[q] = fy[q] = fz[q] = ux[q] = uy[q] = uz[q] = 0ull;
+        }
         int64_t cur_cell = b;
 
         while (u < ub1) {
@@ -235,9 +249,9 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
             // difference vector is zero), so only the other cases mask it.
             const bool diag = cell == b && (MU || !uni || p.eps2 == 0.0f);
             const int jl0 = diag ? (int)(tt * J - base) : 0;
-#define NBK_VTILE(DG, UN, FL)                                                                              \
-    vjp_tile<T, IP, J, UNROLL, MU, DG, UN, FL>(tile, xi, yi, zi, nlx, nly, nlz, mi, nmi, nmui, eps2, gx, gy, gz, gm, \
-                                               jl0, tid, jlo, jhi)
+#define NBK_VTILE(DG, UN, FL)                                                                                 \
+    vjp_tile<T, IP, J, UNROLL, MU, DG, UN, FL, FORCE>(tile, xi, yi, zi, nlx, nly, nlz, mi, nmi, nmui, eps2, gx, gy, gz, \
+                                                      gm, fx, fy, fz, jl0, tid, jlo, jhi)
             if (whole) {
                 if (diag) {
                     if (uni) NBK_VTILE(true, true, true); else NBK_VTILE(true, false, true);
@@ -259,6 +273,12 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
                 tz[q] = add2(tz[q], gz[q]);
                 tm[q] = add2(tm[q], gm[q]);
                 gx[q] = gy[q] = gz[q] = gm[q] = 0ull;
+                if (FORCE) {
+                    ux[q] = add2(ux[q], fx[q]);
+                    uy[q] = add2(uy[q], fy[q]);
+                    uz[q] = add2(uz[q], fz[q]);
+                    fx[q] = fy[q] = fz[q] = 0ull;
+                }
             }
             __syncthreads();
             if (tid == 0) {
@@ -279,16 +299,25 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
         const int slot = (b == u_begin / p.gpb) ? 0 : 1;
 #pragma unroll
         for (int q = 0; q < IP; ++q) {
-            float v[2][4];
+            float v[2][4], f[2][3];
             upk(tx[q], v[0][0], v[1][0]);
             upk(ty[q], v[0][1], v[1][1]);
             upk(tz[q], v[0][2], v[1][2]);
             upk(tm[q], v[0][3], v[1][3]);
+            if (FORCE) {
+                upk(ux[q], f[0][0], f[1][0]);
+                upk(uy[q], f[0][1], f[1][1]);
+                upk(uz[q], f[0][2], f[1][2]);
+            }
             if (uni) {
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     v[0][k] *= mu;
                     v[1][k] *= mu;
+                    if (FORCE) {
+                        f[0][k] *= mu;
+                        f[1][k] *= mu;
+                    }
                 }
             }
 #pragma unroll
@@ -302,12 +331,21 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
                         p.g_pos[3 * g + 1] = v[h][1];
                         p.g_pos[3 * g + 2] = v[h][2];
                         p.g_mass[g] = -v[h][3];
+                        if (FORCE) {
+                            p.acc[3 * g + 0] = f[h][0];
+                            p.acc[3 * g + 1] = f[h][1];
+                            p.acc[3 * g + 2] = f[h][2];
+                        }
                     }
                 } else {
                     const int64_t pi = (cta * 2 + slot) * C + lb;
                     if (!in_range(pi, p.nctas * 2 * C, p.err)) continue;
                     double4_16a* dst = reinterpret_cast<double4_16a*>(p.partial) + pi;
                     *dst = make_double4_16a(v[h][0], v[h][1], v[h][2], v[h][3]);
+                    if (FORCE) {
+                        double4_16a* fa = reinterpret_cast<double4_16a*>(p.partial_acc) + pi;
+                        *fa = make_double4_16a(f[h][0], f[h][1], f[h][2], 0.0);
+                    }
                 }
             }
         }
@@ -356,11 +394,35 @@ __global__ void __launch_bounds__(kVChunk) vjp_step_kernel(int64_t n, const doub
                                                            const float* __restrict__ gprev,
                                                            const float* __restrict__ gmprev,
                                                            double* __restrict__ gm_acc, double drift,
-                                                           double* __restrict__ chunks, const SplitSums ss) {
+                                                           double* __restrict__ chunks, const SplitSums ss,
+                                                           const ReverseStep rev) {
     __shared__ double red[3][kVChunk / 32];
     const int tid = threadIdx.x;
     const int64_t g = (int64_t)blockIdx.x * kVChunk + tid;
+    const BlockSplit bs = block_split(ss, (int64_t)blockIdx.x * kVChunk);
+    const BlockSplit ba = block_split(rev.ss_acc, (int64_t)blockIdx.x * kVChunk);
     double x = 0.0, y = 0.0, z = 0.0;
+    double r[3] = {0.0, 0.0, 0.0};  // positions after the reverse step (pos aliases rev.x then)
+    if (g < n && rev.x != nullptr) {  // the leapfrog step s run backwards
+        double w[3];
+        if (rev.anchor_x != nullptr) {
+            for (int c = 0; c < 3; ++c) {
+                r[c] = rev.anchor_x[3 * g + c];
+                w[c] = rev.anchor_v[3 * g + c];
+            }
+        } else {
+            float a3[3] = {0.0f, 0.0f, 0.0f};
+            if (rev.a != nullptr) split_acc(rev.ss_acc, ba, g, g, rev.a, a3);
+            for (int c = 0; c < 3; ++c) {
+                w[c] = rev.vh[3 * g + c] - rev.kick * (double)a3[c];
+                r[c] = rev.x[3 * g + c] - rev.drift * w[c];
+            }
+        }
+        for (int c = 0; c < 3; ++c) {
+            rev.x[3 * g + c] = r[c];
+            rev.vh[3 * g + c] = w[c];
+        }
+    }
     if (g < n) {
         if constexpr (!std::is_const<L>::value) {
             if (lamx != nullptr) {
@@ -369,13 +431,10 @@ __global__ void __launch_bounds__(kVChunk) vjp_step_kernel(int64_t n, const doub
                 if (gprev != nullptr) {
                     bool split = false;
                     if (ss.partial != nullptr) {  // the previous VJP's partials, summed as its fixup would
-                        const int64_t b = g / ss.block;
-                        int64_t c_lo, c_hi;
-                        int slot_lo;
-                        split_ctas(b, ss.gpb, ss.units, ss.nctas, &c_lo, &c_hi, &slot_lo);
-                        if (c_lo < c_hi) {
+                        if (bs.c_lo < bs.c_hi) {
                             double s4[4];
-                            split_sum(ss.partial, ss.block, b, c_lo, c_hi, slot_lo, (int)(g - b * ss.block), s4);
+                            split_sum(ss.partial, ss.block, bs.b, bs.c_lo, bs.c_hi, bs.slot_lo,
+                                      (int)(g - bs.b * ss.block), s4);
                             gp[0] = (float)s4[0];
                             gp[1] = (float)s4[1];
                             gp[2] = (float)s4[2];
@@ -399,9 +458,15 @@ __global__ void __launch_bounds__(kVChunk) vjp_step_kernel(int64_t n, const doub
                 if (gmprev != nullptr) gm_acc[g] += (double)gmp;
             }
         }
-        x = pos[3 * g + 0];
-        y = pos[3 * g + 1];
-        z = pos[3 * g + 2];
+        if (rev.x != nullptr) {
+            x = r[0];
+            y = r[1];
+            z = r[2];
+        } else {
+            x = pos[3 * g + 0];
+            y = pos[3 * g + 1];
+            z = pos[3 * g + 2];
+        }
     }
     x = warp_sum(x);
     y = warp_sum(y);
@@ -468,6 +533,7 @@ typedef void (*VFn)(const VParams);
 struct VShapeEntry {
     VjpShape shape;
     VFn fn[2][2];  // [mu][mixed]
+    VFn fnf[2];    // [mixed]: with the force, no potential cotangent
     size_t smem(bool mixed) const {
         return 2u * shape.jtile * kVjpFloats * 4u + (mixed ? (size_t)shape.ipairs * 3 * shape.threads * 8 : 0);
     }
@@ -477,10 +543,12 @@ template <int T, int IP, int J, int UNROLL>
 VShapeEntry make_ventry() {
     VShapeEntry e;
     e.shape = VjpShape{T, IP, J, 2 * IP * T};
-    e.fn[0][0] = vjp_kernel<T, IP, J, UNROLL, false, false>;
-    e.fn[0][1] = vjp_kernel<T, IP, J, UNROLL, false, true>;
-    e.fn[1][0] = vjp_kernel<T, IP, J, UNROLL, true, false>;
-    e.fn[1][1] = vjp_kernel<T, IP, J, UNROLL, true, true>;
+    e.fn[0][0] = vjp_kernel<T, IP, J, UNROLL, false, false, false>;
+    e.fn[0][1] = vjp_kernel<T, IP, J, UNROLL, false, true, false>;
+    e.fn[1][0] = vjp_kernel<T, IP, J, UNROLL, true, false, false>;
+    e.fn[1][1] = vjp_kernel<T, IP, J, UNROLL, true, true, false>;
+    e.fnf[0] = vjp_kernel<T, IP, J, UNROLL, false, false, true>;
+    e.fnf[1] = vjp_kernel<T, IP, J, UNROLL, false, true, true>;
     return e;
 }
 
@@ -498,10 +566,10 @@ constexpr int kNumVShapes = 4;
 // Resident CTAs per SM for each variant, queried once per device (the
 // shared-memory attribute is set per device).
 struct VOccTable {
-    int v[kNumVShapes][2][2];
+    int v[kNumVShapes][3][2];  // [shape][0: VJP, 1: with mu, 2: with the force][mixed]
     VOccTable() {
         for (int a = 0; a < kNumVShapes; ++a)
-            for (int b = 0; b < 2; ++b)
+            for (int b = 0; b < 3; ++b)
                 for (int c = 0; c < 2; ++c) v[a][b][c] = -1;
     }
 };
@@ -516,9 +584,10 @@ int vocc(int k, int mu, int mixed) {
     if (o < 0) {
         const VShapeEntry& e = vshapes()[k];
         const size_t sm = e.smem(mixed);
-        cudaFuncSetAttribute(e.fn[mu][mixed], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        VFn fn = mu == 2 ? e.fnf[mixed] : e.fn[mu][mixed];
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, e.fn[mu][mixed], e.shape.threads, sm) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, e.shape.threads, sm) != cudaSuccess ||
             nb < 1)
             nb = 1;
         o = std::min(nb, 8);
@@ -532,26 +601,29 @@ int vjp_num_shapes() { return kNumVShapes; }
 VjpShape vjp_shape(int k) { return vshapes()[k].shape; }
 int vjp_floats_per_body() { return kVjpFloats; }
 
+// Two halves: the VJP's partials, then (FORCE launches) the force's.
 size_t vjp_partial_doubles(int k, int num_sms) {
-    return (size_t)num_sms * 8u * 2u * (size_t)vshapes()[k].shape.block * 4u;
+    return 2 * (size_t)num_sms * 8u * 2u * (size_t)vshapes()[k].shape.block * 4u;
 }
 
 cudaError_t pack_vjp(int64_t n, int64_t npad, int block, const double* pos, const float* mass, const float* lam_f32,
                      double* lam_f64, double* lamx, const float* gprev, const float* gmprev, double* gm_acc,
                      double drift, double kappa, const float* mu, bool plain, float* jv, double* centres,
-                     cudaStream_t st, const SplitSums* ss) {
+                     cudaStream_t st, const SplitSums* ss, const ReverseStep* rev) {
     if (block % kVChunk != 0 || npad % block != 0) return cudaErrorInvalidValue;
     const unsigned nch = (unsigned)(npad / kVChunk);
     double* chunks = centres + 3 * (npad / block);
     const SplitSums sv = ss != nullptr ? *ss : SplitSums();
+    const ReverseStep rv = rev != nullptr ? *rev : ReverseStep();
+    if (rev != nullptr && rev->x != nullptr) pos = rev->x;
     if (lam_f64 != nullptr) {
         vjp_step_kernel<double><<<nch, kVChunk, 0, st>>>(n, pos, lam_f64, lamx, gprev, gmprev, gm_acc, drift, chunks,
-                                                         sv);
+                                                         sv, rv);
         vjp_offsets_kernel<double><<<nch, kVChunk, 0, st>>>(n, block, pos, mass, lam_f64, kappa, mu, plain ? 1 : 0,
                                                             jv, centres, chunks);
     } else {
         vjp_step_kernel<const float><<<nch, kVChunk, 0, st>>>(n, pos, lam_f32, nullptr, nullptr, nullptr, nullptr, 0.0,
-                                                              chunks, sv);
+                                                              chunks, sv, rv);
         vjp_offsets_kernel<const float><<<nch, kVChunk, 0, st>>>(n, block, pos, mass, lam_f32, kappa, mu,
                                                                  plain ? 1 : 0, jv, centres, chunks);
     }
@@ -569,10 +641,11 @@ cudaError_t adjoint_accumulate(int64_t n, double* lamx, const float* g, double* 
 }
 
 cudaError_t vjp_launch(int k, const VjpArgs& a, int num_sms, cudaStream_t st, int* launched, cudaEvent_t ev0,
-                       cudaEvent_t ev1, SplitSums* defer) {
+                       cudaEvent_t ev1, SplitSums* defer, SplitSums* defer_acc) {
     const VShapeEntry& e = vshapes()[k];
     const int C = e.shape.block;
     const int mu = a.has_mu ? 1 : 0, mixed = a.centres != nullptr ? 1 : 0;
+    const bool force = a.acc != nullptr && !a.has_mu;
     VParams p;
     p.jv = a.jv;
     p.centres = a.centres;
@@ -581,30 +654,43 @@ cudaError_t vjp_launch(int k, const VjpArgs& a, int num_sms, cudaStream_t st, in
     p.nblk = a.npad / C;
     p.gpb = a.npad / kGranule;
     p.units = p.nblk * p.gpb;
-    p.nctas = std::min<int64_t>((int64_t)num_sms * vocc(k, mu, mixed), p.units);
+    p.nctas = std::min<int64_t>((int64_t)num_sms * vocc(k, force ? 2 : mu, mixed), p.units);
     p.g_pos = a.g_pos;
     p.g_mass = a.g_mass;
+    p.acc = force ? a.acc : nullptr;
     p.partial = a.partial;
+    p.partial_acc = a.partial + (size_t)p.nctas * 2 * C * 4;
     p.err = a.err;
     p.uni = a.uni;
     *launched = 0;
     if (ev0 != nullptr) cudaEventRecord(ev0, st);
-    e.fn[mu][mixed]<<<(unsigned)p.nctas, e.shape.threads, e.smem(mixed), st>>>(p);
+    VFn fn = force ? e.fnf[mixed] : e.fn[mu][mixed];
+    fn<<<(unsigned)p.nctas, e.shape.threads, e.smem(mixed), st>>>(p);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     *launched = 1;
     if (ev1 != nullptr) cudaEventRecord(ev1, st);
+    auto describe = [&](SplitSums* d, double* part) {
+        d->partial = p.nctas > 1 ? part : nullptr;
+        d->units = p.units;
+        d->nctas = p.nctas;
+        d->gpb = p.gpb;
+        d->block = C;
+    };
+    if (force && defer_acc != nullptr) {
+        describe(defer_acc, p.partial_acc);
+    } else if (force && p.nctas > 1) {
+        err = split_fixup(p.n, p.nblk, p.gpb, p.nctas, C, p.partial_acc, p.acc, nullptr, st, nullptr, p.err);
+        if (err != cudaSuccess) return err;
+        *launched += 1;
+    }
     if (defer != nullptr) {  // the next pack_vjp adds the split blocks' partials
-        defer->partial = p.nctas > 1 ? p.partial : nullptr;
-        defer->units = p.units;
-        defer->nctas = p.nctas;
-        defer->gpb = p.gpb;
-        defer->block = C;
+        describe(defer, p.partial);
         return cudaSuccess;
     }
     if (p.nctas > 1) {
         err = split_fixup(p.n, p.nblk, p.gpb, p.nctas, C, p.partial, p.g_pos, p.g_mass, st, nullptr, p.err);
-        if (err == cudaSuccess) *launched = 2;
+        if (err == cudaSuccess) *launched += 1;
     }
     return err;
 }

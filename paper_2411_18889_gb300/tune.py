@@ -3,8 +3,10 @@
 Miki & Hanawa chose the threads per block of their N-body kernel by a
 parameter survey on each machine (Sec. III.A).  This module does the same for
 every compiled shape of the force, VJP and batched kernels: it times each shape
-at a ladder of sizes (with and without the potential for the force) through
-the C ABI and writes the winners as a table the library reads
+at a ladder of sizes through the C ABI -- the force without the potential in
+a leapfrog of 4 steps (its hot path: evaluations and the packs between them),
+with the potential in single nbody_accel calls -- and writes the winners as a
+table the library reads
 (``nbody_tune.txt`` beside libnbody.so, or the file named by NBODY_TUNE_FILE).
 
     python -m paper_2411_18889_gb300.tune --out paper_2411_18889_gb300/nbody_tune.txt
@@ -67,16 +69,32 @@ def survey(sizes=(1024, 4096, 16384, 32768, 65536, 262144, 1048576),
     for pot in (0, 1):
         winners = []
         for n in sizes:
-            p, _, m = ni.plummer(n, 3, masses="loguniform", offset=ni.plummer_offset())
+            p, v, m = ni.plummer(n, 3, masses="loguniform", offset=ni.plummer_offset())
             P = torch.from_numpy(p).cuda()
             M = torch.from_numpy(m.astype(np.float32)).cuda()
-            acc = torch.empty((n, 3), dtype=torch.float32, device="cuda")
-            pt = torch.empty((n,), dtype=torch.float32, device="cuda") if pot else None
             reps = 2 if n >= (1 << 19) else 5
-            t = [_time(lambda k=k: api.nbody_accel(P, M, 2.0 ** -9, acc, pt, config=k), reps) for k in range(nf)]
+            if pot:
+                # the potential is wanted by single evaluations (nbody_accel, nbody_energy)
+                acc = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+                pt = torch.empty((n,), dtype=torch.float32, device="cuda")
+                evals = 1
+                t = [_time(lambda k=k: api.nbody_accel(P, M, 2.0 ** -9, acc, pt, config=k), reps)
+                     for k in range(nf)]
+            else:
+                # without it the hot path is the leapfrog: 4 steps (5 evaluations and their packs)
+                V0 = torch.from_numpy(v).cuda()
+                X, V = P.clone(), V0.clone()
+                evals = 5
+
+                def run(k):
+                    X.copy_(P)
+                    V.copy_(V0)
+                    api.nbody_leapfrog(X, V, M, 2.0 ** -9, 2.0 ** -9, 4, config=k)
+
+                t = [_time(lambda k=k: run(k), reps) for k in range(nf)]
             k = int(np.argmin(t))
             winners.append(k)
-            log(f"force pot={pot} n={n}: " + " ".join(f"{i}:{n * n / x / 1e9:.0f}" for i, x in enumerate(t))
+            log(f"force pot={pot} n={n}: " + " ".join(f"{i}:{evals * n * n / x / 1e9:.0f}" for i, x in enumerate(t))
                 + f" Gint/s -> {k}")
         for n_min, k in _rules(sizes, winners):
             lines.append(f"force {pot} {n_min} {k}")
