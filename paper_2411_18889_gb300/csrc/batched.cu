@@ -37,7 +37,11 @@
 //
 // Layout.  Shared memory holds the system (or a tile of a large one) as
 // j-pairs (x0,x1,y0,y1,z0,z1,m0,m1): 16 bytes per body, so a 4096-body system
-// takes 64 KiB.  Each thread keeps I i-bodies with their coordinates
+// takes 64 KiB.  In a leapfrog call a small system whose velocities fit
+// beside its image (12 more bytes per body) stays resident: every kick and
+// drift of the call is applied in shared memory and the state is written back
+// once, so no evaluation waits on global memory (on GB300 this lifted
+// 256-to-1024-body systems by 3 to 4 points of FP32 peak).  Each thread keeps I i-bodies with their coordinates
 // duplicated in f32x2 registers (x_i, x_i); one pair of 16-byte broadcast
 // loads gives two j-bodies and each i-body then takes the 12 (13 with the
 // potential) packed f32x2 instructions and two MUFU reciprocal square roots
@@ -87,6 +91,7 @@ struct BParams {
     float dt;
     int64_t steps;            // 0: force only
     int cap;                  // bodies the shared-memory image holds (multiple of 128 when large systems occur)
+    int smem;                 // dynamic shared memory of the launch, bytes
     int grid;                 // CTAs of the launch
     int* err;                 // error word
 };
@@ -211,12 +216,44 @@ __device__ __forceinline__ void body_out(const BParams& p, int64_t g, f2 sx, f2 
     }
 }
 
+// Shared memory a small system takes when it stays resident for all steps of
+// a leapfrog call: its image and its velocities ([ns][3] floats after the
+// image, 16-byte aligned).
+__host__ __device__ __forceinline__ int resident_bytes(int ns) {
+    return 32 * ((ns + 1) >> 1) + ((12 * ns + 15) & ~15);
+}
+
+// The kick of i-body b (index within its system) of a resident system: its
+// velocity is read and written in shared memory, with the same FP32
+// operations body_out applies to the copy in global memory.
+template <bool UNI>
+__device__ __forceinline__ void body_kick_resident(float* sv, int b, f2 sx, f2 sy, f2 sz, float mu, float kick) {
+    float a0, a1;
+    upk(sx, a0, a1);
+    float ax = a0 + a1;
+    upk(sy, a0, a1);
+    float ay = a0 + a1;
+    upk(sz, a0, a1);
+    float az = a0 + a1;
+    if (UNI) {
+        ax *= mu;
+        ay *= mu;
+        az *= mu;
+    }
+    float* v = sv + 3 * b;
+    v[0] = fmaf(kick, ax, v[0]);
+    v[1] = fmaf(kick, ay, v[1]);
+    v[2] = fmaf(kick, az, v[2]);
+}
+
 // Small systems: one pass of I i-bodies per thread (slot k of thread t is
-// body base + k*T + t) against every j-pair of the system's image.
-template <int T, int I, bool POT, bool MASK, bool UNI, int U, int JB>
-__device__ __forceinline__ void eval_pass(const float* __restrict__ sj, int npair, int ns, int base, f2 eps2,
-                                          const BParams& p, int64_t off, int64_t ntot, float kick, bool drift,
-                                          float mu) {
+// body base + k*T + t) against every j-pair of the system's image.  RES: the
+// system is resident (velocities in shared memory at sv; the drift is applied
+// to the image after the pass, by run_small).
+template <int T, int I, bool POT, bool MASK, bool UNI, bool RES, int U, int JB>
+__device__ __forceinline__ void eval_pass(const float* __restrict__ sj, float* sv, int npair, int ns, int base,
+                                          f2 eps2, const BParams& p, int64_t off, int64_t ntot, float kick,
+                                          bool drift, float mu) {
     static_assert(T % 32 == 0 && JB % 16 == 0, "a warp's 32 bodies of a slot lie in one j-block");
     const int tid = threadIdx.x;
     f2 xi[I], yi[I], zi[I];
@@ -238,6 +275,10 @@ __device__ __forceinline__ void eval_pass(const float* __restrict__ sj, int npai
 #pragma unroll
     for (int k = 0; k < I; ++k) {
         if (ib[k] >= ns) continue;
+        if (RES) {
+            body_kick_resident<UNI>(sv, ib[k], tx[k], ty[k], tz[k], mu, kick);
+            continue;
+        }
         const int64_t g = off + ib[k];
         if (!in_range(g, ntot, p.err)) continue;
         body_out<POT, UNI>(p, g, tx[k], ty[k], tz[k], tp[k], mu, kick, drift);
@@ -245,18 +286,21 @@ __device__ __forceinline__ void eval_pass(const float* __restrict__ sj, int npai
 }
 
 // eval_pass with I' = min(I, left) i-bodies per thread.
-template <int T, int I, bool POT, bool MASK, bool UNI, int U, int JB>
-__device__ __forceinline__ void pass_dispatch(int left, const float* __restrict__ sj, int npair, int ns, int base,
-                                              f2 eps2, const BParams& p, int64_t off, int64_t ntot, float kick,
-                                              bool drift, float mu) {
+template <int T, int I, bool POT, bool MASK, bool UNI, bool RES, int U, int JB>
+__device__ __forceinline__ void pass_dispatch(int left, const float* __restrict__ sj, float* sv, int npair, int ns,
+                                              int base, f2 eps2, const BParams& p, int64_t off, int64_t ntot,
+                                              float kick, bool drift, float mu) {
     if (I >= 4 && left >= 4) {
-        eval_pass<T, (I >= 4 ? 4 : 1), POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, ntot, kick, drift, mu);
+        eval_pass<T, (I >= 4 ? 4 : 1), POT, MASK, UNI, RES, U, JB>(sj, sv, npair, ns, base, eps2, p, off, ntot, kick,
+                                                                   drift, mu);
     } else if (I >= 3 && left >= 3) {
-        eval_pass<T, (I >= 3 ? 3 : 1), POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, ntot, kick, drift, mu);
+        eval_pass<T, (I >= 3 ? 3 : 1), POT, MASK, UNI, RES, U, JB>(sj, sv, npair, ns, base, eps2, p, off, ntot, kick,
+                                                                   drift, mu);
     } else if (I >= 2 && left >= 2) {
-        eval_pass<T, (I >= 2 ? 2 : 1), POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, ntot, kick, drift, mu);
+        eval_pass<T, (I >= 2 ? 2 : 1), POT, MASK, UNI, RES, U, JB>(sj, sv, npair, ns, base, eps2, p, off, ntot, kick,
+                                                                   drift, mu);
     } else {
-        eval_pass<T, 1, POT, MASK, UNI, U, JB>(sj, npair, ns, base, eps2, p, off, ntot, kick, drift, mu);
+        eval_pass<T, 1, POT, MASK, UNI, RES, U, JB>(sj, sv, npair, ns, base, eps2, p, off, ntot, kick, drift, mu);
     }
 }
 
@@ -301,8 +345,15 @@ __device__ __forceinline__ bool uniform_system(const BParams& p, int64_t off, in
     return __syncthreads_and(same) != 0;
 }
 
-// A small system, owned by this CTA for all steps of the call.
-template <int T, int I, bool POT, int U, int JB>
+// A small system, owned by this CTA for all steps of the call.  RES (a
+// leapfrog call whose system fits resident_bytes): positions and velocities
+// are read from global memory once, every kick and drift of the call is
+// applied in shared memory, and both are written back once at the end, so no
+// evaluation waits on global memory.  Otherwise every evaluation kicks (and
+// drifts) the bodies in global memory and reloads the image from there.  The
+// two give the same bits: each update is the same FP32 operation on the same
+// operands.
+template <int T, int I, bool POT, int U, int JB, bool RES>
 __device__ void run_small(float* sj, const BParams& p, int s, int64_t ntot) {
     const int64_t off = p.offsets[s];
     const int ns = (int)(p.offsets[s + 1] - off);
@@ -311,9 +362,17 @@ __device__ void run_small(float* sj, const BParams& p, int s, int64_t ntot) {
     const float eps2s = e * e;
     const f2 eps2 = pk(eps2s, eps2s);
     const int npair = (ns + 1) >> 1;
+    float* sv = sj + 8 * npair;  // RES: the velocities, [ns][3]
     float mu;
     const bool uni = uniform_system(p, off, ns, ntot, &mu);
     load_image(sj, p, off, ns, ntot);
+    if (RES) {
+        for (int q = threadIdx.x; q < 3 * ns; q += T) {
+            float v = 0.0f;
+            if (in_range(off + q / 3, ntot, p.err)) v = p.vel[3 * off + q];
+            sv[q] = v;
+        }
+    }
     __syncthreads();
     for (int64_t ev = 0; ev <= p.steps; ++ev) {
         const float kick = (p.steps == 0) ? 0.0f : ((ev == 0 || ev == p.steps) ? 0.5f * p.dt : p.dt);
@@ -328,26 +387,47 @@ __device__ void run_small(float* sj, const BParams& p, int s, int64_t ntot) {
             if (left == 0) {
             } else if (POT || eps2s == 0.0f) {  // the self pair must be excluded
                 if (uni)
-                    pass_dispatch<T, I, POT, true, true, U, JB>(left, sj, npair, ns, base, eps2, p, off, ntot, kick,
-                                                                drift, mu);
+                    pass_dispatch<T, I, POT, true, true, RES, U, JB>(left, sj, sv, npair, ns, base, eps2, p, off,
+                                                                     ntot, kick, drift, mu);
                 else
-                    pass_dispatch<T, I, POT, true, false, U, JB>(left, sj, npair, ns, base, eps2, p, off, ntot, kick,
-                                                                 drift, mu);
+                    pass_dispatch<T, I, POT, true, false, RES, U, JB>(left, sj, sv, npair, ns, base, eps2, p, off,
+                                                                      ntot, kick, drift, mu);
             } else {
                 if (uni)
-                    pass_dispatch<T, I, POT, false, true, U, JB>(left, sj, npair, ns, base, eps2, p, off, ntot,
-                                                                 kick, drift, mu);
+                    pass_dispatch<T, I, POT, false, true, RES, U, JB>(left, sj, sv, npair, ns, base, eps2, p, off,
+                                                                      ntot, kick, drift, mu);
                 else
-                    pass_dispatch<T, I, POT, false, false, U, JB>(left, sj, npair, ns, base, eps2, p, off, ntot,
-                                                                  kick, drift, mu);
+                    pass_dispatch<T, I, POT, false, false, RES, U, JB>(left, sj, sv, npair, ns, base, eps2, p, off,
+                                                                       ntot, kick, drift, mu);
             }
         }
         __syncthreads();
         if (drift) {
-            load_image(sj, p, off, ns, ntot);  // the drifted positions of this step
+            if (RES) {
+                // every thread has read this evaluation's positions: drift the image in place
+                for (int b = threadIdx.x; b < ns; b += T) {
+                    float* d = sj + (b >> 1) * 8 + (b & 1);
+                    d[0] = fmaf(p.dt, sv[3 * b + 0], d[0]);
+                    d[2] = fmaf(p.dt, sv[3 * b + 1], d[2]);
+                    d[4] = fmaf(p.dt, sv[3 * b + 2], d[4]);
+                }
+            } else {
+                load_image(sj, p, off, ns, ntot);  // the drifted positions of this step
+            }
             __syncthreads();
         }
         if (threadIdx.x == 0) atomicAdd(p.heartbeat, 1u);
+    }
+    if (RES) {
+        for (int b = threadIdx.x; b < ns; b += T) {
+            if (!in_range(off + b, ntot, p.err)) continue;
+            const float* d = sj + (b >> 1) * 8 + (b & 1);
+            p.pos[3 * (off + b) + 0] = d[0];
+            p.pos[3 * (off + b) + 1] = d[2];
+            p.pos[3 * (off + b) + 2] = d[4];
+        }
+        for (int q = threadIdx.x; q < 3 * ns; q += T)
+            if (in_range(off + q / 3, ntot, p.err)) p.vel[3 * off + q] = sv[q];
     }
 }
 
@@ -530,16 +610,18 @@ __global__ void __launch_bounds__(T) batched_kernel(const BParams p) {
     extern __shared__ __align__(16) float sj[];
     __shared__ unsigned long long s_item;
     if (p.plan[kPlanInvalid] != 0) return;  // a bad batch: nothing is written
-    const int64_t L = p.plan[kPlanLarge];
-    const int64_t TL = p.plan[kPlanLargeItems];
-    const int64_t ntot = p.plan[kPlanBodies];
-    const unsigned long long nitems = (unsigned long long)(TL + (p.nsys - L));
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(p.queue, 1ull);
         __syncthreads();
         const unsigned long long k = s_item;
         __syncthreads();
-        if (k >= nitems) break;
+        // The plan words are read again for every item rather than held in
+        // registers across the item loop: kept live they pushed the pair loop
+        // of the 512-thread shape to a 4-byte spill (128 registers).
+        const int64_t L = __ldcg(p.plan + kPlanLarge);
+        const int64_t TL = __ldcg(p.plan + kPlanLargeItems);
+        const int64_t ntot = __ldcg(p.plan + kPlanBodies);
+        if (k >= (unsigned long long)(TL + (p.nsys - L))) break;
         if ((int64_t)k < TL) {
             // large system r of the order, lprefix[r] <= k < lprefix[r + 1]
             int64_t lo = 0, hi = L;
@@ -559,7 +641,11 @@ __global__ void __launch_bounds__(T) batched_kernel(const BParams p) {
             if (!in_range(r, p.nsys, p.err)) continue;
             const int s = p.order[r];
             if (!in_range(s, p.nsys, p.err)) continue;
-            run_small<T, I, POT, U, JB>(sj, p, s, ntot);
+            const int64_t ns = p.offsets[s + 1] - p.offsets[s];
+            if (p.steps > 0 && ns <= p.cap && resident_bytes((int)ns) <= p.smem)
+                run_small<T, I, POT, U, JB, true>(sj, p, s, ntot);
+            else
+                run_small<T, I, POT, U, JB, false>(sj, p, s, ntot);
         }
         __syncthreads();  // the shared image is reused by the next item
     }
@@ -722,9 +808,9 @@ size_t batched_smem_bytes(int cap) { return (size_t)((cap + 1) / 2) * 8 * sizeof
 
 size_t batched_scratch_bytes(int64_t nsys) { return carve(nullptr, nsys).total; }
 
-int batched_max_cap(int k) {
-    // The image of shape k may take as much shared memory as still lets the
-    // CTAs its registers allow share an SM; never more than one CTA may hold.
+// The shared memory a CTA of shape k may take and still let the CTAs its
+// registers allow share an SM; never more than one CTA may hold.
+static int cta_smem_limit(int k) {
     const BShapeEntry& e = bshapes()[k];
     int dev = 0, optin = 48 * 1024, per_sm = 48 * 1024, occ = 1;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -734,15 +820,20 @@ int batched_max_cap(int k) {
         (void)cudaGetLastError();
     }
     occ = std::max(occ, 1);
-    const int per_cta = std::min(optin, per_sm / occ) - 1024;  // room for static shared memory and the runtime's share
-    return std::max(128, per_cta / 16 / 128 * 128);
+    return std::min(optin, per_sm / occ) - 1024;  // room for static shared memory and the runtime's share
 }
+
+int batched_max_cap(int k) { return std::max(128, cta_smem_limit(k) / 16 / 128 * 128); }
 
 cudaError_t batched_launch(int k, const BatchArgs& a, int num_sms, cudaStream_t st, int* launched) {
     *launched = 0;
     const BShapeEntry& e = bshapes()[k];
     const int pot = a.pot != nullptr ? 1 : 0;
-    const size_t smem = std::max<size_t>(batched_smem_bytes(a.cap), 16);
+    // The image of the largest small system; a leapfrog call takes more, up to
+    // the CTA's share, so that systems keep their velocities resident too.
+    size_t smem = std::max<size_t>(batched_smem_bytes(a.cap), 16);
+    if (a.steps > 0)
+        smem = std::max(smem, std::min<size_t>((size_t)resident_bytes(a.cap), (size_t)cta_smem_limit(k)));
     cudaError_t err = cudaFuncSetAttribute(e.fn[pot], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int occ = 0;
@@ -795,6 +886,7 @@ cudaError_t batched_launch(int k, const BatchArgs& a, int num_sms, cudaStream_t 
     p.dt = a.dt;
     p.steps = a.steps;
     p.cap = a.cap;
+    p.smem = (int)smem;
     p.grid = grid;
     p.err = a.err;
     cudaLaunchConfig_t cfg = {};

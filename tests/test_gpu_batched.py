@@ -128,6 +128,37 @@ def test_leapfrog_batched_matches_oracle(nb, oracle_mod):
             assert abs(eg - er) <= 1e-5 * abs(e0), s
 
 
+@pytest.mark.parametrize("device_offsets", [False, True])
+def test_leapfrog_resident_and_streamed_agree(nb, oracle_mod, device_offsets):
+    """A leapfrog call keeps a system's positions and velocities in shared
+    memory for all steps when they fit beside its image (28 bytes a body),
+    else kicks and drifts them in global memory every step.  Both apply the
+    same FP32 operations, and every shape sums a body's pairs in the same
+    blocks, so the results must be bit-identical: the 5000-body member is
+    resident on shape 0 (one CTA per SM, about 226 KB of shared memory) and
+    streamed on shape 2 (two CTAs per SM, about 113 KB); the others are
+    resident on both."""
+    import torch
+    sizes = [5000, 3000, 1, 700, 64, 0, 2]
+    off, pos, vel, mass, eps = make_batch(sizes, 37)
+    dt, steps = 2.0 ** -8, 8
+    out = []
+    for shape in (0, 2):
+        P, V = t(pos, np.float32), t(vel, np.float32)
+        O = t(off, np.int64) if device_offsets else off
+        nb.nbody_leapfrog_batched(O, P, V, t(mass, np.float32), t(eps, np.float32), dt, steps, config=shape)
+        torch.cuda.synchronize()
+        assert nb.nbody_last_device_error() == 0
+        out.append((P.cpu().numpy(), V.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    pg, vg = out[0][0].astype(np.float64), out[0][1].astype(np.float64)
+    for s in (0, 3):
+        a, b = off[s], off[s + 1]
+        pr, vr, _ = oracle_mod.leapfrog(pos[a:b], vel[a:b], mass[a:b], eps[s], dt, steps)
+        assert np.abs(pg[a:b] - pr).max() <= 2e-5, s
+        assert np.abs(vg[a:b] - vr).max() <= 2e-4, s
+
+
 # Systems larger than one CTA's shared-memory image (about 14,000 bodies for
 # shape 0, 4096 for the others when the sizes are not known on the host) are
 # split over several CTAs that stream the bodies in tiles.
