@@ -29,11 +29,20 @@
 //
 // Shapes (chosen by the largest system of the batch through the tune table
 // when the host knows the sizes; shape 0 otherwise).  From about 760 bodies
-// up one 512-thread CTA per SM owns a system (16 warps on one system,
-// i-passes of 2048 bodies); smaller batches run 256- or 128-thread CTAs,
-// several per SM, each on its own system.  On GB300 the single large CTA ran
-// the ragged 64-to-4096-body workload at 71.7 % of FP32 peak against 66.1 %
-// for two 256-thread CTAs per SM.
+// up one 512-thread CTA per SM owns a system (16 warps on one system, up to
+// 4 slots of 32 i-bodies a warp); smaller batches run 256- or 128-thread
+// CTAs, several per SM, each on its own system.  On GB300 the single large
+// CTA ran the ragged 64-to-4096-body workload at 71.7 % of FP32 peak against
+// 66.1 % for two 256-thread CTAs per SM.
+//
+// Rounds.  A system of S slots (32-body groups) runs whole rounds, every warp
+// taking I1 slots against all j-pairs, and then its remainder: spread over
+// the warps, or, when few slots are left, in groups whose j-pairs are cut
+// into segments, one warp per group and segment, the segment sums added in
+// shared memory in segment order.  The host picks each S's plan by a cost
+// model of the SM's four schedulers fitted on GB300.  A 2112-body system
+// no longer runs its last 64 bodies on two warps while 14 wait: on GB300 the
+// ragged workload went from 71.1 % to 73.6 % of FP32 peak.
 //
 // Layout.  Shared memory holds the system (or a tile of a large one) as
 // j-pairs (x0,x1,y0,y1,z0,z1,m0,m1): 16 bytes per body, so a 4096-body system
@@ -64,6 +73,9 @@
 // self pair is exactly zero, so it adds exactly 0 to the acceleration.
 #include <algorithm>
 #include <climits>
+#include <cstring>
+#include <memory>
+#include <mutex>
 
 #include "nbody_internal.cuh"
 
@@ -72,6 +84,10 @@ namespace {
 
 // Plan words (int64, on the device), written by the planning kernels.
 enum PlanWord { kPlanInvalid = 0, kPlanLarge = 1, kPlanLargeItems = 2, kPlanBodies = 3, kPlanWords = 4 };
+
+// Entries of the round-plan table: small systems of up to 32 * kRoundSlots - 1
+// bodies (every shape's image capacity is below that).
+constexpr int kRoundSlots = 512;
 
 struct BParams {
     int64_t nsys;
@@ -94,6 +110,7 @@ struct BParams {
     int smem;                 // dynamic shared memory of the launch, bytes
     int grid;                 // CTAs of the launch
     int* err;                 // error word
+    unsigned short rounds[kRoundSlots];  // round plan of a small system, by its number of 32-body slots
 };
 
 // One block of j-pairs [jb, je) against the thread's I i-bodies.  M: zero the
@@ -137,26 +154,30 @@ __device__ __forceinline__ void jblock(const ulonglong2* __restrict__ sp, int jb
     }
 }
 
-// The pairs of a j-array image of npair pairs against the thread's I
-// i-bodies, into the FP32 totals t*: FP32 partial sums over blocks of JB
-// pairs folded into t*.  MASK: exclude the self pair; ib[k] is body k's index
-// relative to the image and (ws[k] >> 1) its warp's first pair, or negative
-// when the warp's bodies of slot k are not in this image.
+// The pairs [p0, p1) of a j-array image against the thread's I i-bodies, into
+// the FP32 totals t*: FP32 partial sums over blocks of JB pairs (counted from
+// p0) folded into t*.  MASK: exclude the self pair; ib[k] is body k's index
+// relative to the image (negative or past its end when not in it).  A warp's
+// 32 bodies of a slot start at a multiple of 32, ib[k] & ~31, so their 16
+// self pairs are known without another register, and only the blocks holding
+// them run the masked loop.
 template <int I, bool POT, bool MASK, bool UNI, int U, int JB>
-__device__ __forceinline__ void image_sum(const float* __restrict__ sj, int npair, const f2 (&xi)[I],
-                                          const f2 (&yi)[I], const f2 (&zi)[I], const int (&ib)[I],
-                                          const int (&ws)[I], f2 eps2, f2 (&tx)[I], f2 (&ty)[I], f2 (&tz)[I],
-                                          f2 (&tp)[I]) {
+__device__ __forceinline__ void image_sum(const float* __restrict__ sj, int p0, int p1, const f2 (&xi)[I],
+                                          const f2 (&yi)[I], const f2 (&zi)[I], const int (&ib)[I], f2 eps2,
+                                          f2 (&tx)[I], f2 (&ty)[I], f2 (&tz)[I], f2 (&tp)[I]) {
     const ulonglong2* sp = reinterpret_cast<const ulonglong2*>(sj);
-    for (int jb = 0; jb < npair; jb += JB) {
-        const int je = min(npair, jb + JB);
+    for (int jb = p0; jb < p1; jb += JB) {
+        const int je = min(p1, jb + JB);
         f2 ax[I], ay[I], az[I], ap[I];
 #pragma unroll
         for (int k = 0; k < I; ++k) ax[k] = ay[k] = az[k] = ap[k] = 0ull;
         bool own = false;
         if (MASK) {
 #pragma unroll
-            for (int k = 0; k < I; ++k) own = own || (ws[k] >= 0 && ((ws[k] >> 1) / JB) * JB == jb);
+            for (int k = 0; k < I; ++k) {
+                const int w0 = (ib[k] & ~31) >> 1;  // the warp's first pair (floor, also for negative ib)
+                own = own || (w0 < je && w0 + 16 > jb);
+            }
         }
         if (own)
             jblock<I, POT, true, UNI, U>(sp, jb, je, xi, yi, zi, ib, eps2, ax, ay, az, ap);
@@ -172,33 +193,41 @@ __device__ __forceinline__ void image_sum(const float* __restrict__ sj, int npai
     }
 }
 
-// Result of one i-body g of the batch from its summed pair halves: the
-// acceleration (and potential) of a force-only call, or the kick (and, for
-// small systems, the drift) of a leapfrog evaluation.
-template <bool POT, bool UNI>
-__device__ __forceinline__ void body_out(const BParams& p, int64_t g, f2 sx, f2 sy, f2 sz, f2 sp, float mu,
-                                         float kick, bool drift) {
+// The two halves (even and odd j) of an accumulator, added.
+__device__ __forceinline__ float hsum(f2 v) {
     float a0, a1;
-    upk(sx, a0, a1);
-    float ax = a0 + a1;
-    upk(sy, a0, a1);
-    float ay = a0 + a1;
-    upk(sz, a0, a1);
-    float az = a0 + a1;
+    upk(v, a0, a1);
+    return a0 + a1;
+}
+
+// Result of body b of a system (g = off + b in the batch) from its sums: the
+// acceleration (and potential) of a force-only call, or the kick (and, for a
+// small system, the drift) of a leapfrog evaluation.  RES: the system is
+// resident, its velocities at sv in shared memory; the drift is applied to the
+// image afterwards.  Resident or not, each update is the same FP32 operation.
+template <bool POT, bool UNI, bool RES>
+__device__ __forceinline__ void finish_body(const BParams& p, float* sv, int b, int64_t g, int64_t ntot, float ax,
+                                            float ay, float az, float pt, float mu, float kick, bool drift) {
     if (UNI) {
         ax *= mu;
         ay *= mu;
         az *= mu;
     }
+    if (RES) {
+        float* v = sv + 3 * b;
+        v[0] = fmaf(kick, ax, v[0]);
+        v[1] = fmaf(kick, ay, v[1]);
+        v[2] = fmaf(kick, az, v[2]);
+        return;
+    }
+    if (!in_range(g, ntot, p.err)) return;
     if (p.steps == 0) {
         p.acc[3 * g + 0] = ax;
         p.acc[3 * g + 1] = ay;
         p.acc[3 * g + 2] = az;
         if (POT) {
-            upk(sp, a0, a1);
-            float s = a0 + a1;
-            if (UNI) s *= mu;
-            p.pot[g] = -s;
+            if (UNI) pt *= mu;
+            p.pot[g] = -pt;
         }
     } else {
         float vx = p.vel[3 * g + 0], vy = p.vel[3 * g + 1], vz = p.vel[3 * g + 2];
@@ -223,85 +252,96 @@ __host__ __device__ __forceinline__ int resident_bytes(int ns) {
     return 32 * ((ns + 1) >> 1) + ((12 * ns + 15) & ~15);
 }
 
-// The kick of i-body b (index within its system) of a resident system: its
-// velocity is read and written in shared memory, with the same FP32
-// operations body_out applies to the copy in global memory.
-template <bool UNI>
-__device__ __forceinline__ void body_kick_resident(float* sv, int b, f2 sx, f2 sy, f2 sz, float mu, float kick) {
-    float a0, a1;
-    upk(sx, a0, a1);
-    float ax = a0 + a1;
-    upk(sy, a0, a1);
-    float ay = a0 + a1;
-    upk(sz, a0, a1);
-    float az = a0 + a1;
-    if (UNI) {
-        ax *= mu;
-        ay *= mu;
-        az *= mu;
-    }
-    float* v = sv + 3 * b;
-    v[0] = fmaf(kick, ax, v[0]);
-    v[1] = fmaf(kick, ay, v[1]);
-    v[2] = fmaf(kick, az, v[2]);
-}
+// The staging area of a shape with T threads and I slots a warp: a split
+// round stages at most T * I bodies' partial sums (4 floats each).
+__host__ __device__ constexpr int stage_bytes(int T, int I) { return T * I * 16; }
 
-// Small systems: one pass of I i-bodies per thread (slot k of thread t is
-// body base + k*T + t) against every j-pair of the system's image.  RES: the
-// system is resident (velocities in shared memory at sv; the drift is applied
-// to the image after the pass, by run_small).
-template <int T, int I, bool POT, bool MASK, bool UNI, bool RES, int U, int JB>
-__device__ __forceinline__ void eval_pass(const float* __restrict__ sj, float* sv, int npair, int ns, int base,
-                                          f2 eps2, const BParams& p, int64_t off, int64_t ntot, float kick,
-                                          bool drift, float mu) {
-    static_assert(T % 32 == 0 && JB % 16 == 0, "a warp's 32 bodies of a slot lie in one j-block");
-    const int tid = threadIdx.x;
-    f2 xi[I], yi[I], zi[I];
-    int ib[I], ws[I];
+// Where a split task stages its partial sums: component c of body b goes to
+// sv[so + c * rb + b], sv being the first float after the image.  rb == 0:
+// the task's sums are complete.  (Two integers, as they stay live across the
+// pair loop.)
+struct Staging {
+    int so;  // float offset from sv of the task's segment, less its first staged body
+    int rb;  // bodies staged (one component of one segment)
+};
+
+// One task of an evaluation of a small system: N slots of 32 bodies (lane l
+// takes body b0 + k*stride + l of slot k) against the j-pairs [p0, p1) of the
+// system's image.  With st.rb == 0 the sums are complete and the bodies are
+// finished here; otherwise they are one segment of their sums and go to the
+// staging area for run_small to add up.
+template <int T, int N, bool POT, bool MASK, bool UNI, bool RES, int U, int JB>
+__device__ __forceinline__ void eval_task(const float* __restrict__ sj, float* sv, int ns, int b0, int stride, int p0,
+                                          int p1, f2 eps2, const BParams& p, int64_t off, int64_t ntot, float kick,
+                                          bool drift, float mu, const Staging& st) {
+    static_assert(T % 32 == 0 && JB % 16 == 0, "a warp's 32 bodies of a slot are 16 consecutive pairs");
+    const int lane = threadIdx.x & 31;
+    f2 xi[N], yi[N], zi[N];
+    int ib[N];
 #pragma unroll
-    for (int k = 0; k < I; ++k) {
-        ib[k] = base + k * T + tid;
-        ws[k] = base + k * T + 32 * (tid >> 5);
-        const int b = ib[k] < ns ? ib[k] : 0;  // threads past the end repeat body 0 and write nothing
+    for (int k = 0; k < N; ++k) {
+        ib[k] = b0 + k * stride + lane;
+        const int b = ib[k] < ns ? ib[k] : 0;  // lanes past the end repeat body 0 and write nothing
         const float* s = sj + (b >> 1) * 8 + (b & 1);
         xi[k] = pk(s[0], s[0]);
         yi[k] = pk(s[2], s[2]);
         zi[k] = pk(s[4], s[4]);
     }
-    f2 tx[I], ty[I], tz[I], tp[I];
+    f2 tx[N], ty[N], tz[N], tp[N];
 #pragma unroll
-    for (int k = 0; k < I; ++k) tx[k] = ty[k] = tz[k] = tp[k] = 0ull;
-    image_sum<I, POT, MASK, UNI, U, JB>(sj, npair, xi, yi, zi, ib, ws, eps2, tx, ty, tz, tp);
+    for (int k = 0; k < N; ++k) tx[k] = ty[k] = tz[k] = tp[k] = 0ull;
+    image_sum<N, POT, MASK, UNI, U, JB>(sj, p0, p1, xi, yi, zi, ib, eps2, tx, ty, tz, tp);
 #pragma unroll
-    for (int k = 0; k < I; ++k) {
+    for (int k = 0; k < N; ++k) {
         if (ib[k] >= ns) continue;
-        if (RES) {
-            body_kick_resident<UNI>(sv, ib[k], tx[k], ty[k], tz[k], mu, kick);
+        const float ax = hsum(tx[k]), ay = hsum(ty[k]), az = hsum(tz[k]);
+        const float pt = POT ? hsum(tp[k]) : 0.0f;
+        if (st.rb != 0) {
+            float* d = sv + st.so + ib[k];
+            d[0] = ax;
+            d[st.rb] = ay;
+            d[2 * st.rb] = az;
+            if (POT) d[3 * st.rb] = pt;
             continue;
         }
-        const int64_t g = off + ib[k];
-        if (!in_range(g, ntot, p.err)) continue;
-        body_out<POT, UNI>(p, g, tx[k], ty[k], tz[k], tp[k], mu, kick, drift);
+        finish_body<POT, UNI, RES>(p, sv, ib[k], off + ib[k], ntot, ax, ay, az, pt, mu, kick, drift);
     }
 }
 
-// eval_pass with I' = min(I, left) i-bodies per thread.
-template <int T, int I, bool POT, bool MASK, bool UNI, bool RES, int U, int JB>
-__device__ __forceinline__ void pass_dispatch(int left, const float* __restrict__ sj, float* sv, int npair, int ns,
-                                              int base, f2 eps2, const BParams& p, int64_t off, int64_t ntot,
-                                              float kick, bool drift, float mu) {
-    if (I >= 4 && left >= 4) {
-        eval_pass<T, (I >= 4 ? 4 : 1), POT, MASK, UNI, RES, U, JB>(sj, sv, npair, ns, base, eps2, p, off, ntot, kick,
-                                                                   drift, mu);
-    } else if (I >= 3 && left >= 3) {
-        eval_pass<T, (I >= 3 ? 3 : 1), POT, MASK, UNI, RES, U, JB>(sj, sv, npair, ns, base, eps2, p, off, ntot, kick,
-                                                                   drift, mu);
-    } else if (I >= 2 && left >= 2) {
-        eval_pass<T, (I >= 2 ? 2 : 1), POT, MASK, UNI, RES, U, JB>(sj, sv, npair, ns, base, eps2, p, off, ntot, kick,
-                                                                   drift, mu);
-    } else {
-        eval_pass<T, 1, POT, MASK, UNI, RES, U, JB>(sj, sv, npair, ns, base, eps2, p, off, ntot, kick, drift, mu);
+// eval_task with n (1 to I) slots, the self-pair mask and the equal-mass loop
+// chosen at run time.
+template <int T, int I, bool POT, bool RES, int U, int JB>
+__device__ __forceinline__ void run_task(bool mask, bool uni, int n, const float* __restrict__ sj, float* sv, int ns,
+                                         int b0, int stride, int p0, int p1, f2 eps2, const BParams& p, int64_t off,
+                                         int64_t ntot, float kick, bool drift, float mu, const Staging& st) {
+#define NBK_TASK(N_, M_, U_)                                                                                        \
+    eval_task<T, (I >= N_ ? N_ : 1), POT, M_, U_, RES, U, JB>(sj, sv, ns, b0, stride, p0, p1, eps2, p, off, ntot, \
+                                                              kick, drift, mu, st)
+#define NBK_TASKN(M_, U_)                   \
+    if (I >= 4 && n >= 4) {                 \
+        NBK_TASK(4, M_, U_);                \
+    } else if (I >= 3 && n == 3) {          \
+        NBK_TASK(3, M_, U_);                \
+    } else if (I >= 2 && n == 2) {          \
+        NBK_TASK(2, M_, U_);                \
+    } else {                                \
+        NBK_TASK(1, M_, U_);                \
     }
+    if (mask) {
+        if (uni) {
+            NBK_TASKN(true, true)
+        } else {
+            NBK_TASKN(true, false)
+        }
+    } else {
+        if (uni) {
+            NBK_TASKN(false, true)
+        } else {
+            NBK_TASKN(false, false)
+        }
+    }
+#undef NBK_TASKN
+#undef NBK_TASK
 }
 
 // Position load; CG: through L2 only (ld.global.cg), for positions another
@@ -345,16 +385,28 @@ __device__ __forceinline__ bool uniform_system(const BParams& p, int64_t off, in
     return __syncthreads_and(same) != 0;
 }
 
+// Round plan of a small system of S slots (32-body groups), from the table the
+// host builds per shape (BParams::rounds, indexed by S): F full rounds in
+// which every warp takes I1 slots against all j-pairs, then the R = S - F*W*I1
+// slots left over, either spread (warp w takes slots w, w + W, ... against all
+// j-pairs) or split (groups of I2 slots, each group's j-pairs cut into G
+// segments, one warp per group and segment, partial sums added up in shared
+// memory in segment order).
+enum RoundMode { kRoundNone = 0, kRoundSpread = 1, kRoundSplit = 2 };
+__host__ __device__ __forceinline__ unsigned short round_entry(int I1, int mode, int I2, int G) {
+    return (unsigned short)((I1 - 1) | (mode << 2) | ((I2 - 1) << 4) | ((G - 1) << 6));
+}
+
 // A small system, owned by this CTA for all steps of the call.  RES (a
-// leapfrog call whose system fits resident_bytes): positions and velocities
-// are read from global memory once, every kick and drift of the call is
-// applied in shared memory, and both are written back once at the end, so no
-// evaluation waits on global memory.  Otherwise every evaluation kicks (and
-// drifts) the bodies in global memory and reloads the image from there.  The
-// two give the same bits: each update is the same FP32 operation on the same
-// operands.
+// leapfrog call whose system fits resident_bytes and the staging area):
+// positions and velocities are read from global memory once, every kick and
+// drift of the call is applied in shared memory, and both are written back
+// once at the end, so no evaluation waits on global memory.  Otherwise every
+// evaluation kicks (and drifts) the bodies in global memory and reloads the
+// image from there.  The two give the same bits.
 template <int T, int I, bool POT, int U, int JB, bool RES>
 __device__ void run_small(float* sj, const BParams& p, int s, int64_t ntot) {
+    constexpr int W = T / 32;
     const int64_t off = p.offsets[s];
     const int ns = (int)(p.offsets[s + 1] - off);
     if (ns <= 0) return;
@@ -362,9 +414,12 @@ __device__ void run_small(float* sj, const BParams& p, int s, int64_t ntot) {
     const float eps2s = e * e;
     const f2 eps2 = pk(eps2s, eps2s);
     const int npair = (ns + 1) >> 1;
-    float* sv = sj + 8 * npair;  // RES: the velocities, [ns][3]
+    float* sv = sj + 8 * npair;                     // RES: the velocities, [ns][3]
+    const int so0 = RES ? ((3 * ns + 3) & ~3) : 0;  // the staging area of split tasks, from sv
+    const float* stg = sv + so0;
     float mu;
     const bool uni = uniform_system(p, off, ns, ntot, &mu);
+    const bool mask = POT || eps2s == 0.0f;  // the self pair must be excluded
     load_image(sj, p, off, ns, ntot);
     if (RES) {
         for (int q = threadIdx.x; q < 3 * ns; q += T) {
@@ -373,32 +428,53 @@ __device__ void run_small(float* sj, const BParams& p, int s, int64_t ntot) {
             sv[q] = v;
         }
     }
+    const int S = (ns + 31) >> 5;
+    const unsigned re = S < kRoundSlots ? p.rounds[S] : round_entry(I, kRoundSpread, 1, 1);
+    const int I1 = (int)(re & 3u) + 1, mode = (int)((re >> 2) & 3u), I2 = (int)((re >> 4) & 3u) + 1;
+    const int G = (int)((re >> 6) & 15u) + 1;
+    const int F = S / (W * I1), R = S - F * W * I1;
+    const int sb = F * W * I1 * 32;  // first body of the last round
+    const int w = threadIdx.x >> 5;
+    const Staging whole = {0, 0};
     __syncthreads();
     for (int64_t ev = 0; ev <= p.steps; ++ev) {
         const float kick = (p.steps == 0) ? 0.0f : ((ev == 0 || ev == p.steps) ? 0.5f * p.dt : p.dt);
         const bool drift = ev < p.steps;
-        for (int base = 0; base < ns; base += T * I) {
-            // Each warp takes only as many i-bodies per thread as it has
-            // left in this pass (slot k of lane l is body base + k*T + l),
-            // and a warp with none skips the pass: padding costs less than
-            // one warp's row of bodies per system, not up to T*I - 1.
-            const int lw = ns - base - 32 * (int)(threadIdx.x >> 5);
-            const int left = lw <= 0 ? 0 : (lw + T - 1) / T;
-            if (left == 0) {
-            } else if (POT || eps2s == 0.0f) {  // the self pair must be excluded
+        for (int r = 0; r < F; ++r)
+            run_task<T, I, POT, RES, U, JB>(mask, uni, I1, sj, sv, ns, (r * W + w) * I1 * 32, 32, 0, npair, eps2, p,
+                                            off, ntot, kick, drift, mu, whole);
+        if (mode == kRoundSpread) {
+            const int nw = R > w ? (R - w + W - 1) / W : 0;
+            if (nw > 0)
+                run_task<T, I, POT, RES, U, JB>(mask, uni, nw, sj, sv, ns, sb + 32 * w, T, 0, npair, eps2, p, off,
+                                                ntot, kick, drift, mu, whole);
+        } else if (mode == kRoundSplit) {
+            const int groups = (R + I2 - 1) / I2;
+            const int rb = 32 * R;
+            if (w < groups * G) {
+                const int q = w / G, seg = w - q * G;
+                const Staging st = {so0 + seg * (POT ? 4 : 3) * rb - sb, rb};
+                run_task<T, I, POT, RES, U, JB>(mask, uni, min(I2, R - q * I2), sj, sv, ns, sb + 32 * q * I2, 32,
+                                                seg * npair / G, (seg + 1) * npair / G, eps2, p, off, ntot, kick,
+                                                drift, mu, st);
+            }
+            __syncthreads();  // every segment's partial sums are staged
+            constexpr int NC = POT ? 4 : 3;
+            for (int rel = threadIdx.x; rel < rb && sb + rel < ns; rel += T) {
+                float ax = stg[rel], ay = stg[rb + rel], az = stg[2 * rb + rel];
+                float pt = POT ? stg[3 * rb + rel] : 0.0f;
+                for (int g = 1; g < G; ++g) {
+                    const float* d = stg + g * NC * rb + rel;
+                    ax += d[0];
+                    ay += d[rb];
+                    az += d[2 * rb];
+                    if (POT) pt += d[3 * rb];
+                }
+                const int b = sb + rel;
                 if (uni)
-                    pass_dispatch<T, I, POT, true, true, RES, U, JB>(left, sj, sv, npair, ns, base, eps2, p, off,
-                                                                     ntot, kick, drift, mu);
+                    finish_body<POT, true, RES>(p, sv, b, off + b, ntot, ax, ay, az, pt, mu, kick, drift);
                 else
-                    pass_dispatch<T, I, POT, true, false, RES, U, JB>(left, sj, sv, npair, ns, base, eps2, p, off,
-                                                                      ntot, kick, drift, mu);
-            } else {
-                if (uni)
-                    pass_dispatch<T, I, POT, false, true, RES, U, JB>(left, sj, sv, npair, ns, base, eps2, p, off,
-                                                                      ntot, kick, drift, mu);
-                else
-                    pass_dispatch<T, I, POT, false, false, RES, U, JB>(left, sj, sv, npair, ns, base, eps2, p, off,
-                                                                       ntot, kick, drift, mu);
+                    finish_body<POT, false, RES>(p, sv, b, off + b, ntot, ax, ay, az, pt, mu, kick, drift);
             }
         }
         __syncthreads();
@@ -522,17 +598,13 @@ __device__ void large_chunk(float* sj, const BParams& p, int64_t off, int ns, in
         __syncthreads();  // the previous tile is consumed
         load_image<true>(sj, p, off + j0, nb, ntot);
         __syncthreads();
-        int ibr[I], ws[I];
+        int ibr[I];
 #pragma unroll
-        for (int k = 0; k < I; ++k) {
-            ibr[k] = ib[k] - j0;
-            const int w0 = cb + k * T + 32 * (tid >> 5) - j0;
-            ws[k] = (w0 >= 0 && w0 < nb) ? w0 : -1;
-        }
+        for (int k = 0; k < I; ++k) ibr[k] = ib[k] - j0;
         f2 tx[I], ty[I], tz[I], tp[I];
 #pragma unroll
         for (int k = 0; k < I; ++k) tx[k] = ty[k] = tz[k] = tp[k] = 0ull;
-        image_sum<I, POT, MASK, UNI, U, JB>(sj, (nb + 1) >> 1, xi, yi, zi, ibr, ws, eps2, tx, ty, tz, tp);
+        image_sum<I, POT, MASK, UNI, U, JB>(sj, 0, (nb + 1) >> 1, xi, yi, zi, ibr, eps2, tx, ty, tz, tp);
 #pragma unroll
         for (int k = 0; k < I; ++k) {
             kahan_fold(sx[k], cx[k], tx[k]);
@@ -545,10 +617,9 @@ __device__ void large_chunk(float* sj, const BParams& p, int64_t off, int ns, in
 #pragma unroll
     for (int k = 0; k < I; ++k) {
         if (ib[k] >= ns) continue;
-        const int64_t g = off + ib[k];
-        if (!in_range(g, ntot, p.err)) continue;
-        body_out<POT, UNI>(p, g, sub2(sx[k], cx[k]), sub2(sy[k], cy[k]), sub2(sz[k], cz[k]), sub2(sp[k], cp[k]), mu,
-                           kick, false);
+        finish_body<POT, UNI, false>(p, nullptr, ib[k], off + ib[k], ntot, hsum(sub2(sx[k], cx[k])),
+                                     hsum(sub2(sy[k], cy[k])), hsum(sub2(sz[k], cz[k])), hsum(sub2(sp[k], cp[k])), mu,
+                                     kick, false);
     }
 }
 
@@ -606,7 +677,7 @@ __device__ void run_large(float* sj, const BParams& p, int s, int w, int W, int6
 // The persistent kernel.
 // ---------------------------------------------------------------------------
 template <int T, int I, bool POT, int U, int JB>
-__global__ void __launch_bounds__(T) batched_kernel(const BParams p) {
+__global__ void __launch_bounds__(T, 512 / T) batched_kernel(const BParams p) {
     extern __shared__ __align__(16) float sj[];
     __shared__ unsigned long long s_item;
     if (p.plan[kPlanInvalid] != 0) return;  // a bad batch: nothing is written
@@ -642,7 +713,7 @@ __global__ void __launch_bounds__(T) batched_kernel(const BParams p) {
             const int s = p.order[r];
             if (!in_range(s, p.nsys, p.err)) continue;
             const int64_t ns = p.offsets[s + 1] - p.offsets[s];
-            if (p.steps > 0 && ns <= p.cap && resident_bytes((int)ns) <= p.smem)
+            if (p.steps > 0 && ns <= p.cap && resident_bytes((int)ns) + stage_bytes(T, I) <= p.smem)
                 run_small<T, I, POT, U, JB, true>(sj, p, s, ntot);
             else
                 run_small<T, I, POT, U, JB, false>(sj, p, s, ntot);
@@ -823,17 +894,112 @@ static int cta_smem_limit(int k) {
     return std::min(optin, per_sm / occ) - 1024;  // room for static shared memory and the runtime's share
 }
 
-int batched_max_cap(int k) { return std::max(128, cta_smem_limit(k) / 16 / 128 * 128); }
+int batched_max_cap(int k) {
+    const BatchShape sh = bshapes()[k].shape;
+    return std::max(128, (cta_smem_limit(k) - stage_bytes(sh.threads, sh.ibodies)) / 16 / 128 * 128);
+}
+
+// Round plans.  A cost model of one evaluation of a small system picks, for
+// every slot count S, the plan with the least modelled time: a round's time is
+// the largest, over the SM's four schedulers (warp w runs on scheduler w % 4),
+// of the work its warps hold -- slots times the fraction of j-pairs, each slot
+// weighted by kSlotCost[n] for a warp of n slots (fewer i-bodies per thread
+// reuse each j-load less) -- divided by kSchedEff[m] for m busy warps (with
+// the co-resident CTAs; one warp alone cannot hide its own latency).  A split
+// round adds the cost of the staging and its barrier, about 2 us, in units of
+// one slot against the whole system.  The constants were fitted to the
+// throughput of equal-size batches of 512 to 4096 bodies on GB300 with every
+// remainder spread (rms error 1 point of FP32 peak).
+static double round_cost(const int* n, const double* f, int ntask, int occ) {
+    static const double kSchedEff[5] = {0.0, 0.5, 0.85, 0.95, 1.0};
+    static const double kSlotCost[5] = {0.0, 1.1, 1.04, 1.01, 1.0};
+    double per[4] = {0.0, 0.0, 0.0, 0.0};
+    int cnt[4] = {0, 0, 0, 0};
+    for (int w = 0; w < ntask; ++w) {
+        if (n[w] <= 0) continue;
+        per[w % 4] += n[w] * f[w] * kSlotCost[n[w]];
+        cnt[w % 4] += 1;
+    }
+    double t = 0.0;
+    for (int q = 0; q < 4; ++q)
+        if (cnt[q] > 0) t = std::max(t, per[q] / kSchedEff[std::min(4, cnt[q] * occ)]);
+    return t;
+}
+
+static unsigned short plan_rounds(int S, int W, int I, int occ) {
+    if (S <= 0) return round_entry(I, kRoundNone, 1, 1);
+    const int npair_min = 16 * (S - 1) + 1;  // the smallest system of S slots
+    const double comb = 75.0 / npair_min;
+    int n[32];
+    double f[32];
+    double best = 1e300;
+    unsigned short entry = round_entry(I, kRoundSpread, 1, 1);
+    auto take = [&](double c, unsigned short e) {
+        if (c < best - 1e-9) {
+            best = c;
+            entry = e;
+        }
+    };
+    for (int I1 = I; I1 >= 1; --I1) {
+        const int F = S / (W * I1);
+        if (F == 0 && I1 < I) break;  // no full round: the same plan as I1 = I
+        const int R = S - F * W * I1;
+        for (int w = 0; w < W; ++w) {
+            n[w] = I1;
+            f[w] = 1.0;
+        }
+        const double full = F * round_cost(n, f, W, occ);
+        if (R == 0) {
+            take(full, round_entry(I1, kRoundNone, 1, 1));
+            continue;
+        }
+        for (int w = 0; w < W; ++w) {
+            n[w] = R > w ? (R - w + W - 1) / W : 0;
+            f[w] = 1.0;
+        }
+        take(full + round_cost(n, f, W, occ), round_entry(I1, kRoundSpread, 1, 1));
+        for (int I2 = 1; I2 <= std::min(I, R); ++I2) {
+            const int groups = (R + I2 - 1) / I2;
+            if (groups > W) continue;
+            for (int G = 2; G * groups <= W && G <= 16; ++G) {
+                if (npair_min / G < 16) break;
+                for (int t = 0; t < groups * G; ++t) {
+                    n[t] = std::min(I2, R - (t / G) * I2);
+                    f[t] = 1.0 / G;
+                }
+                take(full + round_cost(n, f, groups * G, occ) + comb, round_entry(I1, kRoundSplit, I2, G));
+            }
+        }
+    }
+    return entry;
+}
+
+// The table of shape k at occ co-resident CTAs, built once.
+static const unsigned short* round_table(int k, int occ) {
+    static std::mutex mu;
+    static std::unique_ptr<unsigned short[]> tabs[kNumBShapes][5];
+    occ = std::min(std::max(occ, 1), 4);
+    std::lock_guard<std::mutex> lock(mu);
+    std::unique_ptr<unsigned short[]>& t = tabs[k][occ];
+    if (!t) {
+        const BatchShape sh = bshapes()[k].shape;
+        t.reset(new unsigned short[kRoundSlots]);
+        for (int S = 0; S < kRoundSlots; ++S) t[S] = plan_rounds(S, sh.threads / 32, sh.ibodies, occ);
+    }
+    return t.get();
+}
 
 cudaError_t batched_launch(int k, const BatchArgs& a, int num_sms, cudaStream_t st, int* launched) {
     *launched = 0;
     const BShapeEntry& e = bshapes()[k];
     const int pot = a.pot != nullptr ? 1 : 0;
-    // The image of the largest small system; a leapfrog call takes more, up to
-    // the CTA's share, so that systems keep their velocities resident too.
-    size_t smem = std::max<size_t>(batched_smem_bytes(a.cap), 16);
+    // The image of the largest small system and the staging area; a leapfrog
+    // call takes more, up to the CTA's share, so that systems keep their
+    // velocities resident too.
+    const size_t stage = (size_t)stage_bytes(e.shape.threads, e.shape.ibodies);
+    size_t smem = batched_smem_bytes(a.cap) + stage;
     if (a.steps > 0)
-        smem = std::max(smem, std::min<size_t>((size_t)resident_bytes(a.cap), (size_t)cta_smem_limit(k)));
+        smem = std::max(smem, std::min<size_t>((size_t)resident_bytes(a.cap) + stage, (size_t)cta_smem_limit(k)));
     cudaError_t err = cudaFuncSetAttribute(e.fn[pot], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int occ = 0;
@@ -888,6 +1054,7 @@ cudaError_t batched_launch(int k, const BatchArgs& a, int num_sms, cudaStream_t 
     p.cap = a.cap;
     p.smem = (int)smem;
     p.grid = grid;
+    std::memcpy(p.rounds, round_table(k, occ), sizeof(p.rounds));
     p.err = a.err;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);

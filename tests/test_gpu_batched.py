@@ -131,15 +131,15 @@ def test_leapfrog_batched_matches_oracle(nb, oracle_mod):
 @pytest.mark.parametrize("device_offsets", [False, True])
 def test_leapfrog_resident_and_streamed_agree(nb, oracle_mod, device_offsets):
     """A leapfrog call keeps a system's positions and velocities in shared
-    memory for all steps when they fit beside its image (28 bytes a body),
+    memory for all steps when they fit beside its image and the staging area,
     else kicks and drifts them in global memory every step.  Both apply the
-    same FP32 operations, and every shape sums a body's pairs in the same
-    blocks, so the results must be bit-identical: the 5000-body member is
-    resident on shape 0 (one CTA per SM, about 226 KB of shared memory) and
-    streamed on shape 2 (two CTAs per SM, about 113 KB); the others are
-    resident on both."""
+    same FP32 operations, so the results must be bit-identical: the 4096-body
+    member is resident on shape 0 (one CTA per SM, about 226 KB of shared
+    memory) and streamed on shape 2 (two CTAs per SM, about 113 KB).  Every
+    member's plan is whole rounds or a spread remainder on both shapes (no
+    split j-range), so every body sums its pairs in the same blocks."""
     import torch
-    sizes = [5000, 3000, 1, 700, 64, 0, 2]
+    sizes = [4096, 2048, 1, 0, 2, 64]
     off, pos, vel, mass, eps = make_batch(sizes, 37)
     dt, steps = 2.0 ** -8, 8
     out = []
@@ -152,11 +152,37 @@ def test_leapfrog_resident_and_streamed_agree(nb, oracle_mod, device_offsets):
         out.append((P.cpu().numpy(), V.cpu().numpy()))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     pg, vg = out[0][0].astype(np.float64), out[0][1].astype(np.float64)
-    for s in (0, 3):
+    for s in (0, 1):
         a, b = off[s], off[s + 1]
         pr, vr, _ = oracle_mod.leapfrog(pos[a:b], vel[a:b], mass[a:b], eps[s], dt, steps)
         assert np.abs(pg[a:b] - pr).max() <= 2e-5, s
         assert np.abs(vg[a:b] - vr).max() <= 2e-4, s
+
+
+# Sizes whose round plans cover every mode on the four shapes: whole rounds of
+# fewer than I slots a warp (1700, 3600, 777), split remainders of 1 to 4 slots
+# a group in 2 to 16 segments (2049, 2112, 2200, 1700, 600, 513, 777), spread
+# remainders (1100, 3600 on shape 2) and systems of one plan per shape.
+ROUND_SIZES = [2112, 2200, 1700, 3600, 777, 513, 600, 1100, 2049]
+
+
+@pytest.mark.parametrize("eps_rule", ["4/sqrt(n)", 1e-5, 0.0])
+@pytest.mark.parametrize("shape", range(4))
+def test_round_plans_match_oracle(nb, oracle_mod, shape, eps_rule):
+    """Every round-plan mode (whole rounds, spread and split remainders, the
+    latter adding segment sums staged in shared memory) against the oracle,
+    with the potential, for the usual, a small and zero softening (the last two
+    take the masked self pair)."""
+    off, pos, vel, mass, eps = make_batch(ROUND_SIZES, 53 + shape, eps_rule=eps_rule)
+    acc, pot = gpu_accel_batched(nb, off, pos, mass, eps, config=shape)
+    assert nb.nbody_last_device_error() == 0
+    for s in range(len(ROUND_SIZES)):
+        a, b = off[s], off[s + 1]
+        ra, rp = oracle_mod.accel(pos[a:b], mass[a:b], eps[s])
+        e = rel(acc[a:b], ra)
+        tol = (ACC_MED, ACC_MAX, POT_MAX) if eps[s] > 0 else (1e-5, 1e-3, 1e-4)
+        assert np.median(e) <= tol[0] and e.max() <= tol[1], (shape, s, np.median(e), e.max())
+        assert rel(pot[a:b], rp).max() <= tol[2], (shape, s)
 
 
 # Systems larger than one CTA's shared-memory image (about 14,000 bodies for
