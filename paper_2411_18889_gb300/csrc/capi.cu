@@ -1556,3 +1556,10 @@ void nbody_finalize(void) {
 }
 
 }  // extern "C"
+
+// Programmatic dependent launch of the step kernels (nbody_internal.cuh):
+// off while kernels are timed one by one, or when NBODY_NO_PDL is set.
+bool nbk::pdl_on() {
+    static const bool env_off = getenv("NBODY_NO_PDL") != nullptr;
+    return !env_off && !g_prof_on.load();
+}

@@ -34,7 +34,10 @@
 // tile's partial is folded into a running sum by Kahan summation (four packed
 // adds per component per tile, amortised over J pairs), so the per-body sum
 // over n terms keeps FP32 pair errors instead of an O(sqrt(n)) FP32 running-sum
-// error.
+// error.  The per-CTA partial sums of split i-blocks are double-float records
+// (hi + lo in FP32, the Kahan pair's s - c exactly), added by their consumer
+// with FP32 two-sums: no FP64 instruction, which runs at 1/64 of the FP32
+// rate on GB300, is left in the epilogue of the mixed kernels.
 //
 // Self term.  The diagonal tiles (j-tile inside the thread's own i-block) run
 // a masked variant that zeroes the pair whose j equals i, so j = i is excluded
@@ -65,7 +68,7 @@ struct KParams {
     int64_t nctas;
     float* acc;
     float* pot;
-    double* partial;  // [nctas][2][block][4]
+    double* partial;  // [nctas][2][block] partial records (four double-float components)
     int* err;
     const int* uni;   // nonzero word: every source has one mass (or nullptr)
 };
@@ -163,6 +166,7 @@ __device__ __forceinline__ void force_body(const KParams& p) {
     static_assert(C % J == 0, "a j-tile must not straddle two cells");
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float s_dc[3];  // MIXED: c_J - c_I of the current j-cell
 
     const int tid = threadIdx.x;
     const int64_t cta = blockIdx.x;
@@ -204,7 +208,7 @@ __device__ __forceinline__ void force_body(const KParams& p) {
     const f2 eps2 = pk(p.eps2, p.eps2);
     // j-slot 0 is always a real body: its mass is every source's mass.
     const bool uni = UNIMODE == 2 ? (p.uni != nullptr && *p.uni != 0) : UNIMODE == 1;
-    const double mu = uni ? (double)p.jdup[6] : 1.0;
+    const float mu = uni ? p.jdup[6] : 1.0f;
     uint32_t parity = 0;
     int s = 0;
     int64_t u = u_begin;
@@ -248,22 +252,28 @@ __device__ __forceinline__ void force_body(const KParams& p) {
             const int64_t tt = (u % p.gpb) / GPT;
             const int jlo = (int)(u % GPT) * kGranule, jhi = jlo + (int)(ue - u) * kGranule;
             const bool whole = jlo == 0 && jhi == J;
+            const int64_t cell = (tt * J) / C;
+            const bool recentre = MIXED && cell != cur_cell;
+            if (recentre && tid == 0) {
+                // i-coordinates relative to the j-cell's centre: x_i - c_J =
+                // (x_i - c_I) - (c_J - c_I), the centre difference in FP64,
+                // once per CTA (FP64 is slow on this GPU), shared by the
+                // barrier below.
+                const double* cj = p.centres + 3 * cell;
+                const double* ci = p.icentres + 3 * b;
+                s_dc[0] = (float)(cj[0] - ci[0]);
+                s_dc[1] = (float)(cj[1] - ci[1]);
+                s_dc[2] = (float)(cj[2] - ci[2]);
+            }
             const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u, kWaitLimitNs);
             if (__syncthreads_or(!ok)) {
                 failed = true;
                 break;
             }
             parity ^= (1u << s);
-            const int64_t cell = (tt * J) / C;
-            if (MIXED && cell != cur_cell) {
-                // i-coordinates relative to the j-cell's centre: x_i - c_J =
-                // (x_i - c_I) - (c_J - c_I), the centre difference in FP64.
+            if (recentre) {
                 cur_cell = cell;
-                const double* cj = p.centres + 3 * cell;
-                const double* ci = p.icentres + 3 * b;
-                const float dx = (float)(cj[0] - ci[0]);
-                const float dy = (float)(cj[1] - ci[1]);
-                const float dz = (float)(cj[2] - ci[2]);
+                const float dx = s_dc[0], dy = s_dc[1], dz = s_dc[2];
                 const f2 dx2 = pk(dx, dx), dy2 = pk(dy, dy), dz2 = pk(dz, dz);
 #pragma unroll
                 for (int q = 0; q < IP; ++q) {
@@ -326,33 +336,77 @@ __device__ __forceinline__ void force_body(const KParams& p) {
         const int slot = (b == u_begin / p.gpb) ? 0 : 1;
 #pragma unroll
         for (int q = 0; q < IP; ++q) {
-            float v[2][4];
-            double d[2][4];
-            if (KAHAN != 0) {
-                // mode 1 keeps (sum, comp) in s*, c*; mode 2 in a*, c*
-                const f2 S[4] = {KAHAN == 1 ? sx[q] : ax[q], KAHAN == 1 ? sy[q] : ay[q], KAHAN == 1 ? sz[q] : az[q],
-                                 KAHAN == 1 ? sp[q] : ap[q]};
-                const f2 Cm[4] = {cx[q], cy[q], cz[q], cp[q]};
+            // the sums in double-float: a Kahan pair (s, c) is s - c exactly
+            DF d[2][4];
+            if (MIXED) {
+                if (KAHAN != 0) {
+                    // mode 1 keeps (sum, comp) in s*, c*; mode 2 in a*, c*
+                    const f2 S[4] = {KAHAN == 1 ? sx[q] : ax[q], KAHAN == 1 ? sy[q] : ay[q],
+                                     KAHAN == 1 ? sz[q] : az[q], KAHAN == 1 ? sp[q] : ap[q]};
+                    const f2 Cm[4] = {cx[q], cy[q], cz[q], cp[q]};
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    float s0, s1, c0, c1;
-                    upk(S[k], s0, s1);
-                    upk(Cm[k], c0, c1);
-                    d[0][k] = (double)s0 - (double)c0;
-                    d[1][k] = (double)s1 - (double)c1;
+                    for (int k = 0; k < 4; ++k) {
+                        float s0, s1, c0, c1;
+                        upk(S[k], s0, s1);
+                        upk(Cm[k], c0, c1);
+                        d[0][k] = two_sum(s0, -c0);
+                        d[1][k] = two_sum(s1, -c1);
+                    }
+                } else {
+                    const f2 A[4] = {ax[q], ay[q], az[q], ap[q]};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float a0, a1;
+                        upk(A[k], a0, a1);
+                        d[0][k] = DF{a0, 0.0f};
+                        d[1][k] = DF{a1, 0.0f};
+                    }
+                }
+                if (uni) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        d[0][k] = df_scale(d[0][k], mu);
+                        d[1][k] = df_scale(d[1][k], mu);
+                    }
                 }
             } else {
-                float a0, a1;
-                upk(ax[q], a0, a1); d[0][0] = a0; d[1][0] = a1;
-                upk(ay[q], a0, a1); d[0][1] = a0; d[1][1] = a1;
-                upk(az[q], a0, a1); d[0][2] = a0; d[1][2] = a1;
-                upk(ap[q], a0, a1); d[0][3] = a0; d[1][3] = a1;
-            }
-            if (uni) {
+                // The plain kernels keep their FP64 arithmetic here (the sums
+                // rounded into double-float at the end): on GB300 the
+                // double-float form above scheduled the FP32-state pair loop
+                // 3.4 % slower (N = 65536), this one 0.8 %, while the mixed
+                // kernels gained 6 % at N = 16384 from dropping the FP64 work.
+                double e[2][4];
+                if (KAHAN != 0) {
+                    const f2 S[4] = {KAHAN == 1 ? sx[q] : ax[q], KAHAN == 1 ? sy[q] : ay[q],
+                                     KAHAN == 1 ? sz[q] : az[q], KAHAN == 1 ? sp[q] : ap[q]};
+                    const f2 Cm[4] = {cx[q], cy[q], cz[q], cp[q]};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float s0, s1, c0, c1;
+                        upk(S[k], s0, s1);
+                        upk(Cm[k], c0, c1);
+                        e[0][k] = (double)s0 - (double)c0;
+                        e[1][k] = (double)s1 - (double)c1;
+                    }
+                } else {
+                    float a0, a1;
+                    upk(ax[q], a0, a1); e[0][0] = a0; e[1][0] = a1;
+                    upk(ay[q], a0, a1); e[0][1] = a0; e[1][1] = a1;
+                    upk(az[q], a0, a1); e[0][2] = a0; e[1][2] = a1;
+                    upk(ap[q], a0, a1); e[0][3] = a0; e[1][3] = a1;
+                }
+                if (uni) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        e[0][k] *= (double)mu;
+                        e[1][k] *= (double)mu;
+                    }
+                }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    d[0][k] *= mu;
-                    d[1][k] *= mu;
+                    const float h0 = (float)e[0][k], h1 = (float)e[1][k];
+                    d[0][k] = DF{h0, (float)(e[0][k] - (double)h0)};
+                    d[1][k] = DF{h1, (float)(e[1][k] - (double)h1)};
                 }
             }
 #pragma unroll
@@ -361,19 +415,17 @@ __device__ __forceinline__ void force_body(const KParams& p) {
                 const int64_t g = base + lb;
                 if (full) {
                     if (g < p.n) {
-                        for (int k = 0; k < 4; ++k) v[h][k] = (float)d[h][k];
                         const int64_t o = p.perm != nullptr ? (int64_t)p.perm[g] : g;
                         if (!in_range(o, p.n, p.err)) continue;
-                        p.acc[3 * o + 0] = v[h][0];
-                        p.acc[3 * o + 1] = v[h][1];
-                        p.acc[3 * o + 2] = v[h][2];
-                        if (POT) p.pot[o] = -v[h][3];
+                        p.acc[3 * o + 0] = df_float(d[h][0]);
+                        p.acc[3 * o + 1] = df_float(d[h][1]);
+                        p.acc[3 * o + 2] = df_float(d[h][2]);
+                        if (POT) p.pot[o] = -df_float(d[h][3]);
                     }
                 } else {
                     const int64_t pi = (cta * 2 + slot) * C + lb;
                     if (!in_range(pi, p.nctas * 2 * C, p.err)) continue;
-                    double4_16a* dst = reinterpret_cast<double4_16a*>(p.partial) + pi;
-                    *dst = make_double4_16a(d[h][0], d[h][1], d[h][2], d[h][3]);
+                    store_partial(p.partial, pi, d[h][0], d[h][1], d[h][2], d[h][3]);
                 }
             }
         }
@@ -399,6 +451,8 @@ __device__ __forceinline__ void force_body(const KParams& p) {
 // 68.1 %).
 template <int T, int IP, int J, int UNROLL, int MINB, bool POT, bool MIXED, int KAHAN, int WF>
 __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
+    pdl_trigger();
+    pdl_wait();  // the packed j-array of this evaluation is complete
     if (MIXED)
         force_body<T, IP, J, UNROLL, POT, MIXED, KAHAN, WF, 2>(p);
     else if (p.uni != nullptr && *p.uni != 0)
@@ -412,6 +466,8 @@ __global__ void __launch_bounds__(T, MINB) force_kernel(const KParams p) {
 // a few large blocks still spread over many SMs; blocks covered by one CTA
 // return at once.
 __global__ void fixup_kernel(const KParams p, int C, int pot_on) {
+    pdl_trigger();
+    pdl_wait();  // every CTA of the force kernel has written its partial sums
     const int64_t b = blockIdx.x;
     int64_t c_lo, c_hi;
     int slot_lo;
@@ -421,14 +477,14 @@ __global__ void fixup_kernel(const KParams p, int C, int pot_on) {
         const int64_t g = b * C + lb;
         if (g >= p.n) break;
         if (!in_range((c_hi * 2) * C + lb, p.nctas * 2 * C, p.err)) continue;
-        double s4[4];
+        float s4[4];
         split_sum(p.partial, C, b, c_lo, c_hi, slot_lo, lb, s4);
         const int64_t o = p.perm != nullptr ? (int64_t)p.perm[g] : g;
         if (!in_range(o, p.n, p.err)) continue;
-        p.acc[3 * o + 0] = (float)s4[0];
-        p.acc[3 * o + 1] = (float)s4[1];
-        p.acc[3 * o + 2] = (float)s4[2];
-        if (pot_on) p.pot[o] = -(float)s4[3];
+        p.acc[3 * o + 0] = s4[0];
+        p.acc[3 * o + 1] = s4[1];
+        p.acc[3 * o + 2] = s4[2];
+        if (pot_on) p.pot[o] = -s4[3];
     }
 }
 
@@ -587,9 +643,8 @@ cudaError_t split_fixup(int64_t n, int64_t nblk, int64_t gpb, int64_t nctas, int
     p.partial = const_cast<double*>(partial);
     p.err = err;
     p.uni = nullptr;
-    fixup_kernel<<<dim3((unsigned)nblk, (unsigned)((block + 255) / 256)), 256, 0, st>>>(p, block,
-                                                                                         out1 != nullptr ? 1 : 0);
-    return cudaGetLastError();
+    return launch_pdl(fixup_kernel, dim3((unsigned)nblk, (unsigned)((block + 255) / 256)), dim3(256), 0, st, p, block,
+                      out1 != nullptr ? 1 : 0);
 }
 
 size_t force_partial_doubles_for(int k, bool pot, bool mixed, bool compensated, int64_t npad, int num_sms) {
@@ -628,8 +683,7 @@ cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st
     const size_t sm = e.smem(mixed);
     *launched = 0;
     if (ev0 != nullptr) cudaEventRecord(ev0, st);
-    e.fn[pot][mixed][kahan]<<<(unsigned)p.nctas, e.shape.threads, sm, st>>>(p);
-    cudaError_t err = cudaGetLastError();
+    cudaError_t err = launch_pdl(e.fn[pot][mixed][kahan], dim3((unsigned)p.nctas), dim3(e.shape.threads), sm, st, p);
     if (err != cudaSuccess) return err;
     *launched = 1;
     if (ev1 != nullptr) cudaEventRecord(ev1, st);
@@ -642,8 +696,8 @@ cudaError_t force_launch(int k, const ForceArgs& a, int num_sms, cudaStream_t st
         return cudaSuccess;
     }
     if (p.nctas > 1) {  // a single CTA covers every i-block whole
-        fixup_kernel<<<dim3((unsigned)p.nblk, (unsigned)((C + 255) / 256)), 256, 0, st>>>(p, C, pot);
-        err = cudaGetLastError();
+        err = launch_pdl(fixup_kernel, dim3((unsigned)p.nblk, (unsigned)((C + 255) / 256)), dim3(256), 0, st, p, C,
+                         pot);
         if (err == cudaSuccess) *launched = 2;
     }
     return err;

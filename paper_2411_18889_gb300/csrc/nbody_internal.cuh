@@ -196,6 +196,42 @@ inline int current_sms() {
 }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  The kernels of a leapfrog step (pack,
+// offsets, force) and of a step of the adjoint sweep (reverse step, offsets,
+// VJP) are launched so that each may be scheduled while its predecessor still
+// runs: a chain kernel lets its successor launch as soon as it starts
+// (pdl_trigger) and waits, in every CTA and before its first access to global
+// memory, until its predecessor has completed with its writes visible
+// (pdl_wait).  Since every kernel of a chain waits that way before it can
+// finish, each one completes only after all earlier ones, and a successor
+// never reads or overwrites data an earlier kernel still uses.  What this
+// hides is the launch latency and CTA start-up between the short kernels of a
+// step.  Outside such a launch both instructions do nothing.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Off while kernels are timed one by one (profiling) or when NBODY_NO_PDL is set.
+bool pdl_on();
+
+// kernel<<<grid, block, smem, st>>>(args...), with programmatic serialisation
+// against the preceding kernel of the stream when pdl_on().
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_on() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launch interfaces (implemented in force.cu / pack.cu / reduce.cu).
 // ---------------------------------------------------------------------------
 struct ForceShape {
@@ -421,34 +457,78 @@ __host__ __device__ __forceinline__ void split_ctas(int64_t b, int64_t gpb, int6
     *slot_lo = (*c_lo * units / nctas == u0) ? 0 : 1;
 }
 
-// Sum in CTA order of the partial double4 (x, y, z, w) of slot lb of block b,
-// loads issued eight at a time (a block of a mid-size launch has ~20 CTAs'
-// partials: three rounds of L2 latency instead of twenty).
+// Partial sums of split i-blocks in double-float: each component is the
+// unevaluated sum hi + lo of two FP32 values (about 48 significant bits), so
+// forming, scaling and adding partials takes FP32 instructions only.  On
+// GB300 the FP64 pipe runs at about 1/64 of the FP32 rate: the FP64 epilogue
+// and partial sums these replace held the FP64 pipe for several microseconds
+// of every mid-size force launch.
+struct DF {
+    float hi, lo;
+};
+// a + b exactly (Knuth's two-sum): s = fl(a + b), e the rounding error.
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return DF{s, (a - (s - bb)) + (b - bb)};
+}
+// a + b, renormalised (|lo| at most half an ulp of hi).
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const DF s = two_sum(a.hi, b.hi);
+    const float lo = s.lo + (a.lo + b.lo);
+    const float hi = s.hi + lo;
+    return DF{hi, lo - (hi - s.hi)};
+}
+// a * m, renormalised (the product's rounding error recovered with an FMA).
+__device__ __forceinline__ DF df_scale(DF a, float m) {
+    const float p = a.hi * m;
+    const float lo = fmaf(a.lo, m, fmaf(a.hi, m, -p));
+    const float hi = p + lo;
+    return DF{hi, lo - (hi - p)};
+}
+__device__ __forceinline__ float df_float(DF a) { return a.hi + a.lo; }
+
+// One partial record: four double-float components (x, y, z, w), 32 bytes,
+// in the buffers sized in doubles (four per record).
+__device__ __forceinline__ double df_bits(DF a) {
+    return __hiloint2double(__float_as_int(a.lo), __float_as_int(a.hi));  // hi in the low word
+}
+__device__ __forceinline__ void store_partial(double* partial, int64_t rec, DF x, DF y, DF z, DF w) {
+    reinterpret_cast<double4_16a*>(partial)[rec] = make_double4_16a(df_bits(x), df_bits(y), df_bits(z), df_bits(w));
+}
+
+// Sum in CTA order of the partial records of slot lb of block b, rounded to
+// FP32 at the end; loads issued eight at a time (a block of a mid-size launch
+// has ~20 CTAs' partials: three rounds of L2 latency instead of twenty).
 __device__ __forceinline__ void split_sum(const double* partial, int C, int64_t b, int64_t c_lo, int64_t c_hi,
-                                          int slot_lo, int lb, double* s4) {
-    const double4_16a* P = reinterpret_cast<const double4_16a*>(partial);
-    double sx = 0.0, sy = 0.0, sz = 0.0, sw = 0.0;
+                                          int slot_lo, int lb, float* s4) {
+    const float4* P = reinterpret_cast<const float4*>(partial);
+    DF sx{0.0f, 0.0f}, sy{0.0f, 0.0f}, sz{0.0f, 0.0f}, sw{0.0f, 0.0f};
     for (int64_t c0 = c_lo; c0 <= c_hi; c0 += 8) {
-        double4_16a v[8];
+        float4 v[8][2];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int64_t c = c0 + q;
-            if (c <= c_hi) v[q] = P[(c * 2 + (c == c_lo ? slot_lo : 0)) * C + lb];
+            if (c <= c_hi) {
+                const int64_t rec = (c * 2 + (c == c_lo ? slot_lo : 0)) * C + lb;
+                v[q][0] = P[2 * rec];
+                v[q][1] = P[2 * rec + 1];
+            }
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             if (c0 + q <= c_hi) {
-                sx += v[q].x;
-                sy += v[q].y;
-                sz += v[q].z;
-                sw += v[q].w;
+                sx = df_add(sx, DF{v[q][0].x, v[q][0].y});
+                sy = df_add(sy, DF{v[q][0].z, v[q][0].w});
+                sz = df_add(sz, DF{v[q][1].x, v[q][1].y});
+                sw = df_add(sw, DF{v[q][1].z, v[q][1].w});
             }
         }
     }
-    s4[0] = sx;
-    s4[1] = sy;
-    s4[2] = sz;
-    s4[3] = sw;
+    s4[0] = df_float(sx);
+    s4[1] = df_float(sy);
+    s4[2] = df_float(sz);
+    s4[3] = df_float(sw);
     (void)b;
 }
 
@@ -477,11 +557,11 @@ __device__ __forceinline__ BlockSplit block_split(const SplitSums& ss, int64_t k
 __device__ __forceinline__ void split_acc(const SplitSums& ss, const BlockSplit& bs, int64_t k, int64_t g,
                                           const float* acc, float* out) {
     if (ss.partial != nullptr && bs.c_lo < bs.c_hi) {
-        double s4[4];
+        float s4[4];
         split_sum(ss.partial, ss.block, bs.b, bs.c_lo, bs.c_hi, bs.slot_lo, (int)(k - bs.b * ss.block), s4);
-        out[0] = (float)s4[0];
-        out[1] = (float)s4[1];
-        out[2] = (float)s4[2];
+        out[0] = s4[0];
+        out[1] = s4[1];
+        out[2] = s4[2];
         return;
     }
     out[0] = acc[3 * g + 0];

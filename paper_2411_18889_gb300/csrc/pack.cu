@@ -45,6 +45,8 @@ __global__ void __launch_bounds__(kChunk) pack_step_kernel(int64_t n, double* __
                                                            int plain, float* __restrict__ jdup,
                                                            double* __restrict__ chunks, const int* __restrict__ perm,
                                                            int* __restrict__ err, const SplitSums ss) {
+    pdl_trigger();
+    pdl_wait();  // the force kernel's accelerations (or partial sums) are complete
     __shared__ double red[3][kChunk / 32];
     const int tid = threadIdx.x;
     const int64_t k = (int64_t)blockIdx.x * kChunk + tid;
@@ -104,6 +106,8 @@ __global__ void __launch_bounds__(kChunk) pack_offsets_kernel(int64_t n, int blo
                                                               float* __restrict__ jdup, double* __restrict__ centres,
                                                               const double* __restrict__ chunks,
                                                               const int* __restrict__ perm, int* __restrict__ err) {
+    pdl_trigger();
+    pdl_wait();  // every chunk's positions and sums are written
     __shared__ double cen[3];
     const int tid = threadIdx.x;
     const int64_t ch = blockIdx.x;
@@ -134,6 +138,8 @@ __global__ void __launch_bounds__(kChunk) pack_f32_kernel(int64_t n, float* __re
                                                           float* __restrict__ vel, const float* __restrict__ acc,
                                                           const float* __restrict__ mass, float kick, float drift,
                                                           float* __restrict__ jdup, const SplitSums ss) {
+    pdl_trigger();
+    pdl_wait();  // the force kernel's accelerations (or partial sums) are complete
     const int64_t g = (int64_t)blockIdx.x * kChunk + threadIdx.x;
     const BlockSplit bs = block_split(ss, (int64_t)blockIdx.x * kChunk);
     if (g < n) {
@@ -176,6 +182,8 @@ __global__ void uniform_mass_kernel(int64_t n, const float* __restrict__ mass, i
 
 template <typename V>
 __global__ void kick_kernel(int64_t n3, V* __restrict__ vel, const float* __restrict__ acc, V kick) {
+    pdl_trigger();
+    pdl_wait();  // the accelerations are complete
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n3; k += (int64_t)gridDim.x * blockDim.x)
         vel[k] += kick * (V)acc[k];
 }
@@ -208,20 +216,18 @@ cudaError_t pack_f64(int64_t n, int64_t npad, int block, double* pos, double* ve
     if (block % kChunk != 0 || npad % block != 0) return cudaErrorInvalidValue;
     const unsigned nch = (unsigned)(npad / kChunk);
     double* chunks = centres + 3 * (npad / block);
-    pack_step_kernel<<<nch, kChunk, 0, st>>>(n, pos, vel, acc, mass, kick, drift, plain ? 1 : 0, jdup, chunks, perm,
-                                            err, ss != nullptr ? *ss : SplitSums());
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(pack_step_kernel, dim3(nch), dim3(kChunk), 0, st, n, pos, vel, acc, mass, kick, drift,
+                               plain ? 1 : 0, jdup, chunks, perm, err, ss != nullptr ? *ss : SplitSums());
     if (e != cudaSuccess || plain) return e;
-    pack_offsets_kernel<<<nch, kChunk, 0, st>>>(n, block, pos, mass, jdup, centres, chunks, perm, err);
-    return cudaGetLastError();
+    return launch_pdl(pack_offsets_kernel, dim3(nch), dim3(kChunk), 0, st, n, block, (const double*)pos, mass, jdup,
+                      centres, (const double*)chunks, perm, err);
 }
 
 cudaError_t pack_f32(int64_t n, int64_t npad, float* pos, float* vel, const float* acc, const float* mass,
                      float kick, float drift, float* jdup, cudaStream_t st, const SplitSums* ss) {
     if (npad % kChunk != 0) return cudaErrorInvalidValue;
-    pack_f32_kernel<<<(unsigned)(npad / kChunk), kChunk, 0, st>>>(n, pos, vel, acc, mass, kick, drift, jdup,
-                                                                 ss != nullptr ? *ss : SplitSums());
-    return cudaGetLastError();
+    return launch_pdl(pack_f32_kernel, dim3((unsigned)(npad / kChunk)), dim3(kChunk), 0, st, n, pos, vel, acc, mass,
+                      kick, drift, jdup, ss != nullptr ? *ss : SplitSums());
 }
 
 cudaError_t uniform_mass_flag(int64_t n, const float* mass, int* flag, cudaStream_t st) {
@@ -234,13 +240,11 @@ cudaError_t uniform_mass_flag(int64_t n, const float* mass, int* flag, cudaStrea
 }
 
 cudaError_t kick_f64(int64_t n, double* vel, const float* acc, double kick, cudaStream_t st) {
-    kick_kernel<double><<<grid_for(3 * n, 256), 256, 0, st>>>(3 * n, vel, acc, kick);
-    return cudaGetLastError();
+    return launch_pdl(kick_kernel<double>, dim3(grid_for(3 * n, 256)), dim3(256), 0, st, 3 * n, vel, acc, kick);
 }
 
 cudaError_t kick_f32(int64_t n, float* vel, const float* acc, float kick, cudaStream_t st) {
-    kick_kernel<float><<<grid_for(3 * n, 256), 256, 0, st>>>(3 * n, vel, acc, kick);
-    return cudaGetLastError();
+    return launch_pdl(kick_kernel<float>, dim3(grid_for(3 * n, 256)), dim3(256), 0, st, 3 * n, vel, acc, kick);
 }
 
 }  // namespace nbk

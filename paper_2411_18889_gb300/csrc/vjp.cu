@@ -43,8 +43,8 @@ struct VParams {
     float* g_pos;
     float* g_mass;
     float* acc;           // FORCE kernels: the force at the same positions, [n][3]
-    double* partial;      // [nctas][2][block] double4: (g_pos, -g_mass) of split blocks
-    double* partial_acc;  // FORCE kernels: [nctas][2][block] double4 (acc, 0), after the VJP's
+    double* partial;      // [nctas][2][block] partial records: (g_pos, -g_mass) of split blocks
+    double* partial_acc;  // FORCE kernels: [nctas][2][block] partial records (acc, 0), after the VJP's
     int* err;
     const int* uni;  // nonzero word: every body has one mass (or nullptr)
 };
@@ -130,11 +130,14 @@ __device__ __forceinline__ void vjp_tile(const unsigned char* tile, const f2 (&x
 
 template <int T, int IP, int J, int UNROLL, bool MU, bool MIXED, bool FORCE>
 __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
+    pdl_trigger();
+    pdl_wait();  // the packed j-array of this step is complete
     constexpr int C = 2 * IP * T;
     constexpr uint32_t TILE_BYTES = J * kVjpFloats * 4u;
     static_assert(C % J == 0, "a j-tile must not straddle two cells");
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float s_dc[3];  // MIXED: c_J - c_I of the current j-cell
 
     const int tid = threadIdx.x;
     const int64_t cta = blockIdx.x;
@@ -221,20 +224,24 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
             const int64_t tt = (u % p.gpb) / GPT;
             const int jlo = (int)(u % GPT) * kGranule, jhi = jlo + (int)(ue - u) * kGranule;
             const bool whole = jlo == 0 && jhi == J;
+            const int64_t cell = (tt * J) / C;
+            const bool recentre = MIXED && cell != cur_cell;
+            if (recentre && tid == 0) {  // c_J - c_I in FP64 once per CTA, shared by the barrier below
+                const double* cj = p.centres + 3 * cell;
+                const double* ci = p.centres + 3 * b;
+                s_dc[0] = (float)(cj[0] - ci[0]);
+                s_dc[1] = (float)(cj[1] - ci[1]);
+                s_dc[2] = (float)(cj[2] - ci[2]);
+            }
             const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u, kWaitLimitNs);
             if (__syncthreads_or(!ok)) {
                 failed = true;
                 break;
             }
             parity ^= (1u << s);
-            const int64_t cell = (tt * J) / C;
-            if (MIXED && cell != cur_cell) {
+            if (recentre) {
                 cur_cell = cell;
-                const double* cj = p.centres + 3 * cell;
-                const double* ci = p.centres + 3 * b;
-                const float ddx = (float)(cj[0] - ci[0]);
-                const float ddy = (float)(cj[1] - ci[1]);
-                const float ddz = (float)(cj[2] - ci[2]);
+                const float ddx = s_dc[0], ddy = s_dc[1], ddz = s_dc[2];
                 const f2 dx2 = pk(ddx, ddx), dy2 = pk(ddy, ddy), dz2 = pk(ddz, ddz);
 #pragma unroll
                 for (int q = 0; q < IP; ++q) {
@@ -340,12 +347,11 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
                 } else {
                     const int64_t pi = (cta * 2 + slot) * C + lb;
                     if (!in_range(pi, p.nctas * 2 * C, p.err)) continue;
-                    double4_16a* dst = reinterpret_cast<double4_16a*>(p.partial) + pi;
-                    *dst = make_double4_16a(v[h][0], v[h][1], v[h][2], v[h][3]);
-                    if (FORCE) {
-                        double4_16a* fa = reinterpret_cast<double4_16a*>(p.partial_acc) + pi;
-                        *fa = make_double4_16a(f[h][0], f[h][1], f[h][2], 0.0);
-                    }
+                    store_partial(p.partial, pi, DF{v[h][0], 0.0f}, DF{v[h][1], 0.0f}, DF{v[h][2], 0.0f},
+                                  DF{v[h][3], 0.0f});
+                    if (FORCE)
+                        store_partial(p.partial_acc, pi, DF{f[h][0], 0.0f}, DF{f[h][1], 0.0f}, DF{f[h][2], 0.0f},
+                                      DF{0.0f, 0.0f});
                 }
             }
         }
@@ -396,6 +402,8 @@ __global__ void __launch_bounds__(kVChunk) vjp_step_kernel(int64_t n, const doub
                                                            double* __restrict__ gm_acc, double drift,
                                                            double* __restrict__ chunks, const SplitSums ss,
                                                            const ReverseStep rev) {
+    pdl_trigger();
+    pdl_wait();  // the previous VJP (and force) results are complete
     __shared__ double red[3][kVChunk / 32];
     const int tid = threadIdx.x;
     const int64_t g = (int64_t)blockIdx.x * kVChunk + tid;
@@ -432,13 +440,13 @@ __global__ void __launch_bounds__(kVChunk) vjp_step_kernel(int64_t n, const doub
                     bool split = false;
                     if (ss.partial != nullptr) {  // the previous VJP's partials, summed as its fixup would
                         if (bs.c_lo < bs.c_hi) {
-                            double s4[4];
+                            float s4[4];
                             split_sum(ss.partial, ss.block, bs.b, bs.c_lo, bs.c_hi, bs.slot_lo,
                                       (int)(g - bs.b * ss.block), s4);
-                            gp[0] = (float)s4[0];
-                            gp[1] = (float)s4[1];
-                            gp[2] = (float)s4[2];
-                            gmp = -(float)s4[3];
+                            gp[0] = s4[0];
+                            gp[1] = s4[1];
+                            gp[2] = s4[2];
+                            gmp = -s4[3];
                             split = true;
                         }
                     }
@@ -492,6 +500,8 @@ __global__ void __launch_bounds__(kVChunk) vjp_offsets_kernel(int64_t n, int blo
                                                               const float* __restrict__ mu, int plain,
                                                               float* __restrict__ jv, double* __restrict__ centres,
                                                               const double* __restrict__ chunks) {
+    pdl_trigger();
+    pdl_wait();  // every chunk's positions, adjoints and sums are written
     __shared__ double cen[3];
     const int tid = threadIdx.x;
     const int64_t ch = blockIdx.x;
@@ -523,6 +533,8 @@ __global__ void __launch_bounds__(kVChunk) vjp_offsets_kernel(int64_t n, int blo
 // lamx += g, gm_acc += gm (the last step of the adjoint sweep).
 __global__ void adjoint_accumulate_kernel(int64_t n, double* __restrict__ lamx, const float* __restrict__ g,
                                           double* __restrict__ gm_acc, const float* __restrict__ gm) {
+    pdl_trigger();
+    pdl_wait();  // the last VJP's results are complete
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 3 * n; k += (int64_t)gridDim.x * blockDim.x) {
         lamx[k] += (double)g[k];
         if (k < n) gm_acc[k] += (double)gm[k];
@@ -617,17 +629,18 @@ cudaError_t pack_vjp(int64_t n, int64_t npad, int block, const double* pos, cons
     const ReverseStep rv = rev != nullptr ? *rev : ReverseStep();
     if (rev != nullptr && rev->x != nullptr) pos = rev->x;
     if (lam_f64 != nullptr) {
-        vjp_step_kernel<double><<<nch, kVChunk, 0, st>>>(n, pos, lam_f64, lamx, gprev, gmprev, gm_acc, drift, chunks,
-                                                         sv, rv);
-        vjp_offsets_kernel<double><<<nch, kVChunk, 0, st>>>(n, block, pos, mass, lam_f64, kappa, mu, plain ? 1 : 0,
-                                                            jv, centres, chunks);
-    } else {
-        vjp_step_kernel<const float><<<nch, kVChunk, 0, st>>>(n, pos, lam_f32, nullptr, nullptr, nullptr, nullptr, 0.0,
-                                                              chunks, sv, rv);
-        vjp_offsets_kernel<const float><<<nch, kVChunk, 0, st>>>(n, block, pos, mass, lam_f32, kappa, mu,
-                                                                 plain ? 1 : 0, jv, centres, chunks);
+        cudaError_t e = launch_pdl(vjp_step_kernel<double>, dim3(nch), dim3(kVChunk), 0, st, n, pos, lam_f64, lamx, gprev,
+                                   gmprev, gm_acc, drift, chunks, sv, rv);
+        if (e != cudaSuccess) return e;
+        return launch_pdl(vjp_offsets_kernel<double>, dim3(nch), dim3(kVChunk), 0, st, n, block, pos, mass,
+                          (const double*)lam_f64, kappa, mu, plain ? 1 : 0, jv, centres, (const double*)chunks);
     }
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(vjp_step_kernel<const float>, dim3(nch), dim3(kVChunk), 0, st, n, pos, lam_f32,
+                               (double*)nullptr, (const float*)nullptr, (const float*)nullptr, (double*)nullptr, 0.0,
+                               chunks, sv, rv);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(vjp_offsets_kernel<const float>, dim3(nch), dim3(kVChunk), 0, st, n, block, pos, mass, lam_f32,
+                      kappa, mu, plain ? 1 : 0, jv, centres, (const double*)chunks);
 }
 
 cudaError_t adjoint_accumulate(int64_t n, double* lamx, const float* g, double* gm_acc, const float* gm,
@@ -636,8 +649,7 @@ cudaError_t adjoint_accumulate(int64_t n, double* lamx, const float* g, double* 
     const int64_t cap = (int64_t)current_sms() * 16;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    adjoint_accumulate_kernel<<<(unsigned)grid, 256, 0, st>>>(n, lamx, g, gm_acc, gm);
-    return cudaGetLastError();
+    return launch_pdl(adjoint_accumulate_kernel, dim3((unsigned)grid), dim3(256), 0, st, n, lamx, g, gm_acc, gm);
 }
 
 cudaError_t vjp_launch(int k, const VjpArgs& a, int num_sms, cudaStream_t st, int* launched, cudaEvent_t ev0,
@@ -665,8 +677,7 @@ cudaError_t vjp_launch(int k, const VjpArgs& a, int num_sms, cudaStream_t st, in
     *launched = 0;
     if (ev0 != nullptr) cudaEventRecord(ev0, st);
     VFn fn = force ? e.fnf[mixed] : e.fn[mu][mixed];
-    fn<<<(unsigned)p.nctas, e.shape.threads, e.smem(mixed), st>>>(p);
-    cudaError_t err = cudaGetLastError();
+    cudaError_t err = launch_pdl(fn, dim3((unsigned)p.nctas), dim3(e.shape.threads), e.smem(mixed), st, p);
     if (err != cudaSuccess) return err;
     *launched = 1;
     if (ev1 != nullptr) cudaEventRecord(ev1, st);
