@@ -21,6 +21,8 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libnbody.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["force.cu", "vjp.cu", "batched.cu", "order.cu", "pack.cu", "reduce.cu", "selftest.cu", "capi.cu", "noalloc.cu"]
+# The persistent batched kernel: one object per (shape, potential) instantiation.
+INSTANCES = [("batched_inst.cu", f"_{k}{p}", [f"-DNBK_BSHAPE={k}", f"-DNBK_BPOT={p}"]) for k in range(4) for p in range(2)]
 
 
 def nvcc() -> str:
@@ -56,13 +58,16 @@ def build(force: bool = False, extra=(), lib_path: str = LIB, verbose: bool = Fa
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "nbody.h"))
     tag = "" if not extra else "_" + hashlib.sha1(" ".join(extra).encode()).hexdigest()[:8]
+    units = [(src, "", []) for src in SOURCES] + INSTANCES
     objs, jobs = [], []
-    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
-        for src in SOURCES:
-            obj = os.path.join(BUILD, src.replace(".cu", f"{tag}.o"))
+    with cf.ThreadPoolExecutor(max_workers=min(len(units), os.cpu_count() or 4)) as ex:
+        # the slowest units first, so they start while the rest compile
+        slow = {"batched_inst.cu": 0, "force.cu": 0, "vjp.cu": 1}
+        for src, suffix, defs in sorted(units, key=lambda u: slow.get(u[0], 2)):
+            obj = os.path.join(BUILD, src.replace(".cu", f"{suffix}{tag}.o"))
             objs.append(obj)
             if force or _stale(obj, [os.path.join(CSRC, src)] + headers):
-                jobs.append((src, ex.submit(_compile, src, obj, extra)))
+                jobs.append((src + suffix, ex.submit(_compile, src, obj, list(defs) + list(extra))))
         reports = [(src, j.result()) for src, j in jobs]
     if reports:
         with open(os.path.join(BUILD, f"ptxas{tag}.log"), "w") as f:
