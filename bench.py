@@ -244,8 +244,9 @@ def profile_case(n: int, kind: str = "force") -> int:
             for _ in range(2):
                 nb.nbody_accel_vjp(P, M, 2.0 ** -9, lam, None, acc, gm)
         else:
+            pot = torch.empty((n,), dtype=torch.float32, device="cuda") if kind == "force_pot" else None
             for _ in range(2):
-                nb.nbody_accel(P, M, 2.0 ** -9, acc, None)
+                nb.nbody_accel(P, M, 2.0 ** -9, acc, pot)
     torch.cuda.synchronize()
     assert nb.nbody_last_device_error() == 0
     print(f"profile case {kind} n={n}: sum|out| = {float(acc.abs().sum()):.6e}")
@@ -573,10 +574,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--profile-case", type=int, default=0, metavar="N",
                     help="only run one kernel twice at size N, for profilers: the force (nbody_accel, mixed, "
-                         "no potential, the precision workload's recipe), the VJP (nbody_accel_vjp) or the "
+                         "no potential, the precision workload's recipe; force_pot: with the potential), the VJP (nbody_accel_vjp) or the "
                          "batched force (the ragged recipe with N systems); 'adjoint' runs the adjoint workload "
                          "once (record + gradient; N is ignored)")
-    ap.add_argument("--profile-kind", default="force", choices=["force", "vjp", "batched", "adjoint"])
+    ap.add_argument("--profile-kind", default="force", choices=["force", "force_pot", "vjp", "batched", "adjoint"])
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

@@ -505,6 +505,7 @@ struct ForcePlan {
     int64_t npad;
     float* jdup;
     double* centres;
+    double* chunks[2];  // 256-body chunk sums, alternately read and written by the packs of a leapfrog
     double* partial;
     int* err;
     int num_sms;
@@ -558,8 +559,11 @@ int plan_force(Workspace* ws, int64_t n, int shape, int num_sms, ForcePlan* fp) 
     void* p;
     NB_CHECK(ensure(ws, B_JDUP, (size_t)fp->npad * nbk::kJdupFloats * sizeof(float), &p));
     fp->jdup = (float*)p;
-    NB_CHECK(ensure(ws, B_CENTRES, nbk::pack_centre_doubles(fp->npad, fp->block) * sizeof(double), &p));
+    const size_t ncen = nbk::pack_centre_doubles(fp->npad, fp->block);
+    NB_CHECK(ensure(ws, B_CENTRES, (ncen + nbk::pack_chunk_doubles(fp->npad)) * sizeof(double), &p));
     fp->centres = (double*)p;
+    fp->chunks[0] = fp->centres + (ncen - nbk::pack_chunk_doubles(fp->npad));  // where pack_f64 writes them
+    fp->chunks[1] = fp->centres + ncen;
     NB_CHECK(ensure(ws, B_PARTIAL, nbk::force_partial_doubles(shape, num_sms) * sizeof(double), &p));
     fp->partial = (double*)p;
     NB_CHECK(ensure(ws, B_ERR, sizeof(int), &p));
@@ -746,8 +750,12 @@ static int leapfrog_issue(int64_t n, V* x, V* v, const float* m, double eps, dou
     NB_CHECK(run_force(fp, n, eps2, f64 && !plain, comp, a, nullptr, st, steps > 0 ? &ss : nullptr));
     for (int64_t s = 0; s < steps; ++s) {
         const double kick = (s == 0) ? 0.5 * dt : dt;  // merged closing + opening half kicks
-        count(f64 ? nbk::pack_f64_launches(plain) : 1);
+        count(1);
         NB_CUDA(timed(PROF_PACK, st, [&] {
+            if (f64 && !plain)  // one kernel: cell centres from the previous step's chunk sums
+                return nbk::pack_f64_lagged(n, fp.npad, fp.block, (double*)x, (double*)v, a, m, kick, dt, fp.jdup,
+                                            fp.centres, fp.chunks[s & 1], fp.chunks[(s + 1) & 1], st, fp.perm,
+                                            fp.err, &ss);
             return f64 ? nbk::pack_f64(n, fp.npad, fp.block, (double*)x, (double*)v, a, m, kick, dt, plain, fp.jdup,
                                        fp.centres, st, fp.perm, fp.err, &ss)
                        : nbk::pack_f32(n, fp.npad, (float*)x, (float*)v, a, m, (float)kick, (float)dt, fp.jdup, st,
@@ -987,6 +995,7 @@ struct VjpPlan {
     int64_t npad;
     float* jv;
     double* centres;
+    double* chunks[2];  // 256-body chunk sums, alternately read and written by the packs of the sweep
     double* partial;
     int* err;
     int* uni = nullptr;  // device word: all masses equal (the flag of the call's force plan)
@@ -1000,8 +1009,11 @@ static int plan_vjp(Workspace* ws, int64_t n, int shape, int num_sms, VjpPlan* v
     void* p;
     NB_CHECK(ensure(ws, B_VJ, (size_t)vp->npad * nbk::vjp_floats_per_body() * sizeof(float), &p));
     vp->jv = (float*)p;
-    NB_CHECK(ensure(ws, B_VCENTRES, nbk::pack_centre_doubles(vp->npad, vp->block) * sizeof(double), &p));
+    const size_t ncen = nbk::pack_centre_doubles(vp->npad, vp->block);
+    NB_CHECK(ensure(ws, B_VCENTRES, (ncen + nbk::pack_chunk_doubles(vp->npad)) * sizeof(double), &p));
     vp->centres = (double*)p;
+    vp->chunks[0] = vp->centres + (ncen - nbk::pack_chunk_doubles(vp->npad));  // where pack_vjp writes them
+    vp->chunks[1] = vp->centres + ncen;
     NB_CHECK(ensure(ws, B_VPARTIAL, nbk::vjp_partial_doubles(shape, num_sms) * sizeof(double), &p));
     vp->partial = (double*)p;
     NB_CHECK(ensure(ws, B_ERR, sizeof(int), &p));
@@ -1130,9 +1142,13 @@ int nbody_leapfrog_record(int64_t n, double* pos, double* vel, const float* mass
         double* slot = tp + (size_t)(s / ckpt_every) * 2 * n * 3;
         if (ck) NB_CUDA(cudaMemcpyAsync(slot, pos, n3b, cudaMemcpyDeviceToDevice, st));
         const double kick = (s == 0) ? 0.5 * dt : dt;
-        count(nbk::pack_f64_launches(plain));
-        NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, pos, vel, a, mass, kick, dt, plain, fp.jdup, fp.centres, st,
-                              fp.perm, fp.err, &ss));
+        count(1);
+        if (plain)
+            NB_CUDA(nbk::pack_f64(n, fp.npad, fp.block, pos, vel, a, mass, kick, dt, plain, fp.jdup, fp.centres, st,
+                                  fp.perm, fp.err, &ss));
+        else  // as nbody_leapfrog: one kernel, centres from the previous step's chunk sums
+            NB_CUDA(nbk::pack_f64_lagged(n, fp.npad, fp.block, pos, vel, a, mass, kick, dt, fp.jdup, fp.centres,
+                                         fp.chunks[s & 1], fp.chunks[(s + 1) & 1], st, fp.perm, fp.err, &ss));
         if (ck) NB_CUDA(cudaMemcpyAsync(slot + (size_t)n * 3, vel, n3b, cudaMemcpyDeviceToDevice, st));
         NB_CHECK(run_force(fp, n, eps2, !plain, comp, a, nullptr, st, s + 1 < steps ? &ss : nullptr));
     }
@@ -1231,9 +1247,16 @@ int nbody_leapfrog_vjp_tape(int64_t n, const float* mass, double eps, double dt,
             rev.drift = dt;
         }
         const double kappa = (s == 0) ? h : dt;
-        count(2);
-        NB_CUDA(nbk::pack_vjp(n, vp.npad, vp.block, X, mass, nullptr, lamv, lamx, g, gm, gm_acc, dt, kappa, nullptr,
-                              plain, vp.jv, vp.centres, st, &ss, &rev));
+        const int64_t it = steps - 1 - s;
+        if (plain) {
+            count(2);
+            NB_CUDA(nbk::pack_vjp(n, vp.npad, vp.block, X, mass, nullptr, lamv, lamx, g, gm, gm_acc, dt, kappa,
+                                  nullptr, plain, vp.jv, vp.centres, st, &ss, &rev));
+        } else {  // one kernel: cell centres from the previous step's chunk sums
+            count(1);
+            NB_CUDA(nbk::pack_vjp_lagged(n, vp.npad, vp.block, mass, lamv, lamx, g, gm, gm_acc, dt, kappa, vp.jv,
+                                         vp.centres, vp.chunks[it & 1], vp.chunks[(it + 1) & 1], st, &ss, &rev));
+        }
         // the force at x_s is needed to step back to x_{s-1} unless that is a checkpoint
         const bool want_a = s > 0 && (s - 1) % ckpt_every != 0;
         NB_CHECK(run_vjp(vp, n, eps2, !plain, false, g, gm, c.sms, st, s > 0 ? &ss : nullptr, want_a ? a : nullptr,

@@ -208,7 +208,7 @@ __device__ __forceinline__ void force_body(const KParams& p) {
     const f2 eps2 = pk(p.eps2, p.eps2);
     // j-slot 0 is always a real body: its mass is every source's mass.
     const bool uni = UNIMODE == 2 ? (p.uni != nullptr && *p.uni != 0) : UNIMODE == 1;
-    const float mu = uni ? p.jdup[6] : 1.0f;
+    const float mu = uni ? ld_chain(p.jdup + 6) : 1.0f;
     uint32_t parity = 0;
     int s = 0;
     int64_t u = u_begin;
@@ -228,9 +228,9 @@ __device__ __forceinline__ void force_body(const KParams& p) {
             if (!in_range(s1, p.nblk * C, p.err)) s1 = 0;
             const float* a0 = p.ipack + s0 * kJdupFloats;
             const float* a1 = p.ipack + s1 * kJdupFloats;
-            xi[q] = pk(a0[0], a1[0]);
-            yi[q] = pk(a0[2], a1[2]);
-            zi[q] = pk(a0[4], a1[4]);
+            xi[q] = pk(ld_chain(a0 + 0), ld_chain(a1 + 0));
+            yi[q] = pk(ld_chain(a0 + 2), ld_chain(a1 + 2));
+            zi[q] = pk(ld_chain(a0 + 4), ld_chain(a1 + 4));
             if (MIXED) {
                 xsave[(q * 3 + 0) * T + tid] = xi[q];
                 xsave[(q * 3 + 1) * T + tid] = yi[q];
@@ -261,9 +261,9 @@ __device__ __forceinline__ void force_body(const KParams& p) {
                 // barrier below.
                 const double* cj = p.centres + 3 * cell;
                 const double* ci = p.icentres + 3 * b;
-                s_dc[0] = (float)(cj[0] - ci[0]);
-                s_dc[1] = (float)(cj[1] - ci[1]);
-                s_dc[2] = (float)(cj[2] - ci[2]);
+                s_dc[0] = (float)(ld_chain(cj + 0) - ld_chain(ci + 0));
+                s_dc[1] = (float)(ld_chain(cj + 1) - ld_chain(ci + 1));
+                s_dc[2] = (float)(ld_chain(cj + 2) - ld_chain(ci + 2));
             }
             const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u, kWaitLimitNs);
             if (__syncthreads_or(!ok)) {

@@ -201,15 +201,31 @@ inline int current_sms() {
 // VJP) are launched so that each may be scheduled while its predecessor still
 // runs: a chain kernel lets its successor launch as soon as it starts
 // (pdl_trigger) and waits, in every CTA and before its first access to global
-// memory, until its predecessor has completed with its writes visible
-// (pdl_wait).  Since every kernel of a chain waits that way before it can
-// finish, each one completes only after all earlier ones, and a successor
-// never reads or overwrites data an earlier kernel still uses.  What this
-// hides is the launch latency and CTA start-up between the short kernels of a
-// step.  Outside such a launch both instructions do nothing.
+// memory that a kernel of the chain writes, until its predecessor has
+// completed with its writes visible (pdl_wait).  Since every kernel of a
+// chain waits that way before it can finish, each one completes only after
+// all earlier ones, and a successor never reads or overwrites data an earlier
+// kernel still uses.  (Before the wait a kernel may read what no kernel of
+// the chain writes, such as the masses and the call's Morton permutation:
+// those are complete before the chain's first kernel starts, and a chain
+// kernel cannot start before that one.)  What this hides is the launch
+// latency and CTA start-up between the short kernels of a step.  Outside such
+// a launch both instructions do nothing.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Load of data that an earlier kernel of such a chain wrote, after pdl_wait.
+// Through L2, the point of coherence (ld.global.cg): the read-only data path,
+// which the compiler may pick for const __restrict__ pointers, gave stale
+// values on GB300 once a kernel could start before its predecessor finished
+// (a three-step leapfrog returned different bits from run to run, once off by
+// 3e-5 in a velocity).  Every chain kernel reads its predecessors' results
+// through this.
+template <typename T>
+__device__ __forceinline__ T ld_chain(const T* p) {
+    return __ldcg(p);
+}
 
 // Off while kernels are timed one by one (profiling) or when NBODY_NO_PDL is set.
 bool pdl_on();
@@ -319,6 +335,16 @@ cudaError_t pack_f64(int64_t n, int64_t npad, int block, double* pos, double* ve
                      const float* mass, double kick, double drift, bool plain, float* jdup,
                      double* centres, cudaStream_t st, const int* perm = nullptr, int* err = nullptr,
                      const SplitSums* ss = nullptr);
+// The mixed-precision pack of a leapfrog step after the first of a call, in
+// one kernel: each cell's centre is the mean of its bodies one step earlier,
+// from the chunk sums (pack_chunk_doubles(npad) doubles) that the previous
+// pack of the call wrote (pack_f64 writes them after the cell centres);
+// the new positions' chunk sums go to chunks_out.  Needs vel and acc.
+size_t pack_chunk_doubles(int64_t npad);
+cudaError_t pack_f64_lagged(int64_t n, int64_t npad, int block, double* pos, double* vel, const float* acc,
+                            const float* mass, double kick, double drift, float* jdup, double* centres,
+                            const double* chunks_in, double* chunks_out, cudaStream_t st, const int* perm = nullptr,
+                            int* err = nullptr, const SplitSums* ss = nullptr);
 cudaError_t pack_f32(int64_t n, int64_t npad, float* pos, float* vel, const float* acc,
                      const float* mass, float kick, float drift, float* jdup, cudaStream_t st,
                      const SplitSums* ss = nullptr);
@@ -422,6 +448,16 @@ cudaError_t pack_vjp(int64_t n, int64_t npad, int block, const double* pos, cons
                      double* lam_f64, double* lamx, const float* gprev, const float* gmprev, double* gm_acc,
                      double drift, double kappa, const float* mu, bool plain, float* jv, double* centres,
                      cudaStream_t st, const SplitSums* ss = nullptr, const ReverseStep* rev = nullptr);
+// The adjoint sweep's pack after its first, in one kernel (mixed precision;
+// lam_f64, lamx and rev->x required): as pack_vjp, with each cell's centre
+// the mean of its bodies one step earlier, from the chunk sums
+// (pack_chunk_doubles(npad) doubles) the previous pack left in chunks_in
+// (pack_vjp writes them after the cell centres); the new positions' chunk
+// sums go to chunks_out.
+cudaError_t pack_vjp_lagged(int64_t n, int64_t npad, int block, const float* mass, double* lam_f64, double* lamx,
+                            const float* gprev, const float* gmprev, double* gm_acc, double drift, double kappa,
+                            float* jv, double* centres, const double* chunks_in, double* chunks_out,
+                            cudaStream_t st, const SplitSums* ss, const ReverseStep* rev);
 cudaError_t adjoint_accumulate(int64_t n, double* lamx, const float* g, double* gm_acc, const float* gm,
                                cudaStream_t st);
 // ev0/ev1 (optional) are recorded on `st` just before and after the VJP kernel.
@@ -498,37 +534,48 @@ __device__ __forceinline__ void store_partial(double* partial, int64_t rec, DF x
 }
 
 // Sum in CTA order of the partial records of slot lb of block b, rounded to
-// FP32 at the end; loads issued eight at a time (a block of a mid-size launch
-// has ~20 CTAs' partials: three rounds of L2 latency instead of twenty).
+// FP32 at the end.  NB loads are issued before the first is added (a block of
+// a mid-size launch has ~20 CTAs' partials: one or a few rounds of L2 latency
+// instead of twenty); the additions keep CTA order whatever NB is, so every
+// NB gives the same bits.  W: also the fourth component (the potential, or
+// the VJP's mass gradient); without it s4[3] is left alone and each record's
+// last 8 bytes are not read.
+template <int NB = 8, bool W = true>
 __device__ __forceinline__ void split_sum(const double* partial, int C, int64_t b, int64_t c_lo, int64_t c_hi,
                                           int slot_lo, int lb, float* s4) {
     const float4* P = reinterpret_cast<const float4*>(partial);
+    const float2* P2 = reinterpret_cast<const float2*>(partial);
     DF sx{0.0f, 0.0f}, sy{0.0f, 0.0f}, sz{0.0f, 0.0f}, sw{0.0f, 0.0f};
-    for (int64_t c0 = c_lo; c0 <= c_hi; c0 += 8) {
-        float4 v[8][2];
+    for (int64_t c0 = c_lo; c0 <= c_hi; c0 += NB) {
+        float4 v0[NB], v1[NB];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < NB; ++q) {
             const int64_t c = c0 + q;
             if (c <= c_hi) {
                 const int64_t rec = (c * 2 + (c == c_lo ? slot_lo : 0)) * C + lb;
-                v[q][0] = P[2 * rec];
-                v[q][1] = P[2 * rec + 1];
+                v0[q] = ld_chain(P + 2 * rec);
+                if (W) {
+                    v1[q] = ld_chain(P + 2 * rec + 1);
+                } else {
+                    const float2 z = ld_chain(P2 + 4 * rec + 2);
+                    v1[q] = make_float4(z.x, z.y, 0.0f, 0.0f);
+                }
             }
         }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < NB; ++q) {
             if (c0 + q <= c_hi) {
-                sx = df_add(sx, DF{v[q][0].x, v[q][0].y});
-                sy = df_add(sy, DF{v[q][0].z, v[q][0].w});
-                sz = df_add(sz, DF{v[q][1].x, v[q][1].y});
-                sw = df_add(sw, DF{v[q][1].z, v[q][1].w});
+                sx = df_add(sx, DF{v0[q].x, v0[q].y});
+                sy = df_add(sy, DF{v0[q].z, v0[q].w});
+                sz = df_add(sz, DF{v1[q].x, v1[q].y});
+                if (W) sw = df_add(sw, DF{v1[q].z, v1[q].w});
             }
         }
     }
     s4[0] = df_float(sx);
     s4[1] = df_float(sy);
     s4[2] = df_float(sz);
-    s4[3] = df_float(sw);
+    if (W) s4[3] = df_float(sw);
     (void)b;
 }
 
@@ -554,19 +601,24 @@ __device__ __forceinline__ BlockSplit block_split(const SplitSums& ss, int64_t k
     return sh;
 }
 
+// The acceleration of slot k (body g): from the deferred partial sums of its
+// block when the block was split, else from acc.  NB: loads in flight (see
+// split_sum).
+template <int NB = 8>
 __device__ __forceinline__ void split_acc(const SplitSums& ss, const BlockSplit& bs, int64_t k, int64_t g,
                                           const float* acc, float* out) {
     if (ss.partial != nullptr && bs.c_lo < bs.c_hi) {
         float s4[4];
-        split_sum(ss.partial, ss.block, bs.b, bs.c_lo, bs.c_hi, bs.slot_lo, (int)(k - bs.b * ss.block), s4);
+        split_sum<NB, false>(ss.partial, ss.block, bs.b, bs.c_lo, bs.c_hi, bs.slot_lo, (int)(k - bs.b * ss.block),
+                             s4);
         out[0] = s4[0];
         out[1] = s4[1];
         out[2] = s4[2];
         return;
     }
-    out[0] = acc[3 * g + 0];
-    out[1] = acc[3 * g + 1];
-    out[2] = acc[3 * g + 2];
+    out[0] = ld_chain(acc + 3 * g + 0);
+    out[1] = ld_chain(acc + 3 * g + 1);
+    out[2] = ld_chain(acc + 3 * g + 2);
 }
 
 }  // namespace nbk

@@ -19,6 +19,12 @@ __device__ __forceinline__ void store_jdup(float* jdup, int64_t k, float x, floa
     d[1] = make_float4(z, z, m, m);
 }
 
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -55,14 +61,14 @@ __global__ void __launch_bounds__(kChunk) pack_step_kernel(int64_t n, double* __
     if (k < n) {
         int64_t g = perm != nullptr ? perm[k] : k;  // body in slot k
         if (!in_range(g, n, err)) g = k;
-        x = pos[3 * g + 0];
-        y = pos[3 * g + 1];
-        z = pos[3 * g + 2];
+        x = ld_chain(pos + 3 * g + 0);
+        y = ld_chain(pos + 3 * g + 1);
+        z = ld_chain(pos + 3 * g + 2);
         if (vel != nullptr && (kick != 0.0 || drift != 0.0)) {
-            double vx = vel[3 * g + 0], vy = vel[3 * g + 1], vz = vel[3 * g + 2];
+            double vx = ld_chain(vel + 3 * g + 0), vy = ld_chain(vel + 3 * g + 1), vz = ld_chain(vel + 3 * g + 2);
             if (acc != nullptr && kick != 0.0) {
                 float a3[3];
-                split_acc(ss, bs, k, g, acc, a3);
+                split_acc<16>(ss, bs, k, g, acc, a3);
                 vx += kick * (double)a3[0];
                 vy += kick * (double)a3[1];
                 vz += kick * (double)a3[2];
@@ -115,7 +121,7 @@ __global__ void __launch_bounds__(kChunk) pack_offsets_kernel(int64_t n, int blo
     const int64_t cell = ch / per_cell;
     if (tid < 3) {
         double t = 0.0;
-        for (int q = 0; q < per_cell; ++q) t += chunks[3 * (cell * per_cell + q) + tid];
+        for (int q = 0; q < per_cell; ++q) t += ld_chain(chunks + 3 * (cell * per_cell + q) + tid);
         const int64_t base = cell * block;
         const int64_t cnt = (n - base) < block ? (n - base) : (int64_t)block;
         cen[tid] = t / (double)cnt;
@@ -126,10 +132,120 @@ __global__ void __launch_bounds__(kChunk) pack_offsets_kernel(int64_t n, int blo
     if (k < n) {
         int64_t g = perm != nullptr ? perm[k] : k;
         if (!in_range(g, n, err)) g = k;
-        store_jdup(jdup, k, (float)(pos[3 * g + 0] - cen[0]), (float)(pos[3 * g + 1] - cen[1]),
-                   (float)(pos[3 * g + 2] - cen[2]), mass != nullptr ? mass[g] : 0.0f);
+        store_jdup(jdup, k, (float)(ld_chain(pos + 3 * g + 0) - cen[0]), (float)(ld_chain(pos + 3 * g + 1) - cen[1]),
+                   (float)(ld_chain(pos + 3 * g + 2) - cen[2]), mass != nullptr ? mass[g] : 0.0f);
     } else {
         store_jdup(jdup, k, kPadPos, kPadPos, kPadPos, 0.0f);
+    }
+}
+
+// Mixed precision, every pack of a leapfrog call after its first: one kernel
+// instead of two.  The centre of a cell is the mean of its bodies' positions
+// one step earlier, from the chunk sums the previous pack left in chunks_in
+// (a call keeps its bodies in the same cells), so the packed offsets are
+// written in the same pass as the kick and the drift; the new positions' chunk
+// sums go to chunks_out for the next pack.  Any FP64 point near a cell serves
+// as its centre: the lag moves it by one drift, |v| dt, well inside the cell.
+// The centre is computed exactly as pack_offsets_kernel computes it (the same
+// sums in the same order).
+//
+// The kernel sits between two force launches on the critical path of a step,
+// so it is arranged for latency: the work that needs nothing the previous
+// kernels of the call write -- the split of the block's partial sums
+// (arithmetic on the launch parameters), the Morton permutation and the
+// masses (fixed for the call, written before its first kernel) -- is done
+// before the dependency wait; after it, the chunk sums, the state and the
+// partial sums are all requested before any of them is used.
+constexpr int kMaxChunksPerCell = 8;  // blocks of up to 2048 bodies
+
+__global__ void __launch_bounds__(kChunk) pack_lagged_kernel(int64_t n, int block, double* __restrict__ pos,
+                                                             double* __restrict__ vel, const float* __restrict__ acc,
+                                                             const float* __restrict__ mass, double kick,
+                                                             double drift, float* __restrict__ jdup,
+                                                             double* __restrict__ centres,
+                                                             const double* __restrict__ chunks_in,
+                                                             double* __restrict__ chunks_out,
+                                                             const int* __restrict__ perm, int* __restrict__ err,
+                                                             const SplitSums ss) {
+    pdl_trigger();
+    __shared__ double cin[3 * kMaxChunksPerCell];
+    __shared__ double cen[3];
+    __shared__ float redf[3][kChunk / 32];
+    const int tid = threadIdx.x;
+    const int64_t ch = blockIdx.x;
+    const int per_cell = block / kChunk;
+    const int64_t cell = ch / per_cell;
+    const int64_t k = ch * kChunk + tid;
+    const BlockSplit bs = block_split(ss, ch * kChunk);
+    int64_t g = k;
+    float m = 0.0f;
+    if (k < n) {
+        g = perm != nullptr ? perm[k] : k;  // body in slot k
+        if (!in_range(g, n, err)) g = k;
+        m = mass != nullptr ? mass[g] : 0.0f;
+    }
+    pdl_wait();  // the force kernel's results and the previous pack's chunk sums are complete
+    if (tid < 3 * per_cell) cin[tid] = ld_chain(chunks_in + 3 * cell * per_cell + tid);
+    double x = 0.0, y = 0.0, z = 0.0;
+    if (k < n) {
+        double vx = ld_chain(vel + 3 * g + 0), vy = ld_chain(vel + 3 * g + 1), vz = ld_chain(vel + 3 * g + 2);
+        x = ld_chain(pos + 3 * g + 0);
+        y = ld_chain(pos + 3 * g + 1);
+        z = ld_chain(pos + 3 * g + 2);
+        float a3[3];
+        split_acc<16>(ss, bs, k, g, acc, a3);
+        vx += kick * (double)a3[0];
+        vy += kick * (double)a3[1];
+        vz += kick * (double)a3[2];
+        vel[3 * g + 0] = vx;
+        vel[3 * g + 1] = vy;
+        vel[3 * g + 2] = vz;
+        x += drift * vx;
+        y += drift * vy;
+        z += drift * vz;
+        pos[3 * g + 0] = x;
+        pos[3 * g + 1] = y;
+        pos[3 * g + 2] = z;
+    }
+    __syncthreads();  // the cell's chunk sums are in shared memory
+    if (tid < 3) {
+        double t = 0.0;
+        for (int q = 0; q < per_cell; ++q) t += cin[3 * q + tid];
+        const int64_t base = cell * block;
+        const int64_t cnt = (n - base) < block ? (n - base) : (int64_t)block;
+        cen[tid] = t / (double)cnt;
+        if (ch % per_cell == 0) centres[3 * cell + tid] = cen[tid];
+    }
+    __syncthreads();
+    float ox = 0.0f, oy = 0.0f, oz = 0.0f;
+    if (k < n) {
+        ox = (float)(x - cen[0]);
+        oy = (float)(y - cen[1]);
+        oz = (float)(z - cen[2]);
+        store_jdup(jdup, k, ox, oy, oz, m);
+    } else {
+        store_jdup(jdup, k, kPadPos, kPadPos, kPadPos, 0.0f);
+    }
+    // The chunk's position sum for the next step's centres: its body count
+    // times this centre plus the FP32 sum of its offsets.  Any point near the
+    // cell serves as a centre, so the offsets' rounding does not matter, and
+    // the FP64 pipe (1/64 of the FP32 rate) is left out of the reduction.
+    ox = warp_sum_f(ox);
+    oy = warp_sum_f(oy);
+    oz = warp_sum_f(oz);
+    const int w = tid >> 5, l = tid & 31;
+    if (l == 0) {
+        redf[0][w] = ox;
+        redf[1][w] = oy;
+        redf[2][w] = oz;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        float t = 0.0f;
+        for (int q = 0; q < kChunk / 32; ++q) t += redf[tid][q];
+        const int64_t left = n - ch * kChunk;
+        const int64_t cnt = left < 0 ? 0 : (left < kChunk ? left : (int64_t)kChunk);
+        chunks_out[3 * ch + tid] = (double)cnt * cen[tid] + (double)t;
     }
 }
 
@@ -143,12 +259,12 @@ __global__ void __launch_bounds__(kChunk) pack_f32_kernel(int64_t n, float* __re
     const int64_t g = (int64_t)blockIdx.x * kChunk + threadIdx.x;
     const BlockSplit bs = block_split(ss, (int64_t)blockIdx.x * kChunk);
     if (g < n) {
-        float x = pos[3 * g + 0], y = pos[3 * g + 1], z = pos[3 * g + 2];
+        float x = ld_chain(pos + 3 * g + 0), y = ld_chain(pos + 3 * g + 1), z = ld_chain(pos + 3 * g + 2);
         if (vel != nullptr && (kick != 0.0f || drift != 0.0f)) {
-            float vx = vel[3 * g + 0], vy = vel[3 * g + 1], vz = vel[3 * g + 2];
+            float vx = ld_chain(vel + 3 * g + 0), vy = ld_chain(vel + 3 * g + 1), vz = ld_chain(vel + 3 * g + 2);
             if (acc != nullptr && kick != 0.0f) {
                 float a3[3];
-                split_acc(ss, bs, g, g, acc, a3);
+                split_acc<16>(ss, bs, g, g, acc, a3);
                 vx = fmaf(kick, a3[0], vx);
                 vy = fmaf(kick, a3[1], vy);
                 vz = fmaf(kick, a3[2], vz);
@@ -185,7 +301,7 @@ __global__ void kick_kernel(int64_t n3, V* __restrict__ vel, const float* __rest
     pdl_trigger();
     pdl_wait();  // the accelerations are complete
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n3; k += (int64_t)gridDim.x * blockDim.x)
-        vel[k] += kick * (V)acc[k];
+        vel[k] += kick * (V)ld_chain(acc + k);
 }
 
 }  // namespace
@@ -208,6 +324,8 @@ unsigned grid_for(int64_t work, int threads) {
 
 size_t pack_centre_doubles(int64_t npad, int block) { return 3 * (size_t)(npad / block) + 3 * (size_t)(npad / kChunk); }
 
+size_t pack_chunk_doubles(int64_t npad) { return 3 * (size_t)(npad / kChunk); }
+
 int pack_f64_launches(bool plain) { return plain ? 1 : 2; }
 
 cudaError_t pack_f64(int64_t n, int64_t npad, int block, double* pos, double* vel, const float* acc,
@@ -221,6 +339,18 @@ cudaError_t pack_f64(int64_t n, int64_t npad, int block, double* pos, double* ve
     if (e != cudaSuccess || plain) return e;
     return launch_pdl(pack_offsets_kernel, dim3(nch), dim3(kChunk), 0, st, n, block, (const double*)pos, mass, jdup,
                       centres, (const double*)chunks, perm, err);
+}
+
+cudaError_t pack_f64_lagged(int64_t n, int64_t npad, int block, double* pos, double* vel, const float* acc,
+                            const float* mass, double kick, double drift, float* jdup, double* centres,
+                            const double* chunks_in, double* chunks_out, cudaStream_t st, const int* perm, int* err,
+                            const SplitSums* ss) {
+    if (block % kChunk != 0 || block / kChunk > kMaxChunksPerCell || npad % block != 0 || vel == nullptr ||
+        acc == nullptr)
+        return cudaErrorInvalidValue;
+    return launch_pdl(pack_lagged_kernel, dim3((unsigned)(npad / kChunk)), dim3(kChunk), 0, st, n, block, pos, vel,
+                      acc, mass, kick, drift, jdup, centres, chunks_in, chunks_out, perm, err,
+                      ss != nullptr ? *ss : SplitSums());
 }
 
 cudaError_t pack_f32(int64_t n, int64_t npad, float* pos, float* vel, const float* acc, const float* mass,

@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
     // One mass for every body (j-slot 0 is always a real body): the pair loop
     // leaves the masses out of u and the position gradient is scaled by mu.
     const bool uni = p.uni != nullptr && *p.uni != 0;
-    const float mu = uni ? p.jv[6] : 1.0f;
+    const float mu = uni ? ld_chain(p.jv + 6) : 1.0f;
     uint32_t parity = 0;
     int s = 0;
     int64_t u = u_begin;
@@ -195,15 +195,15 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
             if (!in_range(s1, p.nblk * C, p.err)) s1 = 0;
             const float* a0 = p.jv + s0 * kVjpFloats;
             const float* a1 = p.jv + s1 * kVjpFloats;
-            xi[q] = pk(a0[0], a1[0]);
-            yi[q] = pk(a0[2], a1[2]);
-            zi[q] = pk(a0[4], a1[4]);
-            mi[q] = pk(a0[6], a1[6]);
-            nlx[q] = pk(-a0[8], -a1[8]);
-            nly[q] = pk(-a0[10], -a1[10]);
-            nlz[q] = pk(-a0[12], -a1[12]);
-            nmi[q] = pk(-a0[6], -a1[6]);
-            nmui[q] = pk(-a0[14], -a1[14]);
+            xi[q] = pk(ld_chain(a0 + 0), ld_chain(a1 + 0));
+            yi[q] = pk(ld_chain(a0 + 2), ld_chain(a1 + 2));
+            zi[q] = pk(ld_chain(a0 + 4), ld_chain(a1 + 4));
+            mi[q] = pk(ld_chain(a0 + 6), ld_chain(a1 + 6));
+            nlx[q] = pk(-ld_chain(a0 + 8), -ld_chain(a1 + 8));
+            nly[q] = pk(-ld_chain(a0 + 10), -ld_chain(a1 + 10));
+            nlz[q] = pk(-ld_chain(a0 + 12), -ld_chain(a1 + 12));
+            nmi[q] = pk(-ld_chain(a0 + 6), -ld_chain(a1 + 6));
+            nmui[q] = pk(-ld_chain(a0 + 14), -ld_chain(a1 + 14));
             if (MIXED) {
                 xsave[(q * 3 + 0) * T + tid] = xi[q];
                 xsave[(q * 3 + 1) * T + tid] = yi[q];
@@ -229,9 +229,9 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
             if (recentre && tid == 0) {  // c_J - c_I in FP64 once per CTA, shared by the barrier below
                 const double* cj = p.centres + 3 * cell;
                 const double* ci = p.centres + 3 * b;
-                s_dc[0] = (float)(cj[0] - ci[0]);
-                s_dc[1] = (float)(cj[1] - ci[1]);
-                s_dc[2] = (float)(cj[2] - ci[2]);
+                s_dc[0] = (float)(ld_chain(cj + 0) - ld_chain(ci + 0));
+                s_dc[1] = (float)(ld_chain(cj + 1) - ld_chain(ci + 1));
+                s_dc[2] = (float)(ld_chain(cj + 2) - ld_chain(ci + 2));
             }
             const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u, kWaitLimitNs);
             if (__syncthreads_or(!ok)) {
@@ -369,6 +369,12 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VParams p) {
     }
 }
 
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -394,21 +400,48 @@ __device__ __forceinline__ void store_jv(float* jv, int64_t k, float x, float y,
 // absolute (plain).
 constexpr int kVChunk = 256;
 
-template <typename L>
+// FUSED (mixed precision, every pack of the adjoint sweep after its first):
+// the same kernel also writes the j-array entries, relative to each cell's
+// centre taken one step earlier -- the mean of the cell's positions from the
+// chunk sums the previous pack left in fz.chunks_in -- so the sweep step is
+// one kernel instead of two; its own chunk sums go to `chunks` for the next.
+constexpr int kVMaxChunksPerCell = 8;  // blocks of up to 2048 bodies
+struct VjpFused {
+    int block = 0;
+    const double* chunks_in = nullptr;
+    const float* mass = nullptr;
+    double kappa = 0.0;
+    float* jv = nullptr;
+    double* centres = nullptr;
+};
+
+template <typename L, bool FUSED = false>
 __global__ void __launch_bounds__(kVChunk) vjp_step_kernel(int64_t n, const double* __restrict__ pos,
                                                            L* __restrict__ lam, double* __restrict__ lamx,
                                                            const float* __restrict__ gprev,
                                                            const float* __restrict__ gmprev,
                                                            double* __restrict__ gm_acc, double drift,
                                                            double* __restrict__ chunks, const SplitSums ss,
-                                                           const ReverseStep rev) {
+                                                           const ReverseStep rev, const VjpFused fz) {
     pdl_trigger();
-    pdl_wait();  // the previous VJP (and force) results are complete
     __shared__ double red[3][kVChunk / 32];
+    __shared__ float redf[3][kVChunk / 32];
+    __shared__ double cin[3 * kVMaxChunksPerCell];
+    __shared__ double cen[3];
     const int tid = threadIdx.x;
     const int64_t g = (int64_t)blockIdx.x * kVChunk + tid;
+    // Before the wait: arithmetic on the launch parameters, and (FUSED) the
+    // masses, which no kernel of the sweep writes.
     const BlockSplit bs = block_split(ss, (int64_t)blockIdx.x * kVChunk);
     const BlockSplit ba = block_split(rev.ss_acc, (int64_t)blockIdx.x * kVChunk);
+    const int per_cell = FUSED ? fz.block / kVChunk : 1;
+    const int64_t cell = (int64_t)blockIdx.x / per_cell;
+    float mg = 0.0f;
+    if (FUSED && g < n) mg = fz.mass[g];
+    pdl_wait();  // the previous VJP (and force) results are complete
+    // FUSED: the cell's chunk sums of one step earlier, for its centre
+    if (FUSED && tid < 3 * per_cell) cin[tid] = ld_chain(fz.chunks_in + 3 * cell * per_cell + tid);
+    double lv[3] = {0.0, 0.0, 0.0};  // FUSED: the updated cotangent lam of this body
     double x = 0.0, y = 0.0, z = 0.0;
     double r[3] = {0.0, 0.0, 0.0};  // positions after the reverse step (pos aliases rev.x then)
     if (g < n && rev.x != nullptr) {  // the leapfrog step s run backwards
@@ -422,8 +455,8 @@ __global__ void __launch_bounds__(kVChunk) vjp_step_kernel(int64_t n, const doub
             float a3[3] = {0.0f, 0.0f, 0.0f};
             if (rev.a != nullptr) split_acc(rev.ss_acc, ba, g, g, rev.a, a3);
             for (int c = 0; c < 3; ++c) {
-                w[c] = rev.vh[3 * g + c] - rev.kick * (double)a3[c];
-                r[c] = rev.x[3 * g + c] - rev.drift * w[c];
+                w[c] = ld_chain(rev.vh + 3 * g + c) - rev.kick * (double)a3[c];
+                r[c] = ld_chain(rev.x + 3 * g + c) - rev.drift * w[c];
             }
         }
         for (int c = 0; c < 3; ++c) {
@@ -451,19 +484,20 @@ __global__ void __launch_bounds__(kVChunk) vjp_step_kernel(int64_t n, const doub
                         }
                     }
                     if (!split) {
-                        gp[0] = gprev[3 * g + 0];
-                        gp[1] = gprev[3 * g + 1];
-                        gp[2] = gprev[3 * g + 2];
-                        gmp = gmprev != nullptr ? gmprev[g] : 0.0f;
+                        gp[0] = ld_chain(gprev + 3 * g + 0);
+                        gp[1] = ld_chain(gprev + 3 * g + 1);
+                        gp[2] = ld_chain(gprev + 3 * g + 2);
+                        gmp = gmprev != nullptr ? ld_chain(gmprev + g) : 0.0f;
                     }
                 }
                 for (int c = 0; c < 3; ++c) {
-                    double lx = lamx[3 * g + c];
+                    double lx = ld_chain(lamx + 3 * g + c);
                     if (gprev != nullptr) lx += (double)gp[c];
                     lamx[3 * g + c] = lx;
-                    lam[3 * g + c] = (L)((double)lam[3 * g + c] + drift * lx);
+                    lv[c] = (double)(L)((double)ld_chain(lam + 3 * g + c) + drift * lx);
+                    lam[3 * g + c] = (L)lv[c];
                 }
-                if (gmprev != nullptr) gm_acc[g] += (double)gmp;
+                if (gmprev != nullptr) gm_acc[g] = ld_chain(gm_acc + g) + (double)gmp;
             }
         }
         if (rev.x != nullptr) {
@@ -471,10 +505,52 @@ __global__ void __launch_bounds__(kVChunk) vjp_step_kernel(int64_t n, const doub
             y = r[1];
             z = r[2];
         } else {
-            x = pos[3 * g + 0];
-            y = pos[3 * g + 1];
-            z = pos[3 * g + 2];
+            x = ld_chain(pos + 3 * g + 0);
+            y = ld_chain(pos + 3 * g + 1);
+            z = ld_chain(pos + 3 * g + 2);
         }
+    }
+    if (FUSED) {
+        __syncthreads();  // the chunk sums are in shared memory
+        if (tid < 3) {  // as vjp_offsets_kernel computes it (the same sums in the same order)
+            double t = 0.0;
+            for (int q = 0; q < per_cell; ++q) t += cin[3 * q + tid];
+            const int64_t base = cell * fz.block;
+            const int64_t cnt = (n - base) < fz.block ? (n - base) : (int64_t)fz.block;
+            cen[tid] = t / (double)cnt;
+            if (blockIdx.x % per_cell == 0) fz.centres[3 * cell + tid] = cen[tid];
+        }
+        __syncthreads();
+        float ox = 0.0f, oy = 0.0f, oz = 0.0f;
+        if (g < n) {
+            ox = (float)(x - cen[0]);
+            oy = (float)(y - cen[1]);
+            oz = (float)(z - cen[2]);
+            store_jv(fz.jv, g, ox, oy, oz, mg, (float)(fz.kappa * lv[0]), (float)(fz.kappa * lv[1]),
+                     (float)(fz.kappa * lv[2]), 0.0f);
+        } else {
+            store_jv(fz.jv, g, kPadPos, kPadPos, kPadPos, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f);
+        }
+        // the chunk's position sum for the next step's centres: its body count
+        // times this centre plus the FP32 sum of its offsets (any point near
+        // the cell serves as a centre; no FP64 reduction)
+        ox = warp_sum_f(ox);
+        oy = warp_sum_f(oy);
+        oz = warp_sum_f(oz);
+        if ((tid & 31) == 0) {
+            redf[0][tid >> 5] = ox;
+            redf[1][tid >> 5] = oy;
+            redf[2][tid >> 5] = oz;
+        }
+        __syncthreads();
+        if (tid < 3) {
+            float t = 0.0f;
+            for (int q = 0; q < kVChunk / 32; ++q) t += redf[tid][q];
+            const int64_t left = n - (int64_t)blockIdx.x * kVChunk;
+            const int64_t cnt = left < 0 ? 0 : (left < kVChunk ? left : (int64_t)kVChunk);
+            chunks[3 * (int64_t)blockIdx.x + tid] = (double)cnt * cen[tid] + (double)t;
+        }
+        return;
     }
     x = warp_sum(x);
     y = warp_sum(y);
@@ -511,7 +587,7 @@ __global__ void __launch_bounds__(kVChunk) vjp_offsets_kernel(int64_t n, int blo
         double c = 0.0;
         if (!plain) {
             double t = 0.0;
-            for (int q = 0; q < per_cell; ++q) t += chunks[3 * (cell * per_cell + q) + tid];
+            for (int q = 0; q < per_cell; ++q) t += ld_chain(chunks + 3 * (cell * per_cell + q) + tid);
             const int64_t base = cell * block;
             const int64_t cnt = (n - base) < block ? (n - base) : (int64_t)block;
             c = t / (double)cnt;
@@ -522,9 +598,10 @@ __global__ void __launch_bounds__(kVChunk) vjp_offsets_kernel(int64_t n, int blo
     __syncthreads();
     const int64_t g = ch * kVChunk + tid;
     if (g < n) {
-        store_jv(jv, g, (float)(pos[3 * g + 0] - cen[0]), (float)(pos[3 * g + 1] - cen[1]),
-                 (float)(pos[3 * g + 2] - cen[2]), mass[g], (float)(kappa * (double)lam[3 * g + 0]),
-                 (float)(kappa * (double)lam[3 * g + 1]), (float)(kappa * (double)lam[3 * g + 2]), mu ? mu[g] : 0.0f);
+        store_jv(jv, g, (float)(ld_chain(pos + 3 * g + 0) - cen[0]), (float)(ld_chain(pos + 3 * g + 1) - cen[1]),
+                 (float)(ld_chain(pos + 3 * g + 2) - cen[2]), mass[g],
+                 (float)(kappa * (double)ld_chain(lam + 3 * g + 0)), (float)(kappa * (double)ld_chain(lam + 3 * g + 1)),
+                 (float)(kappa * (double)ld_chain(lam + 3 * g + 2)), mu ? mu[g] : 0.0f);
     } else {
         store_jv(jv, g, kPadPos, kPadPos, kPadPos, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f);
     }
@@ -536,8 +613,8 @@ __global__ void adjoint_accumulate_kernel(int64_t n, double* __restrict__ lamx, 
     pdl_trigger();
     pdl_wait();  // the last VJP's results are complete
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 3 * n; k += (int64_t)gridDim.x * blockDim.x) {
-        lamx[k] += (double)g[k];
-        if (k < n) gm_acc[k] += (double)gm[k];
+        lamx[k] = ld_chain(lamx + k) + (double)ld_chain(g + k);
+        if (k < n) gm_acc[k] = ld_chain(gm_acc + k) + (double)ld_chain(gm + k);
     }
 }
 
@@ -630,17 +707,36 @@ cudaError_t pack_vjp(int64_t n, int64_t npad, int block, const double* pos, cons
     if (rev != nullptr && rev->x != nullptr) pos = rev->x;
     if (lam_f64 != nullptr) {
         cudaError_t e = launch_pdl(vjp_step_kernel<double>, dim3(nch), dim3(kVChunk), 0, st, n, pos, lam_f64, lamx, gprev,
-                                   gmprev, gm_acc, drift, chunks, sv, rv);
+                                   gmprev, gm_acc, drift, chunks, sv, rv, VjpFused());
         if (e != cudaSuccess) return e;
         return launch_pdl(vjp_offsets_kernel<double>, dim3(nch), dim3(kVChunk), 0, st, n, block, pos, mass,
                           (const double*)lam_f64, kappa, mu, plain ? 1 : 0, jv, centres, (const double*)chunks);
     }
     cudaError_t e = launch_pdl(vjp_step_kernel<const float>, dim3(nch), dim3(kVChunk), 0, st, n, pos, lam_f32,
                                (double*)nullptr, (const float*)nullptr, (const float*)nullptr, (double*)nullptr, 0.0,
-                               chunks, sv, rv);
+                               chunks, sv, rv, VjpFused());
     if (e != cudaSuccess) return e;
     return launch_pdl(vjp_offsets_kernel<const float>, dim3(nch), dim3(kVChunk), 0, st, n, block, pos, mass, lam_f32,
                       kappa, mu, plain ? 1 : 0, jv, centres, (const double*)chunks);
+}
+
+cudaError_t pack_vjp_lagged(int64_t n, int64_t npad, int block, const float* mass, double* lam_f64, double* lamx,
+                            const float* gprev, const float* gmprev, double* gm_acc, double drift, double kappa,
+                            float* jv, double* centres, const double* chunks_in, double* chunks_out,
+                            cudaStream_t st, const SplitSums* ss, const ReverseStep* rev) {
+    if (block % kVChunk != 0 || block / kVChunk > kVMaxChunksPerCell || npad % block != 0 || lam_f64 == nullptr ||
+        lamx == nullptr || rev == nullptr || rev->x == nullptr)
+        return cudaErrorInvalidValue;
+    VjpFused fz;
+    fz.block = block;
+    fz.chunks_in = chunks_in;
+    fz.mass = mass;
+    fz.kappa = kappa;
+    fz.jv = jv;
+    fz.centres = centres;
+    return launch_pdl(vjp_step_kernel<double, true>, dim3((unsigned)(npad / kVChunk)), dim3(kVChunk), 0, st, n,
+                      (const double*)rev->x, lam_f64, lamx, gprev, gmprev, gm_acc, drift, chunks_out,
+                      ss != nullptr ? *ss : SplitSums(), *rev, fz);
 }
 
 cudaError_t adjoint_accumulate(int64_t n, double* lamx, const float* g, double* gm_acc, const float* gm,

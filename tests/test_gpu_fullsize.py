@@ -82,6 +82,7 @@ def test_precision_workload_steps(nb, oracle_mod, c3):
     v = w.vel.copy()
     a_prev, _ = oracle_mod.accel_subset(x, w.mass, w.eps, idx, with_pot=False)
     P, V = t(x, np.float64), t(v, np.float64)
+    kicks = np.zeros(len(idx))  # sum over the steps of |dt/2 (a_k + a_{k+1})| on the sample
     for k in range(w.steps):
         nb.nbody_leapfrog(P, V, M, w.eps, w.dt, 1)
         torch.cuda.synchronize()
@@ -90,6 +91,7 @@ def test_precision_workload_steps(nb, oracle_mod, c3):
         x_pred = x[idx] + w.dt * (v[idx] + 0.5 * w.dt * a_prev)
         v_pred = v[idx] + 0.5 * w.dt * (a_prev + a_next)
         kick = 0.5 * w.dt * np.linalg.norm(a_prev + a_next, axis=1)
+        kicks += kick
         ev = np.linalg.norm(v1[idx] - v_pred, axis=1) / kick
         assert np.median(ev) <= 2e-6 and ev.max() <= 1e-4, (k, np.median(ev), ev.max())
         assert np.abs(x1[idx] - x_pred).max() <= 1e-9
@@ -97,9 +99,15 @@ def test_precision_workload_steps(nb, oracle_mod, c3):
     P4, V4 = t(w.pos, np.float64), t(w.vel, np.float64)
     nb.nbody_leapfrog(P4, V4, M, w.eps, w.dt, w.steps)
     torch.cuda.synchronize()
-    # each one-step call took its own Morton order from its starting positions
+    # Each one-step call took its own Morton order and cell centres from its
+    # starting positions; the 4-step call keeps one order and centres its cells
+    # on the positions one step earlier.  The two runs differ only by the FP32
+    # rounding of their packed offsets: on the sample, within twice the
+    # per-step tolerance relative to the velocity change (two results, each
+    # within it of the exact one).
     assert np.abs(P4.cpu().numpy() - x).max() <= 1e-9
-    assert np.abs(V4.cpu().numpy() - v).max() <= 1e-7
+    d4 = np.linalg.norm(V4.cpu().numpy()[idx] - v[idx], axis=1) / kicks
+    assert np.median(d4) <= 4e-6 and d4.max() <= 2e-4, (np.median(d4), d4.max())
     assert nb.nbody_last_device_error() == 0
 
 
