@@ -9,7 +9,7 @@
 //             - sum_j s^{-3/2} d (mu_j m_k + mu_k m_j)               (potential)
 //   dL/dm_k = -sum_{j != k} [ s^{-3/2} (lam_j . d) + mu_j s^{-1/2} ]
 // (body k is the source of every pair (i, k) and the sink of every pair
-// (k, j); T(d) = T(-d) lets both be gathered at k).  Per pair that is 30
+// (k, j); T(d) = T(-d) lets both be gathered at k).  Per pair that is 29
 // packed FP32 operations and two MUFU reciprocal square roots, against 12 for
 // the force.
 //
@@ -50,7 +50,7 @@ struct VParams {
 };
 
 // UNI: every body has the same mass mu; u = m_k lam_j - m_j lam_k becomes
-// mu (lam_j - lam_k), formed without the masses (27 instead of 30 packed
+// mu (lam_j - lam_k), formed without the masses (26 instead of 29 packed
 // operations per pair), and the caller scales the position gradient by mu.
 // FULL: the whole tile; else j-bodies [jlo, jhi) of it (granule multiples).
 // FORCE: also the force a_k = sum_j m_j s^{-3/2} d at the same positions (3
@@ -93,7 +93,6 @@ __device__ __forceinline__ void vjp_tile(const unsigned char* tile, const f2 (&x
             const f2 ri = pk(q0, q1);
             const f2 ri2 = mul2(ri, ri);
             const f2 r3 = mul2(ri, ri2);
-            const f2 r5m3 = mul2(r3, mul2(ri2, m3));  // -3 s^{-5/2}
             // u = m_k lam_j - m_j lam_k (UNI: lam_j - lam_k, times mu later)
             const f2 ux = UNI ? add2(lxj, nlx[q]) : fma2(mi[q], lxj, mul2(mj, nlx[q]));
             const f2 uy = UNI ? add2(lyj, nly[q]) : fma2(mi[q], lyj, mul2(mj, nly[q]));
@@ -101,10 +100,12 @@ __device__ __forceinline__ void vjp_tile(const unsigned char* tile, const f2 (&x
             f2 du = mul2(dx, ux);
             du = fma2(dy, uy, du);
             du = fma2(dz, uz, du);
-            const f2 c = mul2(r5m3, du);
-            gx[q] = fma2(c, dx, fma2(r3, ux, gx[q]));
-            gy[q] = fma2(c, dy, fma2(r3, uy, gy[q]));
-            gz[q] = fma2(c, dz, fma2(r3, uz, gz[q]));
+            // T(d) u = s^{-3/2} (u - 3 s^{-1} (d.u) d): the same two terms as
+            // s^{-3/2} u - 3 s^{-5/2} (d.u) d, one product fewer per pair
+            const f2 e = mul2(mul2(ri2, m3), du);  // -3 s^{-1} (d.u)
+            gx[q] = fma2(r3, fma2(e, dx, ux), gx[q]);
+            gy[q] = fma2(r3, fma2(e, dy, uy), gy[q]);
+            gz[q] = fma2(r3, fma2(e, dz, uz), gz[q]);
             f2 dl = mul2(dx, lxj);
             dl = fma2(dy, lyj, dl);
             dl = fma2(dz, lzj, dl);
@@ -416,7 +417,7 @@ struct VjpFused {
 };
 
 template <typename L, bool FUSED = false>
-__global__ void __launch_bounds__(kVChunk) vjp_step_kernel(int64_t n, const double* __restrict__ pos,
+__global__ void __launch_bounds__(kVChunk, 1) vjp_step_kernel(int64_t n, const double* __restrict__ pos,
                                                            L* __restrict__ lam, double* __restrict__ lamx,
                                                            const float* __restrict__ gprev,
                                                            const float* __restrict__ gmprev,
@@ -453,7 +454,7 @@ __global__ void __launch_bounds__(kVChunk) vjp_step_kernel(int64_t n, const doub
             }
         } else {
             float a3[3] = {0.0f, 0.0f, 0.0f};
-            if (rev.a != nullptr) split_acc(rev.ss_acc, ba, g, g, rev.a, a3);
+            if (rev.a != nullptr) split_acc<16>(rev.ss_acc, ba, g, g, rev.a, a3);
             for (int c = 0; c < 3; ++c) {
                 w[c] = ld_chain(rev.vh + 3 * g + c) - rev.kick * (double)a3[c];
                 r[c] = ld_chain(rev.x + 3 * g + c) - rev.drift * w[c];
@@ -474,8 +475,8 @@ __global__ void __launch_bounds__(kVChunk) vjp_step_kernel(int64_t n, const doub
                     if (ss.partial != nullptr) {  // the previous VJP's partials, summed as its fixup would
                         if (bs.c_lo < bs.c_hi) {
                             float s4[4];
-                            split_sum(ss.partial, ss.block, bs.b, bs.c_lo, bs.c_hi, bs.slot_lo,
-                                      (int)(g - bs.b * ss.block), s4);
+                            split_sum<16>(ss.partial, ss.block, bs.b, bs.c_lo, bs.c_hi, bs.slot_lo,
+                                          (int)(g - bs.b * ss.block), s4);
                             gp[0] = s4[0];
                             gp[1] = s4[1];
                             gp[2] = s4[2];

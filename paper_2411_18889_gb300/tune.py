@@ -51,9 +51,60 @@ def _rules(sizes, winners):
     return out
 
 
+def survey_vjp(lib, vjp_sizes, rules, log):
+    """The VJP shapes, timed in their hot path: the adjoint sweep of a
+    recorded leapfrog (nbody_leapfrog_vjp_tape: one VJP per force evaluation,
+    most with the force at the same positions), equal masses as in the
+    adjoint workload, 8 steps with checkpoints every 4.  The sweep takes its
+    VJP shape from the table, so each shape is timed under a one-rule table
+    (the force rules kept)."""
+    import tempfile
+
+    import torch
+
+    import nbody_inputs as ni
+    from . import api
+
+    nv = 4
+    K, ck = 8, 4
+    force_rules = [l for l in rules if l.split()[0] == "force"]
+    tmp = tempfile.mkdtemp()
+    winners = []
+    try:
+        for n in vjp_sizes:
+            p, v, m = ni.plummer(n, 4)
+            M = torch.from_numpy(m.astype(np.float32)).cuda()
+            P = torch.from_numpy(p).cuda()
+            V = torch.from_numpy(v).cuda()
+            tape = torch.empty(api.nbody_tape_bytes(n, K, ck), dtype=torch.uint8, device="cuda")
+            api.nbody_leapfrog_record(P, V, M, 2.0 ** -7, 2.0 ** -8, K, ck, tape)
+            gxT = torch.from_numpy(ni.gaussian((n, 3), 5)).cuda()
+            zero = torch.zeros_like(gxT)
+            gx0, gv0 = torch.empty_like(gxT), torch.empty_like(gxT)
+            gm = torch.empty((n,), dtype=torch.float64, device="cuda")
+            reps = 2 if n >= (1 << 18) else 3
+            t = []
+            for k in range(nv):
+                path = os.path.join(tmp, f"vjp{k}.txt")
+                with open(path, "w") as f:
+                    f.write("\n".join(force_rules + [f"vjp 0 {k}"]) + "\n")
+                if lib.nbody_tune_load(path.encode()) <= 0:
+                    raise RuntimeError(f"the library rejected {path}")
+                t.append(_time(lambda: api.nbody_leapfrog_vjp_tape(M, 2.0 ** -7, 2.0 ** -8, K, ck, tape, gxT, zero,
+                                                                   gx0, gv0, gm), reps))
+            k = int(np.argmin(t))
+            winners.append(k)
+            log(f"vjp sweep n={n}: " + " ".join(f"{i}:{(K + 1) * n * n / x / 1e9:.0f}" for i, x in enumerate(t))
+                + f" Gint/s -> {k}")
+    finally:
+        import shutil
+        shutil.rmtree(tmp, ignore_errors=True)
+    return [f"vjp {n_min} {k}" for n_min, k in _rules(vjp_sizes, winners)]
+
+
 def survey(sizes=(1024, 4096, 16384, 32768, 65536, 262144, 1048576),
-           vjp_sizes=(1024, 4096, 16384, 32768, 65536, 262144),
-           out=DEFAULT_OUT, log=print):
+           vjp_sizes=(1024, 4096, 8192, 16384, 32768, 65536, 262144),
+           out=DEFAULT_OUT, log=print, kinds=("force", "vjp", "batched")):
     import torch
 
     import nbody_inputs as ni
@@ -66,7 +117,12 @@ def survey(sizes=(1024, 4096, 16384, 32768, 65536, 262144, 1048576),
              "# kind pot n_min shape (force), kind n_min shape (vjp), kind n_min shape (batched; n_min compared "
              "with the largest system)"]
     nf = lib.nbody_num_configs()
-    for pot in (0, 1):
+    keep = []  # the current table's rules, for the kinds not surveyed
+    if os.path.exists(out):
+        keep = [l.strip() for l in open(out) if l.strip() and not l.startswith("#")]
+    if "force" not in kinds:
+        lines += [l for l in keep if l.split()[0] == "force"]
+    for pot in ((0, 1) if "force" in kinds else ()):
         winners = []
         for n in sizes:
             p, v, m = ni.plummer(n, 3, masses="loguniform", offset=ni.plummer_offset())
@@ -98,27 +154,17 @@ def survey(sizes=(1024, 4096, 16384, 32768, 65536, 262144, 1048576),
                 + f" Gint/s -> {k}")
         for n_min, k in _rules(sizes, winners):
             lines.append(f"force {pot} {n_min} {k}")
-    nv = 4
-    winners = []
-    for n in vjp_sizes:
-        p, _, m = ni.plummer(n, 4, masses="loguniform")
-        P = torch.from_numpy(p).cuda()
-        M = torch.from_numpy(m.astype(np.float32)).cuda()
-        lam = torch.from_numpy(ni.gaussian((n, 3), 5).astype(np.float32)).cuda()
-        gp = torch.empty((n, 3), dtype=torch.float32, device="cuda")
-        gm = torch.empty((n,), dtype=torch.float32, device="cuda")
-        t = [_time(lambda k=k: api.nbody_accel_vjp(P, M, 2.0 ** -7, lam, None, gp, gm, config=k), 3)
-             for k in range(nv)]
-        k = int(np.argmin(t))
-        winners.append(k)
-        log(f"vjp n={n}: " + " ".join(f"{i}:{n * n / x / 1e9:.0f}" for i, x in enumerate(t)) + f" Gint/s -> {k}")
-    for n_min, k in _rules(vjp_sizes, winners):
-        lines.append(f"vjp {n_min} {k}")
+    if "vjp" in kinds:
+        lines += survey_vjp(lib, vjp_sizes, [l for l in lines if not l.startswith("#")], log)
+    else:
+        lines += [l for l in keep if l.split()[0] == "vjp"]
     # Batched: ragged families keyed by their largest system, each advanced a
     # few leapfrog steps in one persistent launch (the way ensembles run).
     nb_shapes = 4
     fam_max, bwin = [], []
-    for nmax, nsys in ((128, 4096), (512, 2048), (1024, 1024), (4096, 512)):
+    if "batched" not in kinds:
+        lines += [l for l in keep if l.split()[0] == "batched"]
+    for nmax, nsys in (((128, 4096), (512, 2048), (1024, 1024), (4096, 512)) if "batched" in kinds else ()):
         off, pos, vel, mass, eps = ni.ragged_batch(nsys=nsys, seed=4, nmin=max(16, nmax // 64), nmax=nmax)
         O = torch.from_numpy(off).cuda()
         P0 = torch.from_numpy(pos.astype(np.float32)).cuda()
@@ -137,7 +183,7 @@ def survey(sizes=(1024, 4096, 16384, 32768, 65536, 262144, 1048576),
         log(f"batched max {nmax}: " + " ".join(f"{i}:{x * 1e3:.2f}ms" for i, x in enumerate(t)) + f" -> {k}")
         fam_max.append(int(np.diff(off).max()))
         bwin.append(k)
-    for n_min, k in _rules(fam_max, bwin):
+    for n_min, k in (_rules(fam_max, bwin) if "batched" in kinds else ()):
         lines.append(f"batched {n_min} {k}")
     with open(out, "w") as f:
         f.write("\n".join(lines) + "\n")
@@ -150,8 +196,10 @@ def survey(sizes=(1024, 4096, 16384, 32768, 65536, 262144, 1048576),
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--out", default=DEFAULT_OUT)
+    ap.add_argument("--only", action="append", choices=["force", "vjp", "batched"],
+                    help="survey only these kernels (repeatable); the others keep the rules of the table at --out")
     args = ap.parse_args(argv)
-    print(survey(out=args.out))
+    print(survey(out=args.out, kinds=tuple(args.only) if args.only else ("force", "vjp", "batched")))
     return 0
 
 
