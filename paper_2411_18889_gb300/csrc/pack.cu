@@ -45,7 +45,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 // centres (pack_centre_doubles).
 constexpr int kChunk = 256;
 
-__global__ void __launch_bounds__(kChunk) pack_step_kernel(int64_t n, double* __restrict__ pos,
+template <int NB>
+__global__ void __launch_bounds__(kChunk, NB > 8 ? 1 : 2) pack_step_kernel(int64_t n, double* __restrict__ pos,
                                                            double* __restrict__ vel, const float* __restrict__ acc,
                                                            const float* __restrict__ mass, double kick, double drift,
                                                            int plain, float* __restrict__ jdup,
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(kChunk) pack_step_kernel(int64_t n, double* __
             double vx = ld_chain(vel + 3 * g + 0), vy = ld_chain(vel + 3 * g + 1), vz = ld_chain(vel + 3 * g + 2);
             if (acc != nullptr && kick != 0.0) {
                 float a3[3];
-                split_acc<16>(ss, bs, k, g, acc, a3);
+                split_acc<NB>(ss, bs, k, g, acc, a3);
                 vx += kick * (double)a3[0];
                 vy += kick * (double)a3[1];
                 vz += kick * (double)a3[2];
@@ -158,7 +159,8 @@ __global__ void __launch_bounds__(kChunk) pack_offsets_kernel(int64_t n, int blo
 // partial sums are all requested before any of them is used.
 constexpr int kMaxChunksPerCell = 8;  // blocks of up to 2048 bodies
 
-__global__ void __launch_bounds__(kChunk) pack_lagged_kernel(int64_t n, int block, double* __restrict__ pos,
+template <int NB>
+__global__ void __launch_bounds__(kChunk, NB > 8 ? 1 : 2) pack_lagged_kernel(int64_t n, int block, double* __restrict__ pos,
                                                              double* __restrict__ vel, const float* __restrict__ acc,
                                                              const float* __restrict__ mass, double kick,
                                                              double drift, float* __restrict__ jdup,
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(kChunk) pack_lagged_kernel(int64_t n, int bloc
         y = ld_chain(pos + 3 * g + 1);
         z = ld_chain(pos + 3 * g + 2);
         float a3[3];
-        split_acc<16>(ss, bs, k, g, acc, a3);
+        split_acc<NB>(ss, bs, k, g, acc, a3);
         vx += kick * (double)a3[0];
         vy += kick * (double)a3[1];
         vz += kick * (double)a3[2];
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(kChunk) pack_lagged_kernel(int64_t n, int bloc
 }
 
 // FP32 state, absolute coordinates: one thread per slot (256-slot chunks).
-__global__ void __launch_bounds__(kChunk) pack_f32_kernel(int64_t n, float* __restrict__ pos,
+__global__ void __launch_bounds__(kChunk, 2) pack_f32_kernel(int64_t n, float* __restrict__ pos,
                                                           float* __restrict__ vel, const float* __restrict__ acc,
                                                           const float* __restrict__ mass, float kick, float drift,
                                                           float* __restrict__ jdup, const SplitSums ss) {
@@ -322,6 +324,15 @@ unsigned grid_for(int64_t work, int threads) {
 
 }  // namespace
 
+// The pack kernels come in two variants that give the same bits: with 16
+// partial-sum loads in flight per body (one round of L2 latency for the ~20
+// CTAs' partials of a mid-size block; about 180 registers, one CTA per SM)
+// when the launch has at most one CTA per SM anyway, and with 8 (two CTAs per
+// SM, to hide the latency of the state gathers) when it has more.  At
+// N = 2^20 (4096 CTAs) a pack took 143 us with the one-CTA variant and 99 us
+// with the two-CTA one (CUDA events, GB300).
+static bool few_chunks(unsigned nch) { return nch <= (unsigned)current_sms(); }
+
 size_t pack_centre_doubles(int64_t npad, int block) { return 3 * (size_t)(npad / block) + 3 * (size_t)(npad / kChunk); }
 
 size_t pack_chunk_doubles(int64_t npad) { return 3 * (size_t)(npad / kChunk); }
@@ -334,8 +345,9 @@ cudaError_t pack_f64(int64_t n, int64_t npad, int block, double* pos, double* ve
     if (block % kChunk != 0 || npad % block != 0) return cudaErrorInvalidValue;
     const unsigned nch = (unsigned)(npad / kChunk);
     double* chunks = centres + 3 * (npad / block);
-    cudaError_t e = launch_pdl(pack_step_kernel, dim3(nch), dim3(kChunk), 0, st, n, pos, vel, acc, mass, kick, drift,
-                               plain ? 1 : 0, jdup, chunks, perm, err, ss != nullptr ? *ss : SplitSums());
+    cudaError_t e = launch_pdl(few_chunks(nch) ? pack_step_kernel<16> : pack_step_kernel<8>, dim3(nch), dim3(kChunk), 0,
+                               st, n, pos, vel, acc, mass, kick, drift, plain ? 1 : 0, jdup, chunks, perm, err,
+                               ss != nullptr ? *ss : SplitSums());
     if (e != cudaSuccess || plain) return e;
     return launch_pdl(pack_offsets_kernel, dim3(nch), dim3(kChunk), 0, st, n, block, (const double*)pos, mass, jdup,
                       centres, (const double*)chunks, perm, err);
@@ -348,8 +360,9 @@ cudaError_t pack_f64_lagged(int64_t n, int64_t npad, int block, double* pos, dou
     if (block % kChunk != 0 || block / kChunk > kMaxChunksPerCell || npad % block != 0 || vel == nullptr ||
         acc == nullptr)
         return cudaErrorInvalidValue;
-    return launch_pdl(pack_lagged_kernel, dim3((unsigned)(npad / kChunk)), dim3(kChunk), 0, st, n, block, pos, vel,
-                      acc, mass, kick, drift, jdup, centres, chunks_in, chunks_out, perm, err,
+    const unsigned nch = (unsigned)(npad / kChunk);
+    return launch_pdl(few_chunks(nch) ? pack_lagged_kernel<16> : pack_lagged_kernel<8>, dim3(nch), dim3(kChunk), 0,
+                      st, n, block, pos, vel, acc, mass, kick, drift, jdup, centres, chunks_in, chunks_out, perm, err,
                       ss != nullptr ? *ss : SplitSums());
 }
 
