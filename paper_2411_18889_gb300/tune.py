@@ -102,7 +102,7 @@ def survey_vjp(lib, vjp_sizes, rules, log):
     return [f"vjp {n_min} {k}" for n_min, k in _rules(vjp_sizes, winners)]
 
 
-def survey(sizes=(1024, 4096, 16384, 32768, 65536, 262144, 1048576),
+def survey(sizes=(1024, 4096, 8192, 16384, 32768, 65536, 262144, 1048576),
            vjp_sizes=(1024, 4096, 8192, 16384, 32768, 65536, 262144),
            out=DEFAULT_OUT, log=print, kinds=("force", "vjp", "batched")):
     import torch
