@@ -105,6 +105,31 @@ def test_host_state_roundtrip(nb):
     assert np.array_equal(ph, P.cpu().numpy()) and np.array_equal(vh, V.cpu().numpy())
 
 
+@pytest.mark.parametrize("n", [1024, 20011, 65536])
+def test_chained_launches_repeatable(nb, n):
+    """The kernels of a step are chained by programmatic dependent launch, so
+    each may start before its predecessor finishes; whatever the timing, the
+    same call gives the same bits (five device runs from fresh arrays, one
+    host run).  Reading the chain's data through the read-only path instead of
+    L2 once made these runs differ.  The sizes take the pack variant for fewer
+    CTAs than SMs (1024, 20011) and the one for more (65536)."""
+    import torch
+    p, v, m = ni.plummer(n, 16, masses="loguniform")
+    m32 = m.astype(np.float32)
+    runs = []
+    for _ in range(5):
+        P, V = t(p, np.float64), t(v, np.float64)
+        nb.nbody_leapfrog(P, V, t(m32, np.float32), 2.0 ** -8, 2.0 ** -8, 3)
+        torch.cuda.synchronize()
+        runs.append((P.cpu().numpy(), V.cpu().numpy()))
+    ph, vh = p.copy(), v.copy()
+    nb.nbody_leapfrog(ph, vh, m32, 2.0 ** -8, 2.0 ** -8, 3)
+    runs.append((ph, vh))
+    assert nb.nbody_last_device_error() == 0
+    for k, (pk_, vk_) in enumerate(runs[1:], 1):
+        assert np.array_equal(pk_, runs[0][0]) and np.array_equal(vk_, runs[0][1]), k
+
+
 def test_kepler_orbit_second_order(nb):
     """Eccentric binary (e=0.5, FP64 state) after 0.37 of a period matches
     Kepler's equation, with the error falling ~4x per halving of dt: the FP32
