@@ -172,7 +172,9 @@ NBODY_API int nbody_energy_f32(int64_t n, const float* pos, const float* vel, co
  * systems is computed on the device in both cases.
  * FP32 state and pair arithmetic; per-body sums in two levels (64-pair
  * blocks), plus a Kahan fold per tile for systems split over several CTAs.
- * opts->config selects the batched kernel shape (0 .. 3), -1 = the tuned
+ * opts->config selects the batched kernel shape (0 .. nbody_num_batched_configs()-1:
+ * threads per CTA, i-slots per warp, j-loop unroll and the depth of the FP32
+ * j-blocks differ), -1 = the tuned
  * choice for the largest system when the offsets are host memory, else 0;
  * precision and accumulate are ignored.
  */
@@ -263,6 +265,9 @@ NBODY_API int nbody_leapfrog_vjp_tape(int64_t n, const float* mass, double eps, 
  * bodies per i-block of shape k (0 if k is out of range). */
 NBODY_API int nbody_num_configs(void);
 NBODY_API int nbody_config_block(int k);
+/* Number of batched-kernel shapes compiled in (opts->config of the batched
+ * calls). */
+NBODY_API int nbody_num_batched_configs(void);
 
 /*
  * Kernel-shape table (the paper chose its thread count by a parameter survey

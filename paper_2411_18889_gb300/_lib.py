@@ -63,6 +63,7 @@ SIGNATURES = {
     "nbody_tune_load": (_int, [ctypes.c_char_p]),
     "nbody_tuned_shape": (_int, [_int, _i64, _int]),
     "nbody_num_configs": (_int, []),
+    "nbody_num_batched_configs": (_int, []),
     "nbody_config_block": (_int, [_int]),
     "nbody_last_device_error": (_int, []),
     "nbody_last_cuda_error": (_int, []),

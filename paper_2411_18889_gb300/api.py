@@ -257,6 +257,10 @@ def nbody_num_configs():
     return int(load().nbody_num_configs())
 
 
+def nbody_num_batched_configs():
+    return int(load().nbody_num_batched_configs())
+
+
 def nbody_config_block(k):
     return int(load().nbody_config_block(int(k)))
 

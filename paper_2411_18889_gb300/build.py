@@ -22,7 +22,9 @@ LIB = os.path.join(PKG, "libnbody.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["force.cu", "vjp.cu", "batched.cu", "order.cu", "pack.cu", "reduce.cu", "selftest.cu", "capi.cu", "noalloc.cu"]
 # The persistent batched kernel: one object per (shape, potential) instantiation.
-INSTANCES = [("batched_inst.cu", f"_{k}{p}", [f"-DNBK_BSHAPE={k}", f"-DNBK_BPOT={p}"]) for k in range(4) for p in range(2)]
+NUM_BATCHED_SHAPES = 6  # kNumBShapes in csrc/batched_kernel.cuh
+INSTANCES = [("batched_inst.cu", f"_{k}{p}", [f"-DNBK_BSHAPE={k}", f"-DNBK_BPOT={p}"])
+             for k in range(NUM_BATCHED_SHAPES) for p in range(2)]
 
 
 def nvcc() -> str:

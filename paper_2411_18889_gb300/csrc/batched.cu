@@ -170,6 +170,8 @@ const BShapeEntry* bshapes() {
         {{kBShapes[1].threads, kBShapes[1].ibodies}, {batched_fn_10(), batched_fn_11()}},
         {{kBShapes[2].threads, kBShapes[2].ibodies}, {batched_fn_20(), batched_fn_21()}},
         {{kBShapes[3].threads, kBShapes[3].ibodies}, {batched_fn_30(), batched_fn_31()}},
+        {{kBShapes[4].threads, kBShapes[4].ibodies}, {batched_fn_40(), batched_fn_41()}},
+        {{kBShapes[5].threads, kBShapes[5].ibodies}, {batched_fn_50(), batched_fn_51()}},
     };
     return table;
 }

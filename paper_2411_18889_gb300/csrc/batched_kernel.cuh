@@ -652,14 +652,17 @@ __global__ void __launch_bounds__(T, 512 / T) batched_kernel(const BParams p) {
     }
 }
 
-// The kernel shapes, (threads, i-slots per warp, j-unroll, j-block depth), by
-// shape index (the caller's opts->config).  0: one CTA per SM (systems from
-// about 760 bodies up); 2: two CTAs per SM; 1 and 3: smaller CTAs.
+// The kernel shapes, (threads, i-slots per warp, j-unroll, j-block depth in
+// pairs), by shape index (the caller's opts->config).  0: one CTA per SM
+// (systems from about 760 bodies up); 2: two CTAs per SM; 1 and 3: smaller
+// CTAs; 4 and 5: shape 0 with j-blocks of 32 and 128 pairs (the depth of the
+// FP32 partial sums folded into the totals), for the tuner to choose among.
 struct BShapeDef {
     int threads, ibodies, unroll, jblock;
 };
-constexpr int kNumBShapes = 4;
-constexpr BShapeDef kBShapes[kNumBShapes] = {{512, 4, 8, 64}, {128, 4, 4, 64}, {256, 4, 4, 64}, {128, 2, 4, 64}};
+constexpr int kNumBShapes = 6;
+constexpr BShapeDef kBShapes[kNumBShapes] = {{512, 4, 8, 64}, {128, 4, 4, 64}, {256, 4, 4, 64},
+                                             {128, 2, 4, 64}, {512, 4, 8, 32}, {512, 4, 8, 128}};
 
 typedef void (*BFn)(const BParams);
 
@@ -673,4 +676,8 @@ BFn batched_fn_20();
 BFn batched_fn_21();
 BFn batched_fn_30();
 BFn batched_fn_31();
+BFn batched_fn_40();
+BFn batched_fn_41();
+BFn batched_fn_50();
+BFn batched_fn_51();
 }  // namespace nbk

@@ -469,7 +469,9 @@ struct Opts {
     int config = -1;
 };
 
-int read_opts(const nbody_opts* o, Opts* r) {
+// max_config: the number of shapes of the call's kernel (force shapes unless
+// the call says otherwise; the batched calls have their own).
+int read_opts(const nbody_opts* o, Opts* r, int max_config = -1) {
     if (o == nullptr) return NBODY_OK;
     if (o->precision != NBODY_PREC_MIXED && o->precision != NBODY_PREC_PLAIN &&
         o->precision != NBODY_PREC_MIXED_UNSORTED)
@@ -477,7 +479,8 @@ int read_opts(const nbody_opts* o, Opts* r) {
     if (o->accumulate != NBODY_ACC_COMPENSATED && o->accumulate != NBODY_ACC_FP32 &&
         o->accumulate != NBODY_ACC_KAHAN_PAIR)
         return NBODY_EINVAL;
-    if (o->config < -1 || o->config >= nbk::force_num_shapes()) return NBODY_EINVAL;
+    if (max_config < 0) max_config = nbk::force_num_shapes();
+    if (o->config < -1 || o->config >= max_config) return NBODY_EINVAL;
     if (o->reserved != 0) return NBODY_EINVAL;
     r->stream = (cudaStream_t)o->stream;
     r->precision = o->precision;
@@ -605,8 +608,8 @@ struct Ctx {
     Workspace* ws;
 };
 
-int begin(const nbody_opts* opts, Ctx* c) {
-    NB_CHECK(read_opts(opts, &c->o));
+int begin(const nbody_opts* opts, Ctx* c, int max_config = -1) {
+    NB_CHECK(read_opts(opts, &c->o, max_config));
     NB_CHECK(device_check(&c->dev, &c->sms));
     c->ws = workspace(c->dev, c->o.stream);
     return NBODY_OK;
@@ -614,9 +617,9 @@ int begin(const nbody_opts* opts, Ctx* c) {
 
 int shape_for(const Ctx& c, int64_t n, bool pot) { return c.o.config >= 0 ? c.o.config : choose_shape(n, pot); }
 
-int check_opts_only(const nbody_opts* opts) {
+int check_opts_only(const nbody_opts* opts, int max_config = -1) {
     Opts o;
-    return read_opts(opts, &o);
+    return read_opts(opts, &o, max_config);
 }
 
 // ---- force evaluation on device arrays ----
@@ -667,6 +670,8 @@ void nbody_opts_default(nbody_opts* o) {
 int nbody_version(void) { return 1 * 10000 + 0 * 100 + 0; }
 
 int nbody_num_configs(void) { return nbk::force_num_shapes(); }
+
+int nbody_num_batched_configs(void) { return nbk::batched_num_shapes(); }
 
 int nbody_config_block(int k) {
     if (k < 0 || k >= nbk::force_num_shapes()) return 0;
@@ -1316,12 +1321,11 @@ static int batched_common(int64_t nsys, const int64_t* offsets, float* pos, floa
     if (nsys > 0 && (offsets == nullptr || pos == nullptr || mass == nullptr || eps == nullptr)) return NBODY_EINVAL;
     if (nsys > 0 && leapfrog && vel == nullptr) return NBODY_EINVAL;
     if (nsys > 0 && !leapfrog && acc == nullptr) return NBODY_EINVAL;
-    NB_CHECK(check_opts_only(opts));
-    if (opts != nullptr && opts->config >= nbk::batched_num_shapes()) return NBODY_EINVAL;
+    NB_CHECK(check_opts_only(opts, nbk::batched_num_shapes()));
     if (nsys == 0 || (leapfrog && steps == 0)) return NBODY_OK;
     if (nsys > (int64_t)1 << 30) return NBODY_EINVAL;
     Ctx c;
-    NB_CHECK(begin(opts, &c));
+    NB_CHECK(begin(opts, &c, nbk::batched_num_shapes()));
     cudaStream_t st = c.o.stream;
     int64_t max_ns = -1, ntot = -1;  // -1: not known on the host
     if (is_host_ptr(offsets)) {

@@ -160,7 +160,7 @@ def survey(sizes=(1024, 4096, 8192, 16384, 32768, 65536, 262144, 1048576),
         lines += [l for l in keep if l.split()[0] == "vjp"]
     # Batched: ragged families keyed by their largest system, each advanced a
     # few leapfrog steps in one persistent launch (the way ensembles run).
-    nb_shapes = 4
+    nb_shapes = lib.nbody_num_batched_configs()
     fam_max, bwin = [], []
     if "batched" not in kinds:
         lines += [l for l in keep if l.split()[0] == "batched"]

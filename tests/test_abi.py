@@ -27,6 +27,13 @@ def test_header_symbols_exported(lib):
         assert name in _lib.SIGNATURES, f"{name} has no ctypes signature in the binding"
 
 
+def test_batched_shape_count(lib):
+    """The GPU tests run every batched shape; they assume six (the build's
+    instantiations)."""
+    from paper_2411_18889_gb300 import build
+    assert lib.nbody_num_batched_configs() == build.NUM_BATCHED_SHAPES == 6
+
+
 def test_static_queries(lib):
     assert lib.nbody_version() >= 10000
     k = lib.nbody_num_configs()

@@ -7,6 +7,10 @@ import nbody_inputs as ni
 
 pytestmark = pytest.mark.gpu
 
+# every compiled batched shape (nbody_num_batched_configs(); the CPU tests
+# check that the library has exactly these)
+BATCH_SHAPES = range(6)
+
 ACC_MED, ACC_MAX, POT_MAX = 2e-6, 1e-4, 1e-5
 
 
@@ -51,7 +55,7 @@ def gpu_accel_batched(nb, off, pos, mass, eps, with_pot=True, **kw):
 SIZES = [1, 2, 3, 0, 63, 64, 65, 127, 511, 513, 1000, 2049, 4096, 5, 0, 777]
 
 
-@pytest.mark.parametrize("shape", range(4))
+@pytest.mark.parametrize("shape", BATCH_SHAPES)
 def test_accel_batched_matches_oracle(nb, oracle_mod, shape):
     off, pos, vel, mass, eps = make_batch(SIZES, 11 + shape)
     acc, pot = gpu_accel_batched(nb, off, pos, mass, eps, config=shape)
@@ -68,7 +72,7 @@ def test_accel_batched_matches_oracle(nb, oracle_mod, shape):
         assert rel(pot[a:b], rp).max() <= POT_MAX, (s, b - a)
 
 
-@pytest.mark.parametrize("shape", range(4))
+@pytest.mark.parametrize("shape", BATCH_SHAPES)
 def test_accel_batched_small_softening(nb, oracle_mod, shape):
     """Softenings far below the interparticle spacing (1e-6, 1e-5, 2^-12) beside
     eps = 4/sqrt(n), every kernel shape.  The self pair would add m_i/eps to the
@@ -167,7 +171,7 @@ ROUND_SIZES = [2112, 2200, 1700, 3600, 777, 513, 600, 1100, 2049]
 
 
 @pytest.mark.parametrize("eps_rule", ["4/sqrt(n)", 1e-5, 0.0])
-@pytest.mark.parametrize("shape", range(4))
+@pytest.mark.parametrize("shape", BATCH_SHAPES)
 def test_round_plans_match_oracle(nb, oracle_mod, shape, eps_rule):
     """Every round-plan mode (whole rounds, spread and split remainders, the
     latter adding segment sums staged in shared memory) against the oracle,
@@ -187,12 +191,13 @@ def test_round_plans_match_oracle(nb, oracle_mod, shape, eps_rule):
 
 # Systems larger than one CTA's shared-memory image (about 14,000 bodies for
 # shape 0, 4096 for the others when the sizes are not known on the host) are
-# split over several CTAs that stream the bodies in tiles.
-LARGE = {0: 20011, 1: 6000, 2: 9001, 3: 5000}
+# split over several CTAs that stream the bodies in tiles (shapes 4 and 5 are
+# shape 0 with other j-block depths: the same image).
+LARGE = {0: 20011, 1: 6000, 2: 9001, 3: 5000, 4: 20011, 5: 20011}
 
 
 @pytest.mark.parametrize("device_offsets", [False, True])
-@pytest.mark.parametrize("shape", range(4))
+@pytest.mark.parametrize("shape", BATCH_SHAPES)
 def test_large_member_every_shape(nb, oracle_mod, shape, device_offsets):
     """A batch with a member too large for one CTA's image beside small ones
     (and, with eps = 0 on the large one, its masked self pairs), every kernel
@@ -285,6 +290,21 @@ def test_batched_rejects_bad_offsets(nb, where):
             assert nb.nbody_last_device_error() == nb.NBODY_EINVAL
             assert bool((acc == 7.0).all())
     assert nb.nbody_last_device_error() == 0  # the flag was cleared
+
+
+def test_batched_config_range(nb):
+    """opts->config of a batched call is checked against the batched shapes,
+    not the force shapes: the last batched shape runs, one past it is
+    NBODY_EINVAL before any work is queued."""
+    import torch
+    k = nb.nbody_num_batched_configs()
+    assert k == len(BATCH_SHAPES)
+    off, pos, _, mass, eps = make_batch([100, 37], 23)
+    acc = torch.empty((pos.shape[0], 3), dtype=torch.float32, device="cuda")
+    nb.nbody_accel_batched(off, t(pos, np.float32), t(mass, np.float32), eps.astype(np.float32), acc, config=k - 1)
+    with pytest.raises(nb.NbodyError) as ei:
+        nb.nbody_accel_batched(off, t(pos, np.float32), t(mass, np.float32), eps.astype(np.float32), acc, config=k)
+    assert ei.value.code == nb.NBODY_EINVAL
 
 
 def test_batched_call_is_asynchronous(nb):

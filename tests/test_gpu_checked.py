@@ -146,7 +146,7 @@ def test_leapfrog_in_bounds(nb, checked_lib, precision):
     both(nb, checked_lib, run32)
 
 
-@pytest.mark.parametrize("shape", range(4))
+@pytest.mark.parametrize("shape", range(6))
 def test_batched_in_bounds(nb, checked_lib, shape):
     import torch
     # 15001 bodies: more than one CTA's image, so split over several CTAs
