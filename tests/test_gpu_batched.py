@@ -253,13 +253,18 @@ def test_large_member_leapfrog(nb, oracle_mod):
 
 
 def test_batched_deterministic_and_host_arrays(nb):
+    """Repeated calls give the same bits, and host arrays the same as device
+    ones.  The shape is named: a device-offset call takes shape 0 while a
+    host-offset call would take the tune table's choice for its largest
+    system, another blocking of the FP32 sums."""
     off, pos, vel, mass, eps = make_batch([100, 2000, 3, 700], 41)
-    a1, p1 = gpu_accel_batched(nb, off, pos, mass, eps)
-    a2, p2 = gpu_accel_batched(nb, off, pos, mass, eps)
+    a1, p1 = gpu_accel_batched(nb, off, pos, mass, eps, config=0)
+    a2, p2 = gpu_accel_batched(nb, off, pos, mass, eps, config=0)
     assert np.array_equal(a1, a2) and np.array_equal(p1, p2)
     acc_h = np.zeros((pos.shape[0], 3), np.float32)
     pot_h = np.zeros(pos.shape[0], np.float32)
-    nb.nbody_accel_batched(off, pos.astype(np.float32), mass.astype(np.float32), eps.astype(np.float32), acc_h, pot_h)
+    nb.nbody_accel_batched(off, pos.astype(np.float32), mass.astype(np.float32), eps.astype(np.float32), acc_h, pot_h,
+                           config=0)
     assert np.array_equal(acc_h, a1) and np.array_equal(pot_h, p1)
 
 
@@ -311,20 +316,22 @@ def test_batched_call_is_asynchronous(nb):
     """With device arrays a batched call queues its work and returns: an event
     recorded right after a long call (the ragged workload, 64 steps, about
     0.2 s of GPU time) is not complete when the call returns.  Its results
-    equal those of the same call with the offsets in host memory."""
+    equal those of the same call with the offsets in host memory (shape 0
+    named for both: a host-offset call would otherwise take the tune table's
+    choice for its largest system)."""
     import torch
     off, pos, vel, mass, eps = ni.ragged_batch()
     O, M, E = t(off, np.int64), t(mass, np.float32), t(eps, np.float32)
     P1, V1 = t(pos, np.float32), t(vel, np.float32)
     P2, V2 = P1.clone(), V1.clone()
     torch.cuda.synchronize()
-    nb.nbody_leapfrog_batched(O, P1, V1, M, E, 2.0 ** -8, 64)
+    nb.nbody_leapfrog_batched(O, P1, V1, M, E, 2.0 ** -8, 64, config=0)
     ev = torch.cuda.Event()
     ev.record()
     pending = not ev.query()
     torch.cuda.synchronize()
     assert pending
-    nb.nbody_leapfrog_batched(off, P2, V2, M, E, 2.0 ** -8, 64)  # host offsets
+    nb.nbody_leapfrog_batched(off, P2, V2, M, E, 2.0 ** -8, 64, config=0)  # host offsets
     torch.cuda.synchronize()
     assert nb.nbody_last_device_error() == 0
     assert torch.equal(P1, P2) and torch.equal(V1, V2)
