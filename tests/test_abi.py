@@ -126,6 +126,20 @@ def test_tune_table_parse_and_query(lib, tmp_path):
             assert 0 <= lib.nbody_tuned_shape(0, n, pot) < lib.nbody_num_configs()
 
 
+def test_tune_table_batched_shapes(lib, tmp_path):
+    """Batched rules are checked against the batched shapes (six), not the
+    force shapes (five): the last batched shape loads, one past it does not."""
+    k = lib.nbody_num_batched_configs()
+    f = tmp_path / "b.txt"
+    f.write_text(f"force 0 0 3\nbatched 0 {k - 1}\n")
+    assert lib.nbody_tune_load(str(f).encode()) == 2
+    assert lib.nbody_tuned_shape(2, 4096, 0) == k - 1
+    f.write_text(f"force 0 0 3\nbatched 0 {k}\n")
+    assert lib.nbody_tune_load(str(f).encode()) == -1
+    assert lib.nbody_tuned_shape(2, 4096, 0) == k - 1  # unchanged
+    assert lib.nbody_tune_load(None) >= 0
+
+
 def test_tune_table_fault_injection(lib, tmp_path, monkeypatch):
     """NBODY_FAULT=tune: reading a shape table fails as if the file were bad;
     the built-in table keeps serving and nothing touches a GPU."""
